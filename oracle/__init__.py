@@ -1,0 +1,276 @@
+"""DartMinHash ORACLE -- test infrastructure only.
+
+A plain CPU statement of the method of T. Christiani, "DartMinHash: Fast Sketching for
+Weighted Sets" (arXiv 2005.11547).  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s ``cpu_baseline`` leg / ``--impl reference`` arm may import this package.
+It shares no code, header, table or constant generator with the CUDA library in
+``paper_2005_11547_gb300``, and neither side imports the other.
+
+Contents
+  * ``t_of_k`` -- t = ceil(k ln k) + k (Theorem 1), from a 60-digit decimal logarithm.
+  * ``poisson_thresholds`` -- the inversion table for X ~ Poi(1) (Algorithm 1, "X ~ Poi(1)";
+    Section 4, "Implementation": a precomputed Poisson CDF table), exact to the last bit.
+  * ``sketch`` / ``sketch_bbit`` / ``lsh`` / ``darthash`` -- thin ctypes calls into
+    ``dm_oracle.c`` (Algorithm 1, Theorem 1, b-bit minhash, (L, K) LSH).
+  * ``bruteforce`` -- an independent exact-Fraction enumeration of the hashed dart process
+    over a bounding box, used to pin the C code.
+
+Parity of the hash bits themselves is unpinned by the paper (it prints no hash values and
+uses random tabulation tables); they are pinned only by the statistical tests in
+``tests/test_oracle_stats.py`` and by the brute force.
+"""
+from __future__ import annotations
+
+import ctypes
+import decimal
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+from fractions import Fraction
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libdmoracle.so")
+
+ERRORS = {0: "ok", 1: "invalid argument", 2: "out of memory", 5: "out of supported range",
+          6: "phi limit reached"}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int):
+        super().__init__(f"oracle error {code}: {ERRORS.get(code, '?')}")
+        self.code = code
+
+
+# ------------------------------------------------------------------------------------------
+# build / load
+# ------------------------------------------------------------------------------------------
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile dm_oracle.c (plain C, no contraction of a*b+c, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64, i32, u64, dbl, flt = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                  ctypes.c_double, ctypes.c_float)
+        lib.dmo_sketch.argtypes = [P, P, P, i64, i32, u64, i64, P, dbl, i32, P, P]
+        lib.dmo_sketch.restype = ctypes.c_int
+        lib.dmo_sketch_bbit.argtypes = [P, P, P, i64, i32, i32, u64, i64, P, P, P]
+        lib.dmo_sketch_bbit.restype = ctypes.c_int
+        lib.dmo_lsh.argtypes = [P, P, P, i64, i32, i32, u64, P, dbl, P, P]
+        lib.dmo_lsh.restype = ctypes.c_int
+        lib.dmo_darthash.argtypes = [P, P, i64, i64, u64, P, flt, P, i64, P]
+        lib.dmo_darthash.restype = ctypes.c_int64
+        lib.dmo_dart_record_size.restype = ctypes.c_int64
+        lib.dmo_mix64.argtypes = [u64]
+        lib.dmo_mix64.restype = u64
+        assert lib.dmo_dart_record_size() == DART_DTYPE.itemsize
+        _lib = lib
+        return lib
+
+
+# ------------------------------------------------------------------------------------------
+# exact constants
+# ------------------------------------------------------------------------------------------
+def t_of_k(k: int) -> int:
+    """t = ceil(k ln k) + k (Theorem 1's proof).  k ln k is irrational for k >= 2, so a
+    60-digit logarithm decides the ceiling; the margin is asserted."""
+    if k < 1:
+        raise ValueError("k >= 1")
+    if k == 1:
+        return 1
+    with decimal.localcontext() as c:
+        c.prec = 60
+        v = decimal.Decimal(k) * decimal.Decimal(k).ln()
+        f = int(v.to_integral_value(rounding=decimal.ROUND_CEILING))
+        assert f - v > decimal.Decimal("1e-40") and v - (f - 1) > decimal.Decimal("1e-40")
+    return f + k
+
+
+def _einv_bounds(terms: int = 60):
+    """Rational lower/upper bounds on e^{-1} from its alternating series."""
+    s, term = Fraction(0), Fraction(1)
+    for l in range(terms):
+        s += term if l % 2 == 0 else -term
+        term /= (l + 1)
+    return s - term, s + term
+
+
+def poisson_thresholds() -> np.ndarray:
+    """T[n] = ceil(2^32 * P(Poi(1) <= n)) for n = 0..11 (T[12] would be 2^32).
+
+    With u uniform on [0, 2^32), X = #{n : u >= T[n]} has P(X = n) = (T[n] - T[n-1]) / 2^32,
+    i.e. the Poisson(1) pmf to within 2^-32, and X <= 12."""
+    lo, hi = _einv_bounds()
+    out, cum, fact = [], Fraction(0), Fraction(1)
+    for n in range(12):
+        if n:
+            fact /= n
+        cum += fact
+        a, b = lo * cum * 2 ** 32, hi * cum * 2 ** 32
+        ca, cb = -((-a.numerator) // a.denominator), -((-b.numerator) // b.denominator)
+        assert ca == cb, "bounds too loose"
+        out.append(ca)
+    assert out[-1] < 2 ** 32
+    return np.array(out, dtype=np.uint32)
+
+
+_T = None
+
+
+def _table():
+    global _T
+    if _T is None:
+        _T = np.ascontiguousarray(poisson_thresholds())
+    return _T
+
+
+# ------------------------------------------------------------------------------------------
+# calls
+# ------------------------------------------------------------------------------------------
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _csr(indptr, indices, weights):
+    indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(indices, dtype=np.uint32)
+    weights = np.ascontiguousarray(weights, dtype=np.float32)
+    assert indptr.ndim == 1 and indptr[0] == 0 and indptr[-1] <= len(indices) == len(weights)
+    return indptr, indices, weights
+
+
+def _chunks(n, threads):
+    threads = max(1, min(threads, n))
+    b = np.linspace(0, n, threads + 1).astype(np.int64)
+    return [(int(b[i]), int(b[i + 1])) for i in range(threads) if b[i + 1] > b[i]]
+
+
+def _run_chunked(n, threads, fn):
+    ch = _chunks(n, threads)
+    if len(ch) <= 1:
+        rcs = [fn(0, n)] if n else [0]
+    else:
+        with ThreadPoolExecutor(len(ch)) as ex:
+            rcs = list(ex.map(lambda c: fn(*c), ch))
+    rc = next((r for r in rcs if r), 0)
+    if rc:
+        raise OracleError(rc)
+
+
+def sketch(indptr, indices, weights, k: int, seed: int, *, phi0: float = 1.0,
+           schedule: str = "double", threads: int = 1, work: bool = False):
+    """k minhash keys per row (uint64[n, k]); Theorem 1 with Algorithm 1 as inner step.
+    ``schedule`` 'double' (phi <- 2 phi) or 'step' (phi <- phi + 1, Theorem 1's literal loop).
+    With ``work=True`` also returns int64[n, 4]: areas, darts, kept darts, passes."""
+    lib = _load()
+    indptr, indices, weights = _csr(indptr, indices, weights)
+    n = len(indptr) - 1
+    out = np.empty((n, k), dtype=np.uint64)
+    wk = np.zeros((n, 4), dtype=np.int64)
+    t, T = t_of_k(k), _table()
+    sch = {"double": 0, "step": 1}[schedule]
+
+    def fn(a, b):
+        ip = indptr[a:b + 1]
+        return lib.dmo_sketch(_ptr(ip), _ptr(indices), _ptr(weights), b - a, k, seed & (2**64 - 1),
+                              t, _ptr(T), float(phi0), sch,
+                              ctypes.c_void_p(out.ctypes.data + a * k * 8),
+                              ctypes.c_void_p(wk.ctypes.data + a * 32))
+
+    _run_chunked(n, threads, fn)
+    return (out, wk) if work else out
+
+
+def sketch_bbit(indptr, indices, weights, k: int, b: int, seed: int, *, threads: int = 1,
+                keys: bool = False):
+    """b-bit packed sketches: uint64[n, ceil(k b / 64)] (and the uint64 keys if asked)."""
+    lib = _load()
+    indptr, indices, weights = _csr(indptr, indices, weights)
+    n = len(indptr) - 1
+    words = (k * b + 63) // 64
+    out = np.empty((n, words), dtype=np.uint64)
+    kout = np.empty((n, k), dtype=np.uint64) if keys else None
+    t, T = t_of_k(k), _table()
+
+    def fn(a, e):
+        ip = indptr[a:e + 1]
+        return lib.dmo_sketch_bbit(_ptr(ip), _ptr(indices), _ptr(weights), e - a, k, b,
+                                   seed & (2**64 - 1), t, _ptr(T),
+                                   ctypes.c_void_p(out.ctypes.data + a * words * 8),
+                                   ctypes.c_void_p(kout.ctypes.data + a * k * 8) if keys else None)
+
+    _run_chunked(n, threads, fn)
+    return (out, kout) if keys else out
+
+
+def lsh(indptr, indices, weights, L: int, K: int, seed: int, *, phi0: float = 1.0,
+        threads: int = 1, work: bool = False):
+    """(L, K) LSH values uint32[n, L] (t = L K, L buckets, hash of the sorted bottom-K keys)."""
+    lib = _load()
+    indptr, indices, weights = _csr(indptr, indices, weights)
+    n = len(indptr) - 1
+    out = np.empty((n, L), dtype=np.uint32)
+    wk = np.zeros((n, 4), dtype=np.int64)
+    T = _table()
+
+    def fn(a, b):
+        ip = indptr[a:b + 1]
+        return lib.dmo_lsh(_ptr(ip), _ptr(indices), _ptr(weights), b - a, L, K, seed & (2**64 - 1),
+                           _ptr(T), float(phi0), ctypes.c_void_p(out.ctypes.data + a * L * 4),
+                           ctypes.c_void_p(wk.ctypes.data + a * 32))
+
+    _run_chunked(n, threads, fn)
+    return (out, wk) if work else out
+
+
+DART_DTYPE = np.dtype({
+    "names": ["pos", "i", "nu", "rho", "w", "r", "j", "u", "v", "code", "q"],
+    "formats": [np.int64, np.uint32, np.int32, np.int32, np.uint64, np.uint64, np.int32,
+                np.uint32, np.uint32, np.uint32, np.uint64],
+    "offsets": [0, 8, 12, 16, 24, 32, 40, 44, 48, 52, 56],
+    "itemsize": 64})
+
+
+def darthash(indices, weights, t: int, seed: int, theta: float, cap: int = 1 << 20):
+    """The kept darts of one row at rank limit theta (Algorithm 1's output set D) plus the
+    work counts (areas, darts generated, darts kept)."""
+    lib = _load()
+    indices = np.ascontiguousarray(indices, dtype=np.uint32)
+    weights = np.ascontiguousarray(weights, dtype=np.float32)
+    out = np.empty(cap, dtype=DART_DTYPE)
+    wk = np.zeros(3, dtype=np.int64)
+    n = lib.dmo_darthash(_ptr(indices), _ptr(weights), len(indices), t, seed & (2**64 - 1),
+                         _ptr(_table()), float(np.float32(theta)), _ptr(out), cap, _ptr(wk))
+    if n < 0:
+        raise OracleError(-n)
+    assert n <= cap, "increase cap"
+    return out[:n].copy(), wk
+
+
+def mix64(z: int) -> int:
+    return int(_load().dmo_mix64(z & (2**64 - 1)))
+
+
+def fastrange32(h, n):
+    return (np.asarray(h, dtype=np.uint64) * np.uint64(n)) >> np.uint64(32)

@@ -1,0 +1,193 @@
+"""Seeded synthetic weighted-set generators shared by the tests, the bench and the oracle legs.
+
+This module holds no part of the method's arithmetic (no hashing, no dart logic): it only
+draws CSR batches of weighted sets with numpy's PCG64 generator, following the recipes
+below.  Data seed = 1000 + workload number; every call with the same arguments returns the
+same arrays.
+
+  W0  1,000 sets, universe d = 100,000, 64 distinct uniform indices per set (sorted),
+      weights Uniform(0, 1] fp32 (drawn as 1 - u).                         k = 64
+  W1  1,000,000 sets, d = 2^20, 256 distinct uniform indices, weights Exponential(1) fp32.
+                                                                   k = 256 and 1-bit
+  W2  200,000 sets, d = 2^24, nnz = round(exp(ln 100 + 1.5 z)) clipped to [1, 100,000],
+      weights lognormal(0, 1) rescaled per set so ||x||_1 = 10^U(-3, 3).          k = 1024
+  W4  request stream: Poisson arrivals at 50,000/s; nnz = min(100,000, floor(Pareto(1.2)))
+      with x_m = 1; d = 2^24; weights Uniform(0, 5]; k uniform over {64, 256, 1024}.
+
+Plus the pair recipe of the paper's Section 4 ("Synthetic data"): y_i = b x_i on supp(x)
+and y_j = 1 - b on one fresh element j, with ||x||_1 = 1, so J(x, y) = b / (2 - b).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Batch:
+    indptr: np.ndarray      # int64[n + 1]
+    indices: np.ndarray     # uint32[nnz]
+    weights: np.ndarray     # float32[nnz]
+    name: str = ""
+    params: dict = field(default_factory=dict)
+
+    @property
+    def n_sets(self) -> int:
+        return len(self.indptr) - 1
+
+    @property
+    def nnz(self) -> int:
+        return int(self.indptr[-1])
+
+    def rows(self, sel):
+        """Sub-batch of the given row numbers (copied, re-based CSR)."""
+        sel = np.asarray(sel, dtype=np.int64)
+        lens = self.indptr[sel + 1] - self.indptr[sel]
+        ip = np.zeros(len(sel) + 1, dtype=np.int64)
+        np.cumsum(lens, out=ip[1:])
+        take = np.concatenate([np.arange(self.indptr[s], self.indptr[s + 1]) for s in sel]) \
+            if len(sel) else np.zeros(0, dtype=np.int64)
+        return Batch(ip, self.indices[take].copy(), self.weights[take].copy(), self.name,
+                     dict(self.params, rows=len(sel)))
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def distinct_sorted_rows(rng, n: int, m: int, d: int) -> np.ndarray:
+    """n rows of m distinct indices uniform on [0, d), each row sorted ascending."""
+    out = np.sort(rng.integers(0, d, size=(n, m), dtype=np.int64), axis=1)
+    while True:
+        bad = np.nonzero((np.diff(out, axis=1) == 0).any(axis=1))[0] if m > 1 else np.zeros(0, int)
+        if len(bad) == 0:
+            return out.astype(np.uint32)
+        out[bad] = np.sort(rng.integers(0, d, size=(len(bad), m), dtype=np.int64), axis=1)
+
+
+def fixed_nnz_batch(n: int, nnz: int, d: int, weight: str, seed: int, name: str = "") -> Batch:
+    rng = _rng(seed)
+    idx = distinct_sorted_rows(rng, n, nnz, d).reshape(-1)
+    if weight == "uniform01":
+        w = (1.0 - rng.random(n * nnz, dtype=np.float32)).astype(np.float32)
+    elif weight == "exp1":
+        w = rng.standard_exponential(n * nnz, dtype=np.float32)
+    else:
+        raise ValueError(weight)
+    ip = np.arange(0, (n + 1) * nnz, nnz, dtype=np.int64)
+    return Batch(ip, idx, w, name, dict(n=n, nnz=nnz, d=d, weight=weight, seed=seed))
+
+
+def workload0(n: int = 1000) -> Batch:
+    """W0: 1,000 sets x 64 distinct indices over d = 100,000, weights U(0, 1]."""
+    return fixed_nnz_batch(n, 64, 100_000, "uniform01", 1000, "W0")
+
+
+def workload1(n: int = 1_000_000) -> Batch:
+    """W1: 1,000,000 sets x 256 distinct indices over d = 2^20, weights Exp(1)."""
+    return fixed_nnz_batch(n, 256, 1 << 20, "exp1", 1001, "W1")
+
+
+def _ragged_distinct(rng, lens: np.ndarray, d: int) -> np.ndarray:
+    """Concatenated rows of distinct uniform indices on [0, d) with the given lengths,
+    each row sorted."""
+    n = len(lens)
+    ip = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=ip[1:])
+    row = np.repeat(np.arange(n, dtype=np.int64), lens)
+    vals = rng.integers(0, d, size=int(ip[-1]), dtype=np.int64)
+    while True:
+        key = row * d + vals
+        order = np.argsort(key, kind="stable")
+        key = key[order]
+        vals = vals[order]
+        dup = np.zeros(len(key), dtype=bool)
+        dup[1:] = key[1:] == key[:-1]
+        if not dup.any():
+            return vals.astype(np.uint32)
+        vals[dup] = rng.integers(0, d, size=int(dup.sum()), dtype=np.int64)
+
+
+def workload2(n: int = 200_000) -> Batch:
+    """W2: heavy-tailed nnz (log-normal, median 100, sigma 1.5, clipped to [1, 1e5]) over
+    d = 2^24; weights lognormal(0, 1) rescaled so ||x||_1 is log-uniform on [1e-3, 1e3]."""
+    rng = _rng(1002)
+    lens = np.clip(np.rint(np.exp(np.log(100.0) + 1.5 * rng.standard_normal(n))), 1, 100_000)
+    lens = lens.astype(np.int64)
+    idx = _ragged_distinct(rng, lens, 1 << 24)
+    z = rng.lognormal(0.0, 1.0, size=int(lens.sum()))
+    ip = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=ip[1:])
+    target = 10.0 ** rng.uniform(-3.0, 3.0, size=n)
+    sums = np.add.reduceat(z, ip[:-1])
+    w = (z * np.repeat(target / sums, lens)).astype(np.float32)
+    return Batch(ip, idx, w, "W2", dict(n=n, d=1 << 24, seed=1002))
+
+
+def workload4_requests(rate: float = 50_000.0, seconds: float = 60.0, max_requests: int | None = None):
+    """W4 request stream: (arrival times [s], Batch of one set per request, k per request)."""
+    rng = _rng(1004)
+    n = int(rng.poisson(rate * seconds))
+    if max_requests is not None:
+        n = min(n, max_requests)
+    gaps = rng.exponential(1.0 / rate, size=n)
+    arrivals = np.cumsum(gaps)
+    lens = np.minimum(100_000, np.floor(rng.pareto(1.2, size=n) + 1.0)).astype(np.int64)
+    idx = _ragged_distinct(rng, lens, 1 << 24)
+    w = (5.0 * (1.0 - rng.random(int(lens.sum())))).astype(np.float32)
+    ip = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=ip[1:])
+    ks = rng.choice(np.array([64, 256, 1024], dtype=np.int32), size=n)
+    return arrivals, Batch(ip, idx, w, "W4", dict(n=n, rate=rate, seed=1004)), ks
+
+
+def random_sets(n: int, nnz_lo: int, nnz_hi: int, d: int, seed: int, scale_lo=1e-3, scale_hi=1e3,
+                name="random") -> Batch:
+    """Test batch with ragged nnz in [nnz_lo, nnz_hi] and ||x||_1 log-uniform on
+    [scale_lo, scale_hi] (weights lognormal before scaling)."""
+    rng = _rng(seed)
+    lens = rng.integers(nnz_lo, nnz_hi + 1, size=n).astype(np.int64)
+    idx = _ragged_distinct(rng, lens, d)
+    z = rng.lognormal(0.0, 1.0, size=int(lens.sum()))
+    ip = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=ip[1:])
+    if n and lens.min() > 0:
+        target = np.exp(rng.uniform(np.log(scale_lo), np.log(scale_hi), size=n))
+        sums = np.add.reduceat(z, ip[:-1])
+        z = z * np.repeat(target / sums, lens)
+    return Batch(ip, idx, z.astype(np.float32), name, dict(n=n, seed=seed))
+
+
+def simplex_set(rng, nnz: int, l1: float = 1.0, d: int = 1 << 32):
+    """Section 4's synthetic set: a uniform point of the probability simplex (normalised
+    Exp(1) draws) scaled to ||x||_1 = l1, on nnz distinct random elements."""
+    idx = np.sort(rng.choice(d, size=nnz, replace=False)).astype(np.uint32) if d <= 1 << 24 else \
+        distinct_sorted_rows(rng, 1, nnz, d)[0]
+    e = rng.standard_exponential(nnz)
+    return idx, (l1 * e / e.sum()).astype(np.float32)
+
+
+def similar_pair(rng, nnz: int, b: float, d: int = 1 << 30):
+    """Section 4's pair: x on the simplex (||x||_1 = 1), y_i = b x_i, plus y_j = 1 - b on an
+    element j outside supp(x).  Returns (idx_x, w_x, idx_y, w_y)."""
+    idx = distinct_sorted_rows(rng, 1, nnz + 1, d)[0]
+    perm = rng.permutation(nnz + 1)
+    ix, extra = np.sort(idx[perm[:nnz]]), idx[perm[nnz]]
+    e = rng.standard_exponential(nnz)
+    wx = (e / e.sum()).astype(np.float32)
+    wy = (np.float32(b) * wx).astype(np.float32)
+    iy = np.concatenate([ix, [extra]]).astype(np.uint32)
+    wyy = np.concatenate([wy, [np.float32(1.0 - b)]]).astype(np.float32)
+    o = np.argsort(iy)
+    return ix, wx, iy[o], wyy[o]
+
+
+def csr_of(rows) -> Batch:
+    """CSR Batch from a list of (indices, weights) rows."""
+    lens = np.array([len(r[0]) for r in rows], dtype=np.int64)
+    ip = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(lens, out=ip[1:])
+    idx = np.concatenate([np.asarray(r[0], dtype=np.uint32) for r in rows]) if rows else np.zeros(0, np.uint32)
+    w = np.concatenate([np.asarray(r[1], dtype=np.float32) for r in rows]) if rows else np.zeros(0, np.float32)
+    return Batch(ip, idx.astype(np.uint32), w.astype(np.float32), "rows")
