@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the DartMinHash hot path on GB300.
+
+One step = one dm_sketch_bbit call over workload W1 (1,000,000 weighted sets, 256 distinct
+elements each over d = 2^20, Exp(1) weights): k = 256 uint64 minhash keys plus the 1-bit
+packed sketch (4 words) per set, inputs and outputs resident in HBM (2 GB in, 2 GB out: far
+larger than the 129 MB L2, so no flush between steps).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dm|reference] [--sets N]
+
+Under torchrun (N > 1) every rank sketches its own W1 batch on its own GPU (weak scaling,
+no data-path collective); the barrier and the max-over-ranks time use torch.distributed.
+--impl reference times the oracle (plain single-threaded C per set, run over all host cores)
+on the same workload, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K_SLOTS = 256
+B_BITS = 1
+SEED = 1
+METRIC = "weighted sets/s (k=256 minhashes + 1-bit sketch, bit-exact)"
+
+# Algorithmic integer work per unit (32-bit lane operations), counted from the method's own
+# arithmetic: SplitMix64's output function = 3 xor-shifts of a 64-bit word (4 ops each) + 2
+# 64-bit multiplies by constants (3 ops each) = 18.
+OPS_MIX = 18
+OPS_PER_AREA = 2 + OPS_MIX + 2              # counter step, hash, Poisson inversion (E[X]+1 compares)
+OPS_PER_DART = 2 + OPS_MIX + 3 + 1 + 4 + 4 + 1   # counter, hash, U/V, weight test, rank, code, compare
+OPS_PER_KEPT = OPS_MIX + 1 + 1 + 1          # bucket/fingerprint hash, fastrange, key, min
+INT_LANES_PER_SM = 128                      # 4 schedulers x 32 lanes, one integer op per lane per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["dm", "reference"], default="dm")
+    ap.add_argument("--sets", type=int, default=1_000_000, help="prefix of W1 (profiling only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# distributed plumbing (host logic; covered by gloo tests)
+# ------------------------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(world: int, use_cuda: bool):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return dist
+
+
+def barrier(dist, use_cuda: bool):
+    import torch
+    if use_cuda:
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float, use_cuda: bool) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if use_cuda else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float, use_cuda: bool) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if use_cuda else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        return summarize_clocks(rows)
+
+
+def summarize_clocks(rows):
+    import statistics
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# traffic from the committed ncu capture (valid only for the kernel source it was taken on)
+# ------------------------------------------------------------------------------------------
+def kernel_fingerprint() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2005_11547_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_set():
+    path = os.path.join(ROOT, "profiles", "sketch_w1_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("kernel_fingerprint") != kernel_fingerprint():
+        return None
+    return d.get("dram_bytes_per_set")
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ------------------------------------------------------------------------------------------
+def time_oracle(batch, n_sample: int, cores: int):
+    import oracle
+    sub = batch.rows(range(min(n_sample, batch.n_sets)))
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.sketch_bbit(sub.indptr, sub.indices, sub.weights, K_SLOTS, B_BITS, SEED, keys=True, threads=cores)
+    dt = time.perf_counter() - t0
+    return sub.n_sets / dt, sub.n_sets, dt
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads
+    b = workloads.workload1(min(args.sets, 200_000))
+    cores = os.cpu_count() or 1
+    per_step = 4000 * cores
+    sets = []
+    for s in range(args.warmup + args.steps):
+        lo = (s * per_step) % max(1, b.n_sets - per_step)
+        sub = b.rows(range(lo, lo + per_step))
+        v, n, dt = time_oracle(sub, per_step, cores)
+        if s >= args.warmup:
+            sets.append((n, dt))
+    n_tot = sum(n for n, _ in sets)
+    t_tot = sum(dt for _, dt in sets)
+    value = n_tot / t_tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "minhashes_per_s": value * K_SLOTS,
+        "config": {"workload": "W1: 1,000,000 sets x 256 distinct elements (d=2^20), Exp(1) fp32 weights; "
+                               "k=256 uint64 keys + 1-bit words", "k": K_SLOTS, "b": B_BITS,
+                   "step": f"{per_step} sets of W1 per step (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": "sets/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} W1 sets per step x {args.steps} steps"},
+        "e2e": {"value": value, "unit": "sets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    import paper_2005_11547_gb300 as dmx
+    import workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, True)
+    dmx.build()
+    dmx.load()
+    props = torch.cuda.get_device_properties(local)
+
+    b = workloads.workload1(args.sets)
+    n = b.n_sets
+    words = (K_SLOTS * B_BITS + 63) // 64
+    ip = torch.from_numpy(b.indptr).cuda()
+    ix = torch.from_numpy(b.indices.view(np.int32)).cuda()
+    w = torch.from_numpy(b.weights).cuda()
+    keys = torch.empty((n, K_SLOTS), dtype=torch.int64, device="cuda")
+    outw = torch.empty((n, words), dtype=torch.int64, device="cuda")
+    ctx = dmx.dm_create(local)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dmx.dm_sketch_bbit(ctx, ip, ix, w, K_SLOTS, B_BITS, SEED, out_words=outw, out_keys=keys, stream=stream)
+
+    # work units of one launch (untimed counting launch; counters never change output bits)
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    cctx = dmx.dm_create(local)
+    dmx.dm_set_option(cctx, dmx.OPT_COUNTERS, cnt.data_ptr())
+    dmx.dm_sketch_bbit(cctx, ip, ix, w, K_SLOTS, B_BITS, SEED, out_words=outw, out_keys=keys, stream=stream)
+    dmx.dm_sync_status(cctx)
+    areas, darts, kept, passes = [int(v) for v in cnt.cpu().tolist()]
+    cctx.close()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    dmx.dm_sync_status(ctx)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(dist, True)
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    barrier(dist, True)
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    dmx.dm_sync_status(ctx)
+    per_launch_ms = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
+    total_ms = starts[0].elapsed_time(ends[-1])
+    t_max = max_over_ranks(dist, total_ms / 1e3, True)
+    all_sets = sum_over_ranks(dist, float(n * args.steps), True)
+    value = all_sets / t_max
+
+    # end to end through the host-buffer C-ABI entry (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hip = torch.from_numpy(b.indptr).pin_memory()
+        hix = torch.from_numpy(b.indices.view(np.int32)).pin_memory()
+        hw = torch.from_numpy(b.weights).pin_memory()
+        hk = torch.empty((n, K_SLOTS), dtype=torch.int64).pin_memory()
+        hwd = torch.empty((n, words), dtype=torch.int64).pin_memory()
+        dmx.dm_sketch_host(ctx, hip, hix, hw, K_SLOTS, SEED, out_keys=hk, b=B_BITS, out_words=hwd)
+        e2e_steps = max(2, min(args.steps, 5))
+        barrier(dist, True)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            dmx.dm_sketch_host(ctx, hip, hix, hw, K_SLOTS, SEED, out_keys=hk, b=B_BITS, out_words=hwd)
+        barrier(dist, True)
+        te = max_over_ranks(dist, time.perf_counter() - t0, True)
+        if not np.array_equal(hk.numpy(), keys.cpu().numpy()):
+            raise RuntimeError("host-entry keys differ from the device-resident run")
+        h2d = b.indptr.nbytes + b.indices.nbytes + b.weights.nbytes
+        d2h = hk.numel() * 8 + hwd.numel() * 8
+        e2e = {"value": world * n * e2e_steps / te, "unit": "sets/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+        del hip, hix, hw, hk, hwd
+
+    # roofline of the dominant (only) kernel of the step
+    mean_launch_s = sum(per_launch_ms) / len(per_launch_ms) / 1e3
+    ops = areas * OPS_PER_AREA + darts * OPS_PER_DART + kept * OPS_PER_KEPT
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak_ops = props.multi_processor_count * INT_LANES_PER_SM * sm_max * 1e6
+    achieved = ops / mean_launch_s
+    tps = ncu_traffic_per_set()
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                "frac": achieved / peak_ops, "traffic": (tps * n if tps is not None else None),
+                "ops_per_launch": ops, "units_per_launch": {"areas": areas, "darts": darts, "kept": kept,
+                                                            "passes": passes},
+                "hbm_gbs_algorithmic": (b.indptr.nbytes + b.indices.nbytes + b.weights.nbytes
+                                        + keys.numel() * 8 + outw.numel() * 8) / mean_launch_s / 1e9,
+                "peak_source": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int32 lanes x "
+                               f"{sm_max:.0f} MHz (max SM clock)"}
+
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v, ns, dt = time_oracle(b, 16000 * cores // 4, cores)
+        cpu_baseline = {"value": v, "unit": "sets/s", "cores": cores, "kind": "oracle",
+                        "sample": f"first {ns} sets of W1 ({dt:.1f} s wall on {cores} threads)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "minhashes_per_s": value * K_SLOTS,
+            "config": {"workload": "W1: 1,000,000 sets x 256 distinct elements (d=2^20), Exp(1) fp32 weights; "
+                                   "k=256 uint64 keys + 1-bit words" if n == 1_000_000 else f"W1 prefix of {n} sets",
+                       "n_sets": n, "k": K_SLOTS, "b": B_BITS, "seed": SEED, "form": "plain (one warp per set)",
+                       "l2": "inputs 2 GB and outputs 2 GB per step, > 129 MB L2: no flush needed"},
+            "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": args.steps, "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,131 @@
+/*
+ * dartminhash.h -- C ABI of the GB300 (sm_103a) DartMinHash library, libdartminhash.so.
+ *
+ * Method: T. Christiani, "DartMinHash: Fast Sketching for Weighted Sets" (arXiv 2005.11547).
+ *   DartHash (Section 2, Algorithm 1) enumerates the darts of a hashed Poisson dart process
+ *   that hit a weighted set x with rank below a limit; DartMinHash (Section 3, Theorem 1)
+ *   hashes every dart to one of k buckets and keeps the smallest-rank dart per bucket,
+ *   repeating with a doubled limit while a bucket is empty.
+ *
+ * Conventions shared by every call
+ *   - Sets come as CSR: indptr int64[n_sets + 1] (indptr[0] = 0, non-decreasing), indices
+ *     uint32[indptr[n_sets]] (element ids i), weights float32[indptr[n_sets]] (x_i).
+ *     Weights must be finite and >= 0 (the domain R^d_{>=0} of Section 1); zero weights are
+ *     skipped (Algorithm 1 visits only {i | x_i > 0}); a repeated index acts as the largest of
+ *     its weights; element order inside a row does not matter.
+ *   - Unless a call says otherwise, every array argument is a DEVICE pointer owned by the
+ *     caller; the library reads/writes it only on `stream` and keeps no reference after the
+ *     work queued on `stream` completes.  `stream` is a cudaStream_t passed as void* (NULL =
+ *     the legacy default stream).
+ *   - Output key layout: out[s * k + j] is minhash j of set s, the 64-bit key
+ *         (code(rank) << 32) | fingerprint
+ *     where code(rank) is the IEEE binary32 bit pattern of the winning dart's rank rounded
+ *     toward zero and fingerprint a 32-bit hash of the dart.  Keys of two sets are equal iff
+ *     the same dart wins (up to a 2^-32 fingerprint coincidence at equal rank codes).  A set
+ *     with no positive weight gets 0xFFFFFFFFFFFFFFFF in every slot.
+ *   - The same (row, k, seed) always gives the same bits on every GPU, batch composition,
+ *     launch form and tuning choice.
+ *   - Return value: DM_OK or an error code.  Argument errors found on the host are returned
+ *     at once and nothing is queued.  Errors found by the kernels (a negative/NaN/Inf weight:
+ *     DM_EINVAL; a weight with t*x_i >= 2^39 - 1 or a set needing a rank limit >= 2^39 - 1:
+ *     DM_ERANGE) are recorded in the context and returned by dm_sync_status(); the rows they
+ *     concern are filled with 0xFF bytes.
+ *   - Thread safety: one dm_ctx per host thread (or serialize calls on a context).
+ */
+#ifndef DARTMINHASH_H
+#define DARTMINHASH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dm_ctx dm_ctx;
+
+enum dm_status {
+    DM_OK = 0,
+    DM_EINVAL = 1,     /* invalid argument or invalid weight */
+    DM_ENOMEM = 2,     /* device or pinned allocation failed, or over the memory budget */
+    DM_ECUDA = 3,      /* a CUDA runtime call failed */
+    DM_ETIMEOUT = 4,   /* a bounded device wait gave up */
+    DM_ERANGE = 5,     /* input outside the supported numeric range (see above) */
+    DM_EOVERFLOW = 6   /* the doubling loop of Theorem 1 reached its limit */
+};
+
+/* Create a context on CUDA device `device`.  `mem_budget_bytes` caps the device scratch the
+ * context may allocate (0 = no cap).  Uploads the Poisson(1) inversion table of
+ * Algorithm 1 to the device.  *out receives the context (owned by the caller; release with
+ * dm_destroy).  Returns DM_EINVAL for a bad device, DM_ECUDA on a runtime failure. */
+int dm_create(dm_ctx **out, int device, size_t mem_budget_bytes);
+
+/* Release the context and everything it allocated.  NULL is accepted. */
+int dm_destroy(dm_ctx *ctx);
+
+/* k independent weighted minhashes per set (Theorem 1, with Algorithm 1 as the inner
+ * step; t = ceil(k ln k) + k).  out: uint64[n_sets * k] (layout above).  1 <= k <= 8192,
+ * n_sets >= 0; seed selects the hash functions. */
+int dm_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+              int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream);
+
+/* b-bit minhash (Section 1.1, "Similarity estimation": each minhash mapped by a random hash to
+ * b bits; for b = 1, 64 minhashes per machine word).  b in {1, 2, 4, 8, 16, 32}.
+ * out_words: uint64[n_sets * W], W = ceil(k * b / 64); slot j of set s occupies bits
+ * (j*b) mod 64 .. +b-1 of word s*W + floor(j*b/64), least significant bit first; unused high
+ * bits of a row's last word are zero.  The b-bit value of a slot is the low b bits of
+ * SplitMix64's output function applied to (key XOR 0xA4093822299F31D0).  out_keys, when not
+ * NULL, also receives the uint64 keys exactly as dm_sketch writes them (uint64[n_sets * k]). */
+int dm_sketch_bbit(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+                   int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_words,
+                   uint64_t *out_keys, void *stream);
+
+/* Fully independent (L, K) LSH values (Section 1.2 "Fast similarity search" and Section 3,
+ * "Bottom-k minhash and fast approximate near neighbor search"): t = L*K, darts hashed to
+ * L buckets, the rank limit doubled until every bucket holds >= K darts; table l's value is
+ * the high 32 bits of the chain h <- SplitMix64out(h XOR key_m) over the bucket's K smallest
+ * keys in increasing order, from h = 0x082EFA98EC4E6C89.  Two sets collide in a table with
+ * probability J^K, independently across tables.  out: uint32[n_sets * L]; a set with no
+ * positive weight gets 0xFFFFFFFF.  1 <= L <= 1024, 1 <= K <= 32. */
+int dm_lsh(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+           int64_t n_sets, int32_t L, int32_t K, uint64_t seed, uint32_t *out, void *stream);
+
+/* dm_sketch / dm_sketch_bbit with HOST arrays: indptr, indices, weights, out_keys and
+ * out_words are host pointers (page-locked memory gives full copy speed).  b = 0 computes keys
+ * only (out_keys required, out_words ignored); b in {1, 2, 4, 8, 16, 32} also writes the b-bit
+ * words (out_keys may then be NULL).  The library copies the batch to context-owned device
+ * buffers on `stream` in chunks, overlapping the copies of one chunk with the kernel of the
+ * previous one, and returns after every output is back in host memory (synchronous).
+ * Returns DM_ENOMEM if the staging buffers would exceed the context's memory budget. */
+int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+                   int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_keys,
+                   uint64_t *out_words, void *stream);
+
+/* Wait for `stream`, then return (and clear) the first error recorded by a kernel of this
+ * context, or DM_ECUDA if the stream itself failed. */
+int dm_sync_status(dm_ctx *ctx, void *stream);
+
+/* Static English description of a status code. */
+const char *dm_strerror(int status);
+
+/* Tuning and instrumentation options (dm_set_option).  None of them changes any output bit. */
+enum dm_option {
+    DM_OPT_PHI0 = 1,        /* initial phi of Theorem 1's loop, as value/1024 (default 1024 = 1.0) */
+    DM_OPT_COUNTERS = 2,    /* device pointer to uint64[4] accumulating areas inspected, darts
+                               generated, darts kept and passes (0 = off) */
+    DM_OPT_FORM = 3,        /* launch form: 0 = plain (one warp per set), 1 = batched persistent */
+    DM_OPT_WARPS_PER_BLOCK = 4
+};
+int dm_set_option(dm_ctx *ctx, int option, int64_t value);
+
+/* t = ceil(k ln k) + k as the library computes it (Theorem 1's proof); 0 for k < 1. */
+int64_t dm_t_of_k(int32_t k);
+
+/* The Poisson(1) inversion thresholds the library uses: T[n] = ceil(2^32 P(Poi(1) <= n)),
+ * n = 0..11, written to host array out[12]. */
+void dm_poisson_thresholds(uint32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DARTMINHASH_H */

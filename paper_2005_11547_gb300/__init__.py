@@ -1,0 +1,220 @@
+"""GB300 (sm_103a) DartMinHash: Python binding of libdartminhash.so.
+
+Argument marshalling only: every step of the hot path runs in the library's CUDA kernels.
+The functions carry the C ABI's names (include/dartminhash.h) and take torch tensors that
+already live on the GPU (the ``*_host`` entry takes host tensors).  There is no CPU
+fallback: if the library is missing or fails to load, every call raises.
+
+    ctx = dm_create(device=0)
+    keys = dm_sketch(ctx, indptr, indices, weights, k=256, seed=1)       # uint64 as int64
+    words = dm_sketch_bbit(ctx, indptr, indices, weights, k=256, b=1, seed=1)
+    dm_sync_status(ctx)   # raises DartMinHashError on a device-detected input error
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB, build
+
+__all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
+           "dm_sketch_host", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
+           "dm_poisson_thresholds", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
+           "OPT_WARPS_PER_BLOCK"]
+
+OPT_PHI0, OPT_COUNTERS, OPT_FORM, OPT_WARPS_PER_BLOCK = 1, 2, 3, 4
+_lock = threading.Lock()
+_lib = None
+
+
+class DartMinHashError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = dm_strerror(code) if _lib is not None else str(code)
+        super().__init__(f"{what}: DM status {code} ({msg})")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Load libdartminhash.so (built in-tree by build()).  Raises if it is absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libdartminhash.so is not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+        sig = {
+            "dm_create": ([ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
+            "dm_destroy": ([P], ctypes.c_int),
+            "dm_sketch": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
+            "dm_sketch_bbit": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
+            "dm_lsh": ([P, P, P, P, i64, i32, i32, u64, P, P], ctypes.c_int),
+            "dm_sketch_host": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
+            "dm_sync_status": ([P, P], ctypes.c_int),
+            "dm_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "dm_set_option": ([P, ctypes.c_int, i64], ctypes.c_int),
+            "dm_t_of_k": ([i32], i64),
+            "dm_poisson_thresholds": ([P], None),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise DartMinHashError(rc, what)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_ptr(t, dtype_name, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    want = {"int64": (torch.int64,), "uint32": (torch.int32, torch.uint32), "float32": (torch.float32,),
+            "uint64": (torch.int64, torch.uint64)}[dtype_name]
+    if t.dtype not in want:
+        raise TypeError(f"{what} must be {dtype_name} (got {t.dtype})")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns a dm_ctx*."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.dm_create(ctypes.byref(h), int(device), int(mem_budget_bytes)), "dm_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            load().dm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dm_create(device: int = 0, mem_budget_bytes: int = 0) -> Context:
+    return Context(device, mem_budget_bytes)
+
+
+def dm_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def _csr_ptrs(indptr, indices, weights):
+    n = indptr.numel() - 1
+    return (n, _dev_ptr(indptr, "int64", "indptr"), _dev_ptr(indices, "uint32", "indices"),
+            _dev_ptr(weights, "float32", "weights"))
+
+
+def dm_sketch(ctx: Context, indptr, indices, weights, k: int, seed: int, out=None, stream=None):
+    """uint64[n_sets, k] minhash keys (returned as an int64 tensor holding the same bits)."""
+    import torch
+    n, ip, ix, w = _csr_ptrs(indptr, indices, weights)
+    if out is None:
+        out = torch.empty((n, k), dtype=torch.int64, device=indptr.device)
+    elif out.numel() != n * k:
+        raise ValueError("out has the wrong size")
+    _check(load().dm_sketch(ctx.handle, ip, ix, w, n, int(k), int(seed) & (2**64 - 1),
+                            _dev_ptr(out, "uint64", "out"), _stream(stream)), "dm_sketch")
+    return out
+
+
+def dm_sketch_bbit(ctx: Context, indptr, indices, weights, k: int, b: int, seed: int, out_words=None,
+                   out_keys=None, stream=None):
+    """b-bit packed sketches uint64[n_sets, ceil(k b / 64)] (int64 tensor); fills out_keys too
+    when given."""
+    import torch
+    n, ip, ix, w = _csr_ptrs(indptr, indices, weights)
+    words = (k * b + 63) // 64
+    if out_words is None:
+        out_words = torch.empty((n, words), dtype=torch.int64, device=indptr.device)
+    kp = _dev_ptr(out_keys, "uint64", "out_keys") if out_keys is not None else None
+    _check(load().dm_sketch_bbit(ctx.handle, ip, ix, w, n, int(k), int(b), int(seed) & (2**64 - 1),
+                                 _dev_ptr(out_words, "uint64", "out_words"), kp, _stream(stream)),
+           "dm_sketch_bbit")
+    return out_words
+
+
+def dm_lsh(ctx: Context, indptr, indices, weights, L: int, K: int, seed: int, out=None, stream=None):
+    """uint32[n_sets, L] (L, K) LSH values (returned as an int32 tensor holding the same bits)."""
+    import torch
+    n, ip, ix, w = _csr_ptrs(indptr, indices, weights)
+    if out is None:
+        out = torch.empty((n, L), dtype=torch.int32, device=indptr.device)
+    _check(load().dm_lsh(ctx.handle, ip, ix, w, n, int(L), int(K), int(seed) & (2**64 - 1),
+                         _dev_ptr(out, "uint32", "out"), _stream(stream)), "dm_lsh")
+    return out
+
+
+def dm_sketch_host(ctx: Context, indptr, indices, weights, k: int, seed: int, out_keys=None, b: int = 0,
+                   out_words=None, stream=None):
+    """dm_sketch (b = 0) or dm_sketch_bbit (b > 0) on host tensors (pinned memory for full copy
+    speed); synchronous.  Returns (out_keys, out_words)."""
+    import torch
+    n = indptr.numel() - 1
+    words = (k * b + 63) // 64 if b else 0
+    if out_keys is None and b == 0:
+        out_keys = torch.empty((n, k), dtype=torch.int64)
+    if out_words is None and b > 0:
+        out_words = torch.empty((n, words), dtype=torch.int64)
+    for t in (indptr, indices, weights, out_keys, out_words):
+        if t is not None and (t.is_cuda or not t.is_contiguous()):
+            raise ValueError("host entry takes contiguous CPU tensors")
+    if out_keys is not None and out_keys.numel() != n * k:
+        raise ValueError("out_keys must hold n_sets * k values")
+    if out_words is not None and out_words.numel() != n * words:
+        raise ValueError("out_words must hold n_sets * ceil(k b / 64) words")
+    P = ctypes.c_void_p
+    _check(load().dm_sketch_host(ctx.handle, P(indptr.data_ptr()), P(indices.data_ptr()),
+                                 P(weights.data_ptr()), n, int(k), int(b), int(seed) & (2**64 - 1),
+                                 P(out_keys.data_ptr()) if out_keys is not None else None,
+                                 P(out_words.data_ptr()) if out_words is not None else None,
+                                 _stream(stream)), "dm_sketch_host")
+    return out_keys, out_words
+
+
+def dm_sync_status(ctx: Context, stream=None, raise_on_error: bool = True) -> int:
+    rc = load().dm_sync_status(ctx.handle, _stream(stream))
+    if rc and raise_on_error:
+        raise DartMinHashError(rc, "device status")
+    return rc
+
+
+def dm_strerror(code: int) -> str:
+    return load().dm_strerror(int(code)).decode()
+
+
+def dm_set_option(ctx: Context, option: int, value: int) -> None:
+    _check(load().dm_set_option(ctx.handle, int(option), int(value)), "dm_set_option")
+
+
+def dm_t_of_k(k: int) -> int:
+    return int(load().dm_t_of_k(int(k)))
+
+
+def dm_poisson_thresholds():
+    arr = (ctypes.c_uint32 * 12)()
+    load().dm_poisson_thresholds(ctypes.cast(arr, ctypes.c_void_p))
+    return [int(v) for v in arr]

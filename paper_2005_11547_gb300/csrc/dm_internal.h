@@ -1,0 +1,40 @@
+// Internal declarations shared by the host API and the kernel launchers.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dartminhash.h"
+
+namespace dm {
+
+struct SketchParams {
+    const int64_t *indptr;
+    const uint32_t *indices;
+    const float *weights;
+    int64_t n_sets;
+    int32_t k;            // buckets (minhashes) per set, or L for LSH
+    int32_t K;            // LSH: darts kept per bucket (0 for sketches)
+    uint32_t t;           // Theorem 1: ceil(k ln k) + k; LSH: L K
+    uint64_t sigma;       // seed key
+    float phi0;           // initial phi of Theorem 1's loop
+    int32_t b;            // b-bit width (bbit mode)
+    int32_t words;        // uint64 words per set in bbit mode
+    uint64_t *out_keys;   // n_sets * k keys (may be null in bbit mode)
+    uint64_t *out_words;  // bbit words (bbit mode only)
+    uint32_t *out_lsh;    // LSH values (LSH mode only)
+    int *status;          // first device-detected error
+    unsigned long long *counters;   // optional work counters (4)
+    int32_t warp_bytes;   // dynamic shared memory per warp
+    int32_t warps_per_block;
+    const int32_t *order; // optional set order (persistent form), may be null
+    unsigned int *next;   // optional work counter for dynamic scheduling (persistent form)
+};
+
+// Per-warp shared memory for the sketch kernel (k slots + staging rings + tile arrays).
+size_t sketch_warp_bytes(int k);
+
+cudaError_t upload_poisson_table(const uint32_t *T);
+cudaError_t launch_sketch(const SketchParams &p, bool bbit, bool count, int grid, cudaStream_t st);
+
+}  // namespace dm

@@ -1,0 +1,259 @@
+"""GPU parity of dm_sketch / dm_sketch_bbit with the oracle: bit-exact uint64 keys (integer
+work, so the bar is exact equality), at small sizes in full and at the full W1/W2 sizes on
+sampled rows, in the launch configuration the bench uses, plus edge cases."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+U64MAX = np.uint64(2 ** 64 - 1)
+THREADS = 16
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def dmx(torch_mod):
+    import paper_2005_11547_gb300 as dmx
+    dmx.build()
+    dmx.load()
+    return dmx
+
+
+@pytest.fixture(scope="module")
+def ctx(dmx):
+    c = dmx.dm_create(0)
+    yield c
+    c.close()
+
+
+def to_dev(torch, b):
+    return (torch.from_numpy(np.ascontiguousarray(b.indptr, dtype=np.int64)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(b.indices, dtype=np.uint32).view(np.int32)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(b.weights, dtype=np.float32)).cuda())
+
+
+def gpu_sketch(dmx, torch, ctx, b, k, seed):
+    ip, ix, w = to_dev(torch, b)
+    out = dmx.dm_sketch(ctx, ip, ix, w, k, seed)
+    rc = dmx.dm_sync_status(ctx, raise_on_error=False)
+    return out.cpu().numpy().view(np.uint64), rc
+
+
+def assert_same(got, exp, what=""):
+    if not np.array_equal(got, exp):
+        bad = np.argwhere(got != exp)
+        r, c = bad[0]
+        raise AssertionError(f"{what}: {len(bad)} mismatches; first row {r} slot {c}: "
+                             f"gpu {int(got[r, c]):016x} oracle {int(exp[r, c]):016x}")
+
+
+def test_w0_full_parity(dmx, torch_mod, ctx, oracle_mod):
+    """W0 in full: 1,000 sets, 64 elements, k = 64, seed 1."""
+    b = workloads.workload0()
+    got, rc = gpu_sketch(dmx, torch_mod, ctx, b, 64, 1)
+    assert rc == 0
+    assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, 64, 1, threads=THREADS), "W0")
+
+
+@pytest.mark.parametrize("k", [1, 2, 7, 64, 100, 256, 1000, 1024])
+def test_ragged_sets_parity(dmx, torch_mod, ctx, oracle_mod, k):
+    """Ragged nnz (0..300, several 32-element tiles and a ragged tail), ||x||_1 over six
+    decades, several k including non powers of two."""
+    b = workloads.random_sets(300, 0, 300, 1 << 24, seed=10 + k)
+    got, rc = gpu_sketch(dmx, torch_mod, ctx, b, k, 12345)
+    assert rc == 0
+    assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 12345, threads=THREADS), f"k={k}")
+
+
+def test_extreme_norms_parity(dmx, torch_mod, ctx, oracle_mod):
+    """||x||_1 from 1e-6 to 1e6: many rank regions (small norms) or many weight regions."""
+    rows = []
+    rng = np.random.default_rng(3)
+    for l1 in [1e-6, 1e-4, 1e-2, 1.0, 1e2, 1e4, 1e6]:
+        for nnz in [1, 5, 40]:
+            idx = np.sort(rng.choice(1 << 30, nnz, replace=False)).astype(np.uint32)
+            z = rng.exponential(size=nnz)
+            rows.append((idx, (z / z.sum() * l1).astype(np.float32)))
+    b = workloads.csr_of(rows)
+    for k in (16, 256):
+        got, rc = gpu_sketch(dmx, torch_mod, ctx, b, k, 99)
+        assert rc == 0
+        assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 99), f"k={k}")
+
+
+def test_edge_cases_parity(dmx, torch_mod, ctx, oracle_mod):
+    f = np.float32
+    rows = [
+        ([], []),                                         # empty row
+        ([3, 4], [0.0, 0.0]),                             # all zero -> sentinel
+        ([7], [1.0]),                                     # single element
+        ([1, 2, 3], [0.0, 0.5, 0.0]),                     # zeros inside
+        ([5, 5, 5], [0.25, 0.75, 0.5]),                   # duplicates act as the max
+        ([5], [0.75]),
+        ([0, 4294967295], [1e-30, 2.5]),                  # extreme index and tiny weight
+        ([11], [np.float32(1e-40)]),                      # subnormal weight
+        ([9, 10], [-0.0, 3.0]),                           # negative zero is a zero weight
+    ]
+    # weights whose t x lands exactly on a region edge 2^nu - 1 for k = 2 (t = 4)
+    rows += [([20, 21], [0.75, 1.75]), ([22], [0.25])]
+    b = workloads.csr_of([(np.array(i, np.uint32), np.array(w, f)) for i, w in rows])
+    for k in (1, 2, 3, 64):
+        got, rc = gpu_sketch(dmx, torch_mod, ctx, b, k, 5)
+        assert rc == 0
+        exp = oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 5)
+        assert_same(got, exp, f"k={k}")
+    assert (got[0] == U64MAX).all() and (got[1] == U64MAX).all()
+    assert (got[4] == got[5]).all()
+
+
+def test_large_row_parity(dmx, torch_mod, ctx, oracle_mod):
+    """One set with 100,000 elements (the W2 clip) next to tiny ones."""
+    rng = np.random.default_rng(44)
+    big = np.sort(rng.choice(1 << 24, 100_000, replace=False)).astype(np.uint32)
+    rows = [(big, rng.lognormal(size=100_000).astype(np.float32)),
+            (np.array([1], np.uint32), np.array([0.5], np.float32))]
+    b = workloads.csr_of(rows)
+    got, rc = gpu_sketch(dmx, torch_mod, ctx, b, 1024, 8)
+    assert rc == 0
+    assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, 1024, 8), "big")
+
+
+def test_invalid_and_out_of_range_weights(dmx, torch_mod, ctx, oracle_mod):
+    f = np.float32
+    rows = [([1, 2], [0.5, 0.5]), ([1, 2], [0.5, -1.0]), ([3], [np.nan]), ([4], [np.inf]),
+            ([5, 6], [0.25, 0.125])]
+    b = workloads.csr_of([(np.array(i, np.uint32), np.array(w, f)) for i, w in rows])
+    got, rc = gpu_sketch(dmx, torch_mod, ctx, b, 32, 3)
+    assert rc == 1                                              # DM_EINVAL
+    assert (got[1:4] == U64MAX).all()
+    good = b.rows([0, 4])
+    assert_same(got[[0, 4]], oracle_mod.sketch(good.indptr, good.indices, good.weights, 32, 3), "valid rows")
+    assert dmx.dm_sync_status(ctx, raise_on_error=False) == 0   # status cleared
+    big = workloads.csr_of([(np.array([1], np.uint32), np.array([2.0 ** 39], f))])
+    got, rc = gpu_sketch(dmx, torch_mod, ctx, big, 1, 3)
+    assert rc == 5                                              # DM_ERANGE
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.sketch(big.indptr, big.indices, big.weights, 1, 3)
+
+
+@pytest.mark.parametrize("bits", [1, 2, 4, 8, 16, 32])
+def test_bbit_parity(dmx, torch_mod, ctx, oracle_mod, bits):
+    b = workloads.random_sets(200, 1, 120, 1 << 20, seed=70 + bits)
+    ip, ix, w = to_dev(torch_mod, b)
+    for k in (64, 100, 256):
+        keys = torch_mod.empty((b.n_sets, k), dtype=torch_mod.int64, device="cuda")
+        words = dmx.dm_sketch_bbit(ctx, ip, ix, w, k, bits, 21, out_keys=keys)
+        assert dmx.dm_sync_status(ctx, raise_on_error=False) == 0
+        ew, ek = oracle_mod.sketch_bbit(b.indptr, b.indices, b.weights, k, bits, 21, keys=True,
+                                        threads=THREADS)
+        assert_same(words.cpu().numpy().view(np.uint64), ew, f"b={bits} k={k} words")
+        assert_same(keys.cpu().numpy().view(np.uint64), ek, f"b={bits} k={k} keys")
+
+
+def test_options_do_not_change_bits(dmx, torch_mod, ctx):
+    b = workloads.random_sets(400, 1, 200, 1 << 24, seed=5)
+    ref, _ = gpu_sketch(dmx, torch_mod, ctx, b, 256, 77)
+    again, _ = gpu_sketch(dmx, torch_mod, ctx, b, 256, 77)
+    assert_same(again, ref, "repeat")
+    for opt, val in [(dmx.OPT_PHI0, 512), (dmx.OPT_PHI0, 4096), (dmx.OPT_PHI0, 1024 * 3),
+                     (dmx.OPT_WARPS_PER_BLOCK, 1), (dmx.OPT_WARPS_PER_BLOCK, 3)]:
+        c2 = dmx.dm_create(0)
+        dmx.dm_set_option(c2, opt, val)
+        got, rc = gpu_sketch(dmx, torch_mod, c2, b, 256, 77)
+        c2.close()
+        assert rc == 0
+        assert_same(got, ref, f"option {opt}={val}")
+
+
+def test_counters_and_streams(dmx, torch_mod, ctx, oracle_mod):
+    torch = torch_mod
+    b = workloads.workload0(300)
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    c2 = dmx.dm_create(0)
+    dmx.dm_set_option(c2, dmx.OPT_COUNTERS, cnt.data_ptr())
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ip, ix, w = to_dev(torch, b)
+        out = dmx.dm_sketch(c2, ip, ix, w, 64, 1, stream=s)
+    assert dmx.dm_sync_status(c2, stream=s, raise_on_error=False) == 0
+    c2.close()
+    got = out.cpu().numpy().view(np.uint64)
+    exp, wk = oracle_mod.sketch(b.indptr, b.indices, b.weights, 64, 1, work=True)
+    assert_same(got, exp, "counted")
+    areas, darts, kept, passes = cnt.cpu().tolist()
+    assert abs(passes - wk[:, 3].sum()) <= 2              # same retry decisions as the oracle
+    assert abs(darts - areas) < 5 * areas ** 0.5          # Poi(1) darts per area
+    assert kept >= wk[:, 2].sum() * 0.5
+
+
+def test_host_entry_matches_device(dmx, torch_mod, ctx):
+    torch = torch_mod
+    b = workloads.random_sets(500, 1, 100, 1 << 20, seed=8)
+    ref, _ = gpu_sketch(dmx, torch, ctx, b, 128, 4)
+    ip = torch.from_numpy(b.indptr.astype(np.int64)).pin_memory()
+    ix = torch.from_numpy(b.indices.view(np.int32)).pin_memory()
+    w = torch.from_numpy(b.weights).pin_memory()
+    out = torch.empty((b.n_sets, 128), dtype=torch.int64).pin_memory()
+    dmx.dm_sketch_host(ctx, ip, ix, w, 128, 4, out)
+    assert_same(out.numpy().view(np.uint64), ref, "host entry")
+    # keys and 1-bit words together, batch split into several chunks
+    big = workloads.random_sets(40_000, 1, 64, 1 << 20, seed=9)
+    ref2, _ = gpu_sketch(dmx, torch, ctx, big, 64, 6)
+    ipb = torch.from_numpy(big.indptr.astype(np.int64)).pin_memory()
+    ixb = torch.from_numpy(big.indices.view(np.int32)).pin_memory()
+    wb = torch.from_numpy(big.weights).pin_memory()
+    kh, wh = dmx.dm_sketch_host(ctx, ipb, ixb, wb, 64, 6, out_keys=torch.empty((big.n_sets, 64), dtype=torch.int64),
+                                b=1)
+    assert_same(kh.numpy().view(np.uint64), ref2, "host entry chunked keys")
+    dev_words = dmx.dm_sketch_bbit(ctx, *to_dev(torch, big), 64, 1, 6)
+    assert_same(wh.numpy().view(np.uint64), dev_words.cpu().numpy().view(np.uint64), "host entry words")
+
+
+@pytest.fixture(scope="module")
+def w1():
+    return workloads.workload1()
+
+
+def test_w1_full_size_sampled(dmx, torch_mod, ctx, oracle_mod, w1):
+    """W1 at full size (1,000,000 sets, k = 256, keys and 1-bit words in one call, as the
+    bench runs it); 3,000 rows spread over the batch checked against the oracle."""
+    torch = torch_mod
+    ip, ix, w = to_dev(torch, w1)
+    keys = torch.empty((w1.n_sets, 256), dtype=torch.int64, device="cuda")
+    words = dmx.dm_sketch_bbit(ctx, ip, ix, w, 256, 1, 1, out_keys=keys)
+    assert dmx.dm_sync_status(ctx, raise_on_error=False) == 0
+    rng = np.random.default_rng(0)
+    sel = np.unique(np.concatenate([rng.choice(w1.n_sets, 2990, replace=False),
+                                    np.arange(5), np.arange(w1.n_sets - 5, w1.n_sets)]))
+    sub = w1.rows(sel)
+    ew, ek = oracle_mod.sketch_bbit(sub.indptr, sub.indices, sub.weights, 256, 1, 1, keys=True,
+                                    threads=THREADS)
+    sel_t = torch.from_numpy(sel).cuda()
+    assert_same(keys[sel_t].cpu().numpy().view(np.uint64), ek, "W1 keys")
+    assert_same(words[sel_t].cpu().numpy().view(np.uint64), ew, "W1 1-bit")
+    assert (keys.cpu().numpy().view(np.uint64) != U64MAX).all()
+
+
+def test_w2_full_size_sampled(dmx, torch_mod, ctx, oracle_mod):
+    """W2 at full size (200,000 heavy-tailed sets, k = 1024); sampled rows, plus the ten
+    largest sets."""
+    torch = torch_mod
+    b = workloads.workload2()
+    ip, ix, w = to_dev(torch, b)
+    out = dmx.dm_sketch(ctx, ip, ix, w, 1024, 1)
+    assert dmx.dm_sync_status(ctx, raise_on_error=False) == 0
+    lens = np.diff(b.indptr)
+    rng = np.random.default_rng(1)
+    sel = np.unique(np.concatenate([rng.choice(b.n_sets, 600, replace=False), np.argsort(lens)[-10:]]))
+    sub = b.rows(sel)
+    exp = oracle_mod.sketch(sub.indptr, sub.indices, sub.weights, 1024, 1, threads=THREADS)
+    assert_same(out[torch.from_numpy(sel).cuda()].cpu().numpy().view(np.uint64), exp, "W2")
