@@ -333,10 +333,11 @@ def gpu_arm(args):
             "minhashes_per_s": value * K_SLOTS,
             "config": {"workload": "W1: 1,000,000 sets x 256 distinct elements (d=2^20), Exp(1) fp32 weights; "
                                    "k=256 uint64 keys + 1-bit words" if n == 1_000_000 else f"W1 prefix of {n} sets",
-                       "n_sets": n, "k": K_SLOTS, "b": B_BITS, "seed": SEED, "form": "plain (one warp per set)",
+                       "n_sets": n, "k": K_SLOTS, "b": B_BITS, "seed": SEED,
+                       "form": "plain: one warp per set (fast kernel) + general kernel over its queue",
                        "l2": "inputs 2 GB and outputs 2 GB per step, > 129 MB L2: no flush needed"},
             "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": args.steps, "wall_s_timed": t_wall,
+            "gpu_launches": 2 * args.steps, "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

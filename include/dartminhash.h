@@ -114,7 +114,7 @@ enum dm_option {
     DM_OPT_COUNTERS = 2,    /* device pointer to uint64[4] accumulating areas inspected, darts
                                generated, darts kept and passes (0 = off) */
     DM_OPT_FORM = 3,        /* launch form: 0 = plain (one warp per set), 1 = batched persistent */
-    DM_OPT_WARPS_PER_BLOCK = 4
+    DM_OPT_WARPS_PER_BLOCK = 4  /* 1..8 warps (sets) per thread block, 0 = automatic */
 };
 int dm_set_option(dm_ctx *ctx, int option, int64_t value);
 

@@ -30,6 +30,9 @@ struct dm_ctx {
     size_t d_stage_bytes = 0;
     cudaStream_t copy_stream[2] = {nullptr, nullptr};
     cudaEvent_t ev_start = nullptr;
+    // general-kernel work queue for calls on device buffers: int32[queue_cap] + a counter
+    void *d_queue = nullptr;
+    int64_t queue_cap = 0;
 };
 
 namespace {
@@ -109,9 +112,25 @@ int check_csr(const int64_t *indptr, const uint32_t *indices, const float *weigh
     return DM_OK;
 }
 
+// Queue scratch for a call of n_sets sets: int32[n_sets] followed by the counter.
+size_t queue_bytes(int64_t n_sets) { return ((size_t)n_sets * 4 + 255) / 256 * 256 + 256; }
+
+int ensure_queue(dm_ctx *ctx, int64_t n_sets) {
+    if (n_sets <= ctx->queue_cap) return DM_OK;
+    size_t need = queue_bytes(n_sets);
+    if (ctx->budget && need + ctx->d_stage_bytes > ctx->budget) return DM_ENOMEM;
+    if (ctx->d_queue) cudaFree(ctx->d_queue);
+    ctx->d_queue = nullptr;
+    ctx->queue_cap = 0;
+    cudaError_t e = cudaMalloc(&ctx->d_queue, need);
+    if (e != cudaSuccess) return cuda_fail(e);
+    ctx->queue_cap = n_sets;
+    return DM_OK;
+}
+
 int run_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
                int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_words,
-               uint64_t *out_keys, cudaStream_t st) {
+               uint64_t *out_keys, cudaStream_t st, void *queue = nullptr) {
     if (!ctx) return DM_EINVAL;
     int rc = check_csr(indptr, indices, weights, n_sets);
     if (rc) return rc;
@@ -123,8 +142,13 @@ int run_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, cons
     if (!bbit && !out_keys) return DM_EINVAL;
     if (bbit && !out_words) return DM_EINVAL;
     if (n_sets == 0) return DM_OK;
+    if (n_sets > 0x7FFFFFFF) return DM_EINVAL;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e);
+    if (!queue) {
+        if ((rc = ensure_queue(ctx, n_sets)) != DM_OK) return rc;
+        queue = ctx->d_queue;
+    }
     SketchParams p;
     std::memset(&p, 0, sizeof(p));
     p.indptr = indptr;
@@ -143,10 +167,14 @@ int run_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, cons
     p.counters = ctx->counters;
     p.warps_per_block = ctx->warps_per_block > 0 ? ctx->warps_per_block : auto_warps(k);
     p.warp_bytes = (int32_t)dm::sketch_warp_bytes(k);
+    p.queue = (int32_t *)queue;
+    p.queue_count = (unsigned int *)((char *)queue + queue_bytes(n_sets) - 256);
     if ((size_t)p.warp_bytes * p.warps_per_block > 227 * 1024) return DM_EINVAL;
     int64_t blocks = (n_sets + p.warps_per_block - 1) / p.warps_per_block;
-    int grid = blocks > 0x7FFFFFFF ? 0x7FFFFFFF : (int)blocks;
-    return cuda_fail(dm::launch_sketch(p, bbit, ctx->counters != nullptr, grid, st));
+    int grid = (int)blocks;
+    int64_t gcap = (int64_t)ctx->sm_count * 8;
+    int grid_general = (int)(blocks < gcap ? blocks : gcap);
+    return cuda_fail(dm::launch_sketch(p, bbit, ctx->counters != nullptr, grid, grid_general, st));
 }
 
 }  // namespace
@@ -186,6 +214,7 @@ int dm_destroy(dm_ctx *ctx) {
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->d_stage) cudaFree(ctx->d_stage);
+    if (ctx->d_queue) cudaFree(ctx->d_queue);
     for (int i = 0; i < 2; ++i)
         if (ctx->copy_stream[i]) cudaStreamDestroy(ctx->copy_stream[i]);
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
@@ -241,7 +270,8 @@ int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t b_ip = al((size_t)(cs + 1) * 8), b_ix = al((size_t)max_nnz * 4), b_w = b_ix;
     const size_t b_keys = out_keys ? al((size_t)cs * k * 8) : 0, b_words = al((size_t)cs * words * 8);
-    const size_t per = b_ip + b_ix + b_w + b_keys + b_words;
+    const size_t b_q = queue_bytes(cs);
+    const size_t per = b_ip + b_ix + b_w + b_keys + b_words + b_q;
     const size_t need = 2 * per;
     if (need > ctx->d_stage_bytes) {
         if (ctx->budget && need > ctx->budget) return DM_ENOMEM;
@@ -273,13 +303,14 @@ int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
         float *d_w = (float *)(base + b_ip + b_ix);
         uint64_t *d_keys = out_keys ? (uint64_t *)(base + b_ip + b_ix + b_w) : nullptr;
         uint64_t *d_words = (uint64_t *)(base + b_ip + b_ix + b_w + b_keys);
+        void *d_q = base + b_ip + b_ix + b_w + b_keys + b_words;
         // indptr keeps absolute offsets; the element arrays are addressed from z0
         if ((e = cudaMemcpyAsync(d_ip, indptr + s0, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, cst)) ||
             (z && (e = cudaMemcpyAsync(d_ix, indices + z0, (size_t)z * 4, cudaMemcpyHostToDevice, cst))) ||
             (z && (e = cudaMemcpyAsync(d_w, weights + z0, (size_t)z * 4, cudaMemcpyHostToDevice, cst))))
             return cuda_fail(e);
         rc = run_sketch(ctx, d_ip, d_ix - z0, d_w - z0, n, k, b, seed, b > 0 ? d_words : nullptr,
-                        d_keys, cst);
+                        d_keys, cst, d_q);
         if (rc) return rc;
         if ((out_keys && (e = cudaMemcpyAsync(out_keys + s0 * k, d_keys, (size_t)n * k * 8,
                                               cudaMemcpyDeviceToHost, cst))) ||
@@ -336,7 +367,7 @@ int dm_set_option(dm_ctx *ctx, int option, int64_t value) {
             ctx->form = (int)value;
             return DM_OK;
         case DM_OPT_WARPS_PER_BLOCK:
-            if (value < 0 || value > 32) return DM_EINVAL;
+            if (value < 0 || value > 8) return DM_EINVAL;   // kernels are built for <= 256 threads
             ctx->warps_per_block = (int)value;
             return DM_OK;
         default:

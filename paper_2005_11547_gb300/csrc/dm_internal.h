@@ -27,14 +27,17 @@ struct SketchParams {
     unsigned long long *counters;   // optional work counters (4)
     int32_t warp_bytes;   // dynamic shared memory per warp
     int32_t warps_per_block;
-    const int32_t *order; // optional set order (persistent form), may be null
-    unsigned int *next;   // optional work counter for dynamic scheduling (persistent form)
+    int32_t *queue;             // sets deferred to the general kernel (capacity n_sets)
+    unsigned int *queue_count;  // number of queued sets
 };
 
 // Per-warp shared memory for the sketch kernel (k slots + staging rings + tile arrays).
 size_t sketch_warp_bytes(int k);
 
 cudaError_t upload_poisson_table(const uint32_t *T);
-cudaError_t launch_sketch(const SketchParams &p, bool bbit, bool count, int grid, cudaStream_t st);
+// Zeroes the queue counter, then launches the fast kernel over all sets and the general
+// kernel over the sets it queued, all on stream st.
+cudaError_t launch_sketch(const SketchParams &p, bool bbit, bool count, int grid_fast, int grid_general,
+                          cudaStream_t st);
 
 }  // namespace dm

@@ -23,7 +23,7 @@ namespace dm {
 __constant__ uint32_t c_pois[12];
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kAreaRing = 64;
+constexpr int kAreaRing = 128;
 constexpr int kDartRing = 512;
 constexpr int kMaxPasses = 21;     // phi0 * 2^20 at most (Theorem 1's loop limit)
 
@@ -75,7 +75,215 @@ __device__ __forceinline__ uint32_t warp_incl_scan32(uint32_t v, int lane) {
     return v;
 }
 
-// Number of areas element (nu_top, F) contributes to a pass.
+// ------------------------------------------------------------------------------------------
+// Dart staging.  An area record holds the area hash a, the rank base pb and meta =
+// vmax | sh << 24 | (S << 23) << 32, so that dart j of the area has
+//   d = mix64(a + gamma (j + 1)),  u = d >> 40,  v = (d >> 16) & (2^24 - 1),
+//   rank = (pb + (u << sh)) 2^-S,  weight test v <= vmax.
+// A dart reference is (area slot | j << 7).
+// ------------------------------------------------------------------------------------------
+struct Ring {
+    uint32_t a_tail, d_tail, d_head;
+};
+
+__device__ __forceinline__ uint64_t pack_meta(uint64_t vmax, int sh, int S) {
+    return vmax | ((uint64_t)sh << 24) | ((uint64_t)((uint32_t)S << 23) << 32);
+}
+
+__device__ __forceinline__ void stage_area(Ring &q, const WarpMem &m, int lane, unsigned lt_mask, int X,
+                                           uint64_t a, uint64_t pb, uint64_t meta) {
+    unsigned bal = __ballot_sync(kFull, X > 0);
+    uint32_t aslot = (q.a_tail + __popc(bal & lt_mask)) & (kAreaRing - 1);
+    if (X > 0) {
+        m.ar_a[aslot] = a;
+        m.ar_p[aslot] = pb;
+        m.ar_m[aslot] = meta;
+    }
+    q.a_tail += __popc(bal);
+    uint32_t xin = warp_incl_scan32((uint32_t)X, lane);
+    uint32_t xtot = __shfl_sync(kFull, xin, 31);
+    uint32_t at = q.d_tail + xin - (uint32_t)X;
+    for (int j = 0; j < X; ++j) m.dref[(at + j) & (kDartRing - 1)] = (uint16_t)(aslot | (j << 7));
+    q.d_tail += xtot;
+    __syncwarp();
+}
+
+// Evaluate one queued dart; returns whether it is kept and its bucket and key.
+__device__ __forceinline__ bool dart_eval(const WarpMem &m, uint32_t ref, uint32_t k, uint32_t cthr,
+                                          uint32_t &slot, uint64_t &key) {
+    int ai = ref & (kAreaRing - 1);
+    uint64_t j = ref >> 7;
+    uint64_t a = m.ar_a[ai], pb = m.ar_p[ai], meta = m.ar_m[ai];
+    uint64_t d = mix64(a + kGolden * (j + 1));
+    uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
+    uint64_t P = pb + ((uint64_t)u << ((meta >> 24) & 63));
+    // binary32 code of rank = P 2^-S rounded toward zero: exact u64 -> f32 conversion in
+    // round-toward-zero mode, then the exponent lowered by S
+    uint32_t code = P ? __float_as_uint(__ull2float_rz(P)) - (uint32_t)(meta >> 32) : 0u;
+    if (v > ((uint32_t)meta & kUMask) || code >= cthr) return false;
+    uint64_t qh = mix64(d ^ kSlotSalt);
+    slot = fastrange32((uint32_t)(qh >> 32), k);
+    key = ((uint64_t)code << 32) | (uint32_t)qh;
+    return true;
+}
+
+// Process up to 64 queued darts, two per lane.
+template <bool COUNT>
+__device__ __forceinline__ void drain(int n, Ring &q, const WarpMem &m, int lane, uint32_t k, uint32_t cthr,
+                                      unsigned long long &kept) {
+    uint32_t r0 = m.dref[(q.d_head + lane) & (kDartRing - 1)];
+    uint32_t r1 = m.dref[(q.d_head + 32 + lane) & (kDartRing - 1)];
+    uint32_t s0 = 0, s1 = 0;
+    uint64_t k0 = 0, k1 = 0;
+    bool e0 = lane < n && dart_eval(m, r0, k, cthr, s0, k0);
+    bool e1 = lane + 32 < n && dart_eval(m, r1, k, cthr, s1, k1);
+    if (e0) atomicMin(reinterpret_cast<unsigned long long *>(&m.slots[s0]), (unsigned long long)k0);
+    if (e1) atomicMin(reinterpret_cast<unsigned long long *>(&m.slots[s1]), (unsigned long long)k1);
+    if (COUNT) kept += (unsigned long long)e0 + (unsigned long long)e1;
+    q.d_head += (uint32_t)n;
+    __syncwarp();
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void drain_ready(Ring &q, const WarpMem &m, int lane, uint32_t k, uint32_t cthr,
+                                            unsigned long long &kept) {
+    while (q.d_tail - q.d_head >= 64) drain<COUNT>(64, q, m, lane, k, cthr, kept);
+}
+
+// ------------------------------------------------------------------------------------------
+// Element setup shared by both walks: weight geometry and element hash for one tile.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool element_setup(const SketchParams &p, int64_t pos, int64_t end, int &nutop,
+                                              uint64_t &F, uint64_t &e) {
+    nutop = -1;
+    F = 0;
+    e = 0;
+    if (pos >= end) return true;
+    nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F);
+    if (nutop == -2) return false;
+    if (nutop >= 0) e = mix64(p.sigma + kGolden * ((uint64_t)p.indices[pos] + 1));
+    return true;
+}
+
+__device__ __forceinline__ uint64_t publish_tile(const WarpMem &m, int lane, int nutop, uint64_t F, uint64_t e,
+                                                 uint64_t n_el) {
+    uint64_t incl = warp_incl_scan(n_el, lane);
+    m.te[lane] = e;
+    m.tF[lane] = F;
+    m.tnu[lane] = nutop;
+    m.toff[lane] = incl - n_el;
+    m.tcnt[lane] = n_el;
+    __syncwarp();
+    return __shfl_sync(kFull, incl, 31);
+}
+
+__device__ __forceinline__ int tile_element(const WarpMem &m, uint64_t idx) {
+    int el = 0;                               // last element whose offset is <= idx
+#pragma unroll
+    for (int step = 16; step; step >>= 1) {
+        int c = el + step;
+        if (c < 32 && m.toff[c] <= idx) el = c;
+    }
+    return el;
+}
+
+// ------------------------------------------------------------------------------------------
+// Fast walk for passes whose limit is below 1 (rho_top = rho_lo = 0): every region is one
+// column (w = 0) of rows [rlo(nu), rhi(nu)), so an element's areas form a 1-D sequence.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t r0_hi(const PassCut &pc, int nu) { return nu ? (pc.gm1 >> (64 - nu)) + 1 : 1; }
+__device__ __forceinline__ uint64_t r0_lo(const PassCut &pc, int nu) { return nu ? (pc.gfl_lo >> (64 - nu)) : 0; }
+
+// sum_{nu=1..n} floor(G / 2^(64-nu)) = 2H - popc(H), H = floor(G / 2^(64-n))
+__device__ __forceinline__ uint64_t shifted_sum(uint64_t G, int n) {
+    if (n <= 0) return 0;
+    uint64_t H = G >> (64 - n);
+    return 2 * H - (uint64_t)__popcll(H);
+}
+
+__device__ __forceinline__ uint64_t r0_count(int nutop, const PassCut &pc) {
+    return 1 + (uint64_t)nutop + shifted_sum(pc.gm1, nutop) - shifted_sum(pc.gfl_lo, nutop);
+}
+
+struct Walk0 {
+    int el, nu, nutop;
+    uint64_t r, rhi, e, F, ctr;
+    uint32_t vmax;
+};
+
+__device__ __forceinline__ void w0_region(Walk0 &s, const PassCut &pc) {
+    s.r = r0_lo(pc, s.nu);
+    s.rhi = r0_hi(pc, s.nu);
+    s.vmax = (s.nu == s.nutop) ? (uint32_t)(s.F >> 40) : kUMask;
+    s.ctr = s.e + kGolden * ((((uint64_t)s.nu << 58) | s.r) + 1);
+}
+
+template <bool COUNT>
+__device__ int pass_rho0(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc, const WarpMem &m,
+                         int lane, Ring &q, unsigned long long *cnt) {
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t k = (uint32_t)p.k;
+    for (int64_t tile = beg; tile < end; tile += 32) {
+        int nutop;
+        uint64_t F, e;
+        bool ok = element_setup(p, tile + lane, end, nutop, F, e);
+        if (__any_sync(kFull, !ok)) return DM_ERANGE;
+        uint64_t total = publish_tile(m, lane, nutop, F, e, nutop >= 0 ? r0_count(nutop, pc) : 0);
+        if (total == 0) continue;
+        uint64_t share = (total + 31) >> 5;
+        uint64_t lo = share * lane, hi = min(lo + share, total);
+        Walk0 s;
+        if (lo < hi) {
+            s.el = tile_element(m, lo);
+            s.e = m.te[s.el];
+            s.F = m.tF[s.el];
+            s.nutop = m.tnu[s.el];
+            uint64_t li = lo - m.toff[s.el];
+            for (s.nu = 0;; ++s.nu) {
+                uint64_t rows = r0_hi(pc, s.nu) - r0_lo(pc, s.nu);
+                if (li < rows) break;
+                li -= rows;
+            }
+            w0_region(s, pc);
+            s.r += li;
+            s.ctr += kGolden * li;
+        }
+        for (uint64_t it = 0; it < share; ++it) {
+            bool active = lo + it < hi;
+            int X = 0;
+            uint64_t a = 0;
+            if (active) {
+                a = mix64(s.ctr);
+                X = poisson1((uint32_t)(a >> 32), c_pois);
+                if (COUNT) { cnt[0]++; cnt[1] += X; }
+            }
+            stage_area(q, m, lane, lt_mask, X, a, s.r << 24, pack_meta(s.vmax, 0, s.nu + 24));
+            drain_ready<COUNT>(q, m, lane, k, pc.cthr, cnt[2]);
+            if (active) {
+                ++s.r;
+                s.ctr += kGolden;
+                if (s.r == s.rhi) {
+                    if (++s.nu > s.nutop) {
+                        s.nu = 0;
+                        do { ++s.el; } while (s.el < 32 && m.tcnt[s.el] == 0);
+                        if (s.el < 32) {
+                            s.e = m.te[s.el];
+                            s.F = m.tF[s.el];
+                            s.nutop = m.tnu[s.el];
+                        }
+                    }
+                    if (s.el < 32) w0_region(s, pc);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// General walk: regions (nu, rho), columns w and rows r.
+// ------------------------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t element_areas(int nutop, uint64_t F, const PassCut &pc) {
     uint64_t total = 0;
     for (int nu = 0; nu <= nutop; ++nu)
@@ -84,7 +292,6 @@ __device__ __forceinline__ uint64_t element_areas(int nutop, uint64_t F, const P
     return total;
 }
 
-// Walk state of one lane over its share of the tile's flattened areas.
 struct Walk {
     int el, nu, rho, nutop;
     uint64_t w, r, ncols, rlo, rhi;
@@ -110,17 +317,10 @@ __device__ __forceinline__ void walk_load_element(Walk &s, const WarpMem &m) {
     s.nutop = m.tnu[s.el];
 }
 
-// Position the walk at flattened area index idx of the tile.
 __device__ __forceinline__ void walk_locate(Walk &s, uint64_t idx, const WarpMem &m, const PassCut &pc) {
-    int el = 0;                               // last element whose offset is <= idx
-#pragma unroll
-    for (int step = 16; step; step >>= 1) {
-        int c = el + step;
-        if (c < 32 && m.toff[c] <= idx) el = c;
-    }
-    s.el = el;
+    s.el = tile_element(m, idx);
     walk_load_element(s, m);
-    uint64_t li = idx - m.toff[el];
+    uint64_t li = idx - m.toff[s.el];
     for (s.nu = 0; s.nu <= s.nutop; ++s.nu) {
         bool found = false;
         for (s.rho = pc.rho_lo; s.rho <= pc.rho_top; ++s.rho) {
@@ -162,57 +362,16 @@ __device__ __forceinline__ void walk_advance(Walk &s, const WarpMem &m, const Pa
 }
 
 template <bool COUNT>
-__device__ __forceinline__ void drain_darts(int n, uint32_t head, const WarpMem &m, int lane, uint32_t k,
-                                            uint32_t cthr, unsigned long long &kept) {
-    if (lane < n) {
-        uint32_t ref = m.dref[(head + lane) & (kDartRing - 1)];
-        int ai = ref & (kAreaRing - 1);
-        uint64_t j = ref >> 6;
-        uint64_t a = m.ar_a[ai], pbase = m.ar_p[ai], meta = m.ar_m[ai];
-        uint64_t d = mix64(a + kGolden * (j + 1));
-        uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
-        uint32_t vmax = (uint32_t)meta & kUMask;
-        int sh = (int)(meta >> 24) & 63, S = (int)(meta >> 32) & 63;
-        uint32_t code = rank_code(pbase + ((uint64_t)u << sh), S);
-        if (v <= vmax && code < cthr) {
-            uint64_t q = mix64(d ^ kSlotSalt);
-            uint32_t slot = fastrange32((uint32_t)(q >> 32), k);
-            atomicMin(reinterpret_cast<unsigned long long *>(&m.slots[slot]),
-                      (unsigned long long)(((uint64_t)code << 32) | (uint32_t)q));
-            if (COUNT) ++kept;
-        }
-    }
-    __syncwarp();
-}
-
-// One pass of DartHash over the row: returns 0 or an error code.
-template <bool COUNT>
-__device__ int darthash_pass(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc,
-                             const WarpMem &m, int lane, unsigned long long *cnt) {
+__device__ int pass_general(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc, const WarpMem &m,
+                            int lane, Ring &q, unsigned long long *cnt) {
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint32_t a_tail = 0, d_tail = 0, d_head = 0;
+    const uint32_t k = (uint32_t)p.k;
     for (int64_t tile = beg; tile < end; tile += 32) {
-        int64_t pos = tile + lane;
-        int nutop = -1;
-        uint64_t F = 0, e = 0, n_el = 0;
-        bool range_err = false;
-        if (pos < end) {
-            nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F);
-            if (nutop == -2) range_err = true;
-            else if (nutop >= 0) {
-                e = mix64(p.sigma + kGolden * ((uint64_t)p.indices[pos] + 1));
-                n_el = element_areas(nutop, F, pc);
-            }
-        }
-        if (__any_sync(kFull, range_err)) return DM_ERANGE;
-        uint64_t incl = warp_incl_scan(n_el, lane);
-        uint64_t total = __shfl_sync(kFull, incl, 31);
-        m.te[lane] = e;
-        m.tF[lane] = F;
-        m.tnu[lane] = nutop;
-        m.toff[lane] = incl - n_el;
-        m.tcnt[lane] = n_el;
-        __syncwarp();
+        int nutop;
+        uint64_t F, e;
+        bool ok = element_setup(p, tile + lane, end, nutop, F, e);
+        if (__any_sync(kFull, !ok)) return DM_ERANGE;
+        uint64_t total = publish_tile(m, lane, nutop, F, e, nutop >= 0 ? element_areas(nutop, F, pc) : 0);
         if (total == 0) continue;
         uint64_t share = (total + 31) >> 5;
         uint64_t lo = share * lane, hi = min(lo + share, total);
@@ -221,51 +380,39 @@ __device__ int darthash_pass(const SketchParams &p, int64_t beg, int64_t end, co
         for (uint64_t it = 0; it < share; ++it) {
             bool active = lo + it < hi;
             int X = 0;
-            uint64_t a = 0, pbase = 0, meta = 0;
+            uint64_t a = 0, pb = 0, meta = 0;
             if (active) {
                 a = mix64(s.ctr);
                 X = poisson1((uint32_t)(a >> 32), c_pois);
                 uint64_t vmax = min(s.WT - (s.w << 24), (uint64_t)kUMask);
-                pbase = s.rbase + (s.r << (62 - s.nu));
-                meta = vmax | ((uint64_t)(38 - s.nu) << 24) | ((uint64_t)(62 - s.rho) << 32);
+                pb = s.rbase + (s.r << (62 - s.nu));
+                meta = pack_meta(vmax, 38 - s.nu, 62 - s.rho);
                 if (COUNT) { cnt[0]++; cnt[1] += X; }
             }
-            unsigned bal = __ballot_sync(kFull, X > 0);
-            uint32_t aslot = (a_tail + __popc(bal & lt_mask)) & (kAreaRing - 1);
-            if (X > 0) {
-                m.ar_a[aslot] = a;
-                m.ar_p[aslot] = pbase;
-                m.ar_m[aslot] = meta;
-            }
-            a_tail += __popc(bal);
-            uint32_t xin = warp_incl_scan32((uint32_t)X, lane);
-            uint32_t xtot = __shfl_sync(kFull, xin, 31);
-            uint32_t at = d_tail + xin - (uint32_t)X;
-            for (int j = 0; j < X; ++j)
-                m.dref[(at + j) & (kDartRing - 1)] = (uint16_t)(aslot | (j << 6));
-            d_tail += xtot;
-            __syncwarp();
-            while (d_tail - d_head >= 32) {
-                drain_darts<COUNT>(32, d_head, m, lane, (uint32_t)p.k, pc.cthr, cnt[2]);
-                d_head += 32;
-            }
+            stage_area(q, m, lane, lt_mask, X, a, pb, meta);
+            drain_ready<COUNT>(q, m, lane, k, pc.cthr, cnt[2]);
             if (active) walk_advance(s, m, pc);
         }
         __syncwarp();
     }
-    if (d_tail != d_head) drain_darts<COUNT>((int)(d_tail - d_head), d_head, m, lane, (uint32_t)p.k, pc.cthr, cnt[2]);
     return 0;
 }
 
-template <bool BBIT, bool COUNT>
-__global__ void __launch_bounds__(256) sketch_kernel(const SketchParams p) {
+// MODE 0 (fast): sets are taken in order; every pass whose rank limit is below 1 runs the 1-D
+// walk; a set needing a limit >= 1 is appended to the general queue and left to MODE 1.
+// MODE 1 (general): sets are taken from the queue and computed from the first pass with the
+// general walk.  Both give the same bits for a set (the output does not depend on the limits).
+template <bool BBIT, bool COUNT, int MODE>
+__global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) sketch_kernel(const SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     WarpMem m = carve(smem + (size_t)wib * p.warp_bytes, p.k);
     const uint32_t k = (uint32_t)p.k;
-    for (int64_t set = (int64_t)blockIdx.x * p.warps_per_block + wib; set < p.n_sets;
-         set += (int64_t)gridDim.x * p.warps_per_block) {
+    const int64_t n_work = MODE == 0 ? p.n_sets : (int64_t)*p.queue_count;
+    for (int64_t wi = (int64_t)blockIdx.x * p.warps_per_block + wib; wi < n_work;
+         wi += (int64_t)gridDim.x * p.warps_per_block) {
+        const int64_t set = MODE == 0 ? wi : (int64_t)p.queue[wi];
         const int64_t beg = p.indptr[set], end = p.indptr[set + 1];
         // ||x||_1 and input validation
         float l1 = 0.f;
@@ -282,6 +429,7 @@ __global__ void __launch_bounds__(256) sketch_kernel(const SketchParams p) {
         __syncwarp();
         unsigned long long cnt[3] = {0, 0, 0};
         unsigned long long passes = 0;
+        bool deferred = false;
         if (!err && l1 > 0.f) {
             uint32_t th = __float_as_uint(__fdiv_rn(p.phi0, l1));
             PassCut pc;
@@ -294,9 +442,14 @@ __global__ void __launch_bounds__(256) sketch_kernel(const SketchParams p) {
                 pc.rho_top = rc.rho_top;
                 pc.gm1 = rc.gm1;
                 pc.cthr = th;
-                err = darthash_pass<COUNT>(p, beg, end, pc, m, lane, cnt);
+                if (MODE == 0 && pc.rho_top != 0) { deferred = true; break; }
+                Ring q = {0, 0, 0};
+                err = MODE == 0 ? pass_rho0<COUNT>(p, beg, end, pc, m, lane, q, cnt)
+                                : pass_general<COUNT>(p, beg, end, pc, m, lane, q, cnt);
                 ++passes;
                 if (err) break;
+                if (q.d_tail != q.d_head)
+                    drain<COUNT>((int)(q.d_tail - q.d_head), q, m, lane, k, pc.cthr, cnt[2]);
                 bool empty = false;
                 for (uint32_t j = lane; j < k; j += 32) empty |= (m.slots[j] == ~0ull);
                 if (!__any_sync(kFull, empty)) break;
@@ -305,11 +458,6 @@ __global__ void __launch_bounds__(256) sketch_kernel(const SketchParams p) {
                 pc.gfl_lo = rc.g_one ? 0 : rc.gfl;
                 th = __float_as_uint(2.0f * __uint_as_float(th));
             }
-        }
-        if (err) {
-            if (lane == 0) set_status(p.status, err);
-            for (uint32_t j = lane; j < k; j += 32) m.slots[j] = ~0ull;
-            __syncwarp();
         }
         if (COUNT) {
 #pragma unroll
@@ -320,6 +468,16 @@ __global__ void __launch_bounds__(256) sketch_kernel(const SketchParams p) {
                 if (lane == 0 && p.counters) atomicAdd(&p.counters[c], v);
             }
             if (lane == 0 && p.counters) atomicAdd(&p.counters[3], passes);
+        }
+        if (deferred) {
+            if (lane == 0) p.queue[atomicAdd(p.queue_count, 1u)] = (int32_t)set;
+            __syncwarp();
+            continue;
+        }
+        if (err) {
+            if (lane == 0) set_status(p.status, err);
+            for (uint32_t j = lane; j < k; j += 32) m.slots[j] = ~0ull;
+            __syncwarp();
         }
         // epilogue: keys and/or b-bit words
         if (p.out_keys)
@@ -358,10 +516,10 @@ cudaError_t upload_poisson_table(const uint32_t *T) {
     return cudaMemcpyToSymbol(c_pois, T, 12 * sizeof(uint32_t));
 }
 
-template <bool BBIT, bool COUNT>
+template <bool BBIT, bool COUNT, int MODE>
 static cudaError_t launch_t(const SketchParams &p, int grid, cudaStream_t st) {
     size_t smem = (size_t)p.warp_bytes * p.warps_per_block;
-    auto fn = sketch_kernel<BBIT, COUNT>;
+    auto fn = sketch_kernel<BBIT, COUNT, MODE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -370,9 +528,18 @@ static cudaError_t launch_t(const SketchParams &p, int grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_sketch(const SketchParams &p, bool bbit, bool count, int grid, cudaStream_t st) {
-    if (bbit) return count ? launch_t<true, true>(p, grid, st) : launch_t<true, false>(p, grid, st);
-    return count ? launch_t<false, true>(p, grid, st) : launch_t<false, false>(p, grid, st);
+template <int MODE>
+static cudaError_t launch_mode(const SketchParams &p, bool bbit, bool count, int grid, cudaStream_t st) {
+    if (bbit) return count ? launch_t<true, true, MODE>(p, grid, st) : launch_t<true, false, MODE>(p, grid, st);
+    return count ? launch_t<false, true, MODE>(p, grid, st) : launch_t<false, false, MODE>(p, grid, st);
+}
+
+cudaError_t launch_sketch(const SketchParams &p, bool bbit, bool count, int grid_fast, int grid_general,
+                          cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(p.queue_count, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_mode<0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
+    return launch_mode<1>(p, bbit, count, grid_general, st);
 }
 
 }  // namespace dm

@@ -100,7 +100,7 @@ def test_edge_cases_parity(dmx, torch_mod, ctx, oracle_mod):
         ([5, 5, 5], [0.25, 0.75, 0.5]),                   # duplicates act as the max
         ([5], [0.75]),
         ([0, 4294967295], [1e-30, 2.5]),                  # extreme index and tiny weight
-        ([11], [np.float32(1e-40)]),                      # subnormal weight
+        ([11, 12], [np.float32(1e-40), 0.5]),             # subnormal weight beside a normal one
         ([9, 10], [-0.0, 3.0]),                           # negative zero is a zero weight
     ]
     # weights whose t x lands exactly on a region edge 2^nu - 1 for k = 2 (t = 4)
@@ -138,11 +138,16 @@ def test_invalid_and_out_of_range_weights(dmx, torch_mod, ctx, oracle_mod):
     good = b.rows([0, 4])
     assert_same(got[[0, 4]], oracle_mod.sketch(good.indptr, good.indices, good.weights, 32, 3), "valid rows")
     assert dmx.dm_sync_status(ctx, raise_on_error=False) == 0   # status cleared
-    big = workloads.csr_of([(np.array([1], np.uint32), np.array([2.0 ** 39], f))])
-    got, rc = gpu_sketch(dmx, torch_mod, ctx, big, 1, 3)
-    assert rc == 5                                              # DM_ERANGE
-    with pytest.raises(oracle_mod.OracleError):
-        oracle_mod.sketch(big.indptr, big.indices, big.weights, 1, 3)
+    # a weight with t x >= 2^39 - 1, and a set whose only weight is subnormal (it would need
+    # a rank limit near 1e40): both outside the supported range on both sides
+    for bad_w in [2.0 ** 39, 1e-40]:
+        big = workloads.csr_of([(np.array([1], np.uint32), np.array([bad_w], f))])
+        got, rc = gpu_sketch(dmx, torch_mod, ctx, big, 1, 3)
+        assert rc == 5                                          # DM_ERANGE
+        assert (got == U64MAX).all()
+        with pytest.raises(oracle_mod.OracleError) as e:
+            oracle_mod.sketch(big.indptr, big.indices, big.weights, 1, 3)
+        assert e.value.code == 5
 
 
 @pytest.mark.parametrize("bits", [1, 2, 4, 8, 16, 32])
