@@ -169,11 +169,15 @@ int run_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, cons
     p.warp_bytes = (int32_t)dm::sketch_warp_bytes(k);
     p.queue = (int32_t *)queue;
     p.queue_count = (unsigned int *)((char *)queue + queue_bytes(n_sets) - 256);
-    if ((size_t)p.warp_bytes * p.warps_per_block > 227 * 1024) return DM_EINVAL;
+    p.work_next = p.queue_count + 1;
+    size_t smem = (size_t)p.warp_bytes * p.warps_per_block;
+    if (smem > 227 * 1024) return DM_EINVAL;
+    // persistent grids: as many blocks as can be resident, never more than there are sets
     int64_t blocks = (n_sets + p.warps_per_block - 1) / p.warps_per_block;
-    int grid = (int)blocks;
-    int64_t gcap = (int64_t)ctx->sm_count * 8;
-    int grid_general = (int)(blocks < gcap ? blocks : gcap);
+    int64_t cap0 = (int64_t)ctx->sm_count * dm::sketch_blocks_per_sm(0, bbit, p.warps_per_block, smem);
+    int64_t cap1 = (int64_t)ctx->sm_count * dm::sketch_blocks_per_sm(1, bbit, p.warps_per_block, smem);
+    int grid = (int)(blocks < cap0 ? blocks : cap0);
+    int grid_general = (int)(blocks < cap1 ? blocks : cap1);
     return cuda_fail(dm::launch_sketch(p, bbit, ctx->counters != nullptr, grid, grid_general, st));
 }
 

@@ -28,14 +28,18 @@ struct SketchParams {
     int32_t warp_bytes;   // dynamic shared memory per warp
     int32_t warps_per_block;
     int32_t *queue;             // sets deferred to the general kernel (capacity n_sets)
-    unsigned int *queue_count;  // number of queued sets
+    unsigned int *queue_count;  // number of queued sets; followed by the two work counters
+    unsigned int *work_next;    // = queue_count + 1: next work item of the fast / general kernel
 };
 
 // Per-warp shared memory for the sketch kernel (k slots + staging rings + tile arrays).
 size_t sketch_warp_bytes(int k);
 
 cudaError_t upload_poisson_table(const uint32_t *T);
-// Zeroes the queue counter, then launches the fast kernel over all sets and the general
+// Resident blocks per SM of the fast (mode 0) or general (mode 1) kernel.
+int sketch_blocks_per_sm(int mode, bool bbit, int warps_per_block, size_t smem);
+
+// Zeroes the queue and work counters, then launches the fast kernel over all sets and the general
 // kernel over the sets it queued, all on stream st.
 cudaError_t launch_sketch(const SketchParams &p, bool bbit, bool count, int grid_fast, int grid_general,
                           cudaStream_t st);

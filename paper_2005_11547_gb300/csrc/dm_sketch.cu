@@ -6,14 +6,16 @@
 // empty, double theta and enumerate only the areas that reach above the previous limit.
 //
 // GPU mapping
+//  * Persistent warps claim sets from a global counter, so a set that needs a second pass
+//    never holds idle warps of its block.
 //  * Elements are taken 32 at a time (a tile, one lane each).  Each lane computes its
 //    element's area count for this pass in closed form; a warp scan flattens the tile's
 //    areas and every lane walks a contiguous, equal share of them, so lanes stay busy no
 //    matter how unequal the element weights are.
-//  * Each area costs one hash (its Poisson count).  Areas with darts are appended to a
-//    64-entry area ring and their darts (area slot, j) to a 512-entry dart ring in shared
-//    memory; whenever 32 darts are queued the warp processes them together, one per lane,
-//    so the variable Poisson counts never diverge the warp.
+//  * Each area costs one hash (its Poisson count X).  A lane then emits the area's darts one
+//    per iteration into a 128-entry shared-memory dart queue (position = rank of the lane
+//    in a ballot), and whenever 32 or more darts are queued the warp evaluates them
+//    together, so the variable Poisson counts never diverge the warp.
 //  * A kept dart's key is atomically min-ed into the set's k buckets in shared memory.
 #include "dm_device.cuh"
 #include "dm_internal.h"
@@ -23,37 +25,35 @@ namespace dm {
 __constant__ uint32_t c_pois[12];
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kAreaRing = 128;
-constexpr int kDartRing = 512;
+constexpr int kQueue = 128;        // dart records per warp
 constexpr int kMaxPasses = 21;     // phi0 * 2^20 at most (Theorem 1's loop limit)
+constexpr int kDefer = -1;         // a pass the fast kernel leaves to the general kernel
 
 size_t sketch_warp_bytes(int k) {
     size_t b = (size_t)k * 8          // bucket minima
-             + 3 * kAreaRing * 8      // area ring: hash, rank base, meta
-             + 4 * 32 * 8             // tile: element hash, F, offset, count
+             + 2 * kQueue * 8         // dart queue: dart counter, rank base | vmax
+             + 3 * 32 * 8             // tile: element hash, F, offset
              + 32 * 4                 // tile: nu_top
-             + kDartRing * 2;         // dart ring
+             + kQueue * 2;            // dart queue: shift and scale of the rank
     return (b + 15) & ~(size_t)15;
 }
 
 struct WarpMem {
-    uint64_t *slots, *ar_a, *ar_p, *ar_m, *te, *tF, *toff, *tcnt;
+    uint64_t *slots, *dq_c, *dq_p, *te, *tF, *toff;
     int *tnu;
-    uint16_t *dref;
+    uint16_t *dq_m;
 };
 
 __device__ __forceinline__ WarpMem carve(unsigned char *base, int k) {
     WarpMem m;
     m.slots = reinterpret_cast<uint64_t *>(base);
-    m.ar_a = m.slots + k;
-    m.ar_p = m.ar_a + kAreaRing;
-    m.ar_m = m.ar_p + kAreaRing;
-    m.te = m.ar_m + kAreaRing;
+    m.dq_c = m.slots + k;
+    m.dq_p = m.dq_c + kQueue;
+    m.te = m.dq_p + kQueue;
     m.tF = m.te + 32;
     m.toff = m.tF + 32;
-    m.tcnt = m.toff + 32;
-    m.tnu = reinterpret_cast<int *>(m.tcnt + 32);
-    m.dref = reinterpret_cast<uint16_t *>(m.tnu + 32);
+    m.tnu = reinterpret_cast<int *>(m.toff + 32);
+    m.dq_m = reinterpret_cast<uint16_t *>(m.tnu + 32);
     return m;
 }
 
@@ -66,88 +66,82 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
     return v;
 }
 
-__device__ __forceinline__ uint32_t warp_incl_scan32(uint32_t v, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t n = __shfl_up_sync(kFull, v, o);
-        if (lane >= o) v += n;
-    }
-    return v;
-}
-
 // ------------------------------------------------------------------------------------------
-// Dart staging.  An area record holds the area hash a, the rank base pb and meta =
-// vmax | sh << 24 | (S << 23) << 32, so that dart j of the area has
-//   d = mix64(a + gamma (j + 1)),  u = d >> 40,  v = (d >> 16) & (2^24 - 1),
+// Dart queue.  A record holds the dart counter c = a + gamma (j + 1) of dart j of area a,
+// pv = pb | vmax (the rank base pb is a multiple of 2^24, so its low 24 bits carry the weight
+// threshold) and meta = sh | S << 6, so that the dart has
+//   d = mix64(c),  u = d >> 40,  v = (d >> 16) & (2^24 - 1),
 //   rank = (pb + (u << sh)) 2^-S,  weight test v <= vmax.
-// A dart reference is (area slot | j << 7).
 // ------------------------------------------------------------------------------------------
-struct Ring {
-    uint32_t a_tail, d_tail, d_head;
+struct Queue {
+    uint32_t tail, head;
 };
 
-__device__ __forceinline__ uint64_t pack_meta(uint64_t vmax, int sh, int S) {
-    return vmax | ((uint64_t)sh << 24) | ((uint64_t)((uint32_t)S << 23) << 32);
-}
+__device__ __forceinline__ uint32_t pack_meta(int sh, int S) { return (uint32_t)sh | ((uint32_t)S << 6); }
 
-__device__ __forceinline__ void stage_area(Ring &q, const WarpMem &m, int lane, unsigned lt_mask, int X,
-                                           uint64_t a, uint64_t pb, uint64_t meta) {
-    unsigned bal = __ballot_sync(kFull, X > 0);
-    uint32_t aslot = (q.a_tail + __popc(bal & lt_mask)) & (kAreaRing - 1);
-    if (X > 0) {
-        m.ar_a[aslot] = a;
-        m.ar_p[aslot] = pb;
-        m.ar_m[aslot] = meta;
-    }
-    q.a_tail += __popc(bal);
-    uint32_t xin = warp_incl_scan32((uint32_t)X, lane);
-    uint32_t xtot = __shfl_sync(kFull, xin, 31);
-    uint32_t at = q.d_tail + xin - (uint32_t)X;
-    for (int j = 0; j < X; ++j) m.dref[(at + j) & (kDartRing - 1)] = (uint16_t)(aslot | (j << 7));
-    q.d_tail += xtot;
-    __syncwarp();
-}
-
-// Evaluate one queued dart; returns whether it is kept and its bucket and key.
-__device__ __forceinline__ bool dart_eval(const WarpMem &m, uint32_t ref, uint32_t k, uint32_t cthr,
+// Evaluate one queued dart; returns whether it is kept, with its bucket and key.  RHO0: every
+// queued dart has rank shift sh = 0 (rank region 0), so P = pb | u.
+template <bool RHO0>
+__device__ __forceinline__ bool dart_eval(const WarpMem &m, uint32_t pos, uint32_t k, uint32_t cthr,
                                           uint32_t &slot, uint64_t &key) {
-    int ai = ref & (kAreaRing - 1);
-    uint64_t j = ref >> 7;
-    uint64_t a = m.ar_a[ai], pb = m.ar_p[ai], meta = m.ar_m[ai];
-    uint64_t d = mix64(a + kGolden * (j + 1));
-    uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
-    uint64_t P = pb + ((uint64_t)u << ((meta >> 24) & 63));
+    const uint32_t i = pos & (kQueue - 1);
+    const uint64_t pv = m.dq_p[i];
+    const uint32_t meta = m.dq_m[i];
+    const uint64_t d = mix64(m.dq_c[i]);
+    const uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
+    const uint64_t P = RHO0 ? ((pv & ~(uint64_t)kUMask) | u)
+                            : (pv & ~(uint64_t)kUMask) + ((uint64_t)u << (meta & 63));
     // binary32 code of rank = P 2^-S rounded toward zero: exact u64 -> f32 conversion in
     // round-toward-zero mode, then the exponent lowered by S
-    uint32_t code = P ? __float_as_uint(__ull2float_rz(P)) - (uint32_t)(meta >> 32) : 0u;
-    if (v > ((uint32_t)meta & kUMask) || code >= cthr) return false;
-    uint64_t qh = mix64(d ^ kSlotSalt);
+    const uint32_t code = P ? __float_as_uint(__ull2float_rz(P)) - ((meta >> 6) << 23) : 0u;
+    if (v > ((uint32_t)pv & kUMask) || code >= cthr) return false;
+    const uint64_t qh = mix64(d ^ kSlotSalt);
     slot = fastrange32((uint32_t)(qh >> 32), k);
     key = ((uint64_t)code << 32) | (uint32_t)qh;
     return true;
 }
 
-// Process up to 64 queued darts, two per lane.
-template <bool COUNT>
-__device__ __forceinline__ void drain(int n, Ring &q, const WarpMem &m, int lane, uint32_t k, uint32_t cthr,
+// Evaluate up to 64 queued darts, two per lane.
+template <bool COUNT, bool RHO0>
+__device__ __forceinline__ void drain(int n, Queue &q, const WarpMem &m, int lane, uint32_t k, uint32_t cthr,
                                       unsigned long long &kept) {
-    uint32_t r0 = m.dref[(q.d_head + lane) & (kDartRing - 1)];
-    uint32_t r1 = m.dref[(q.d_head + 32 + lane) & (kDartRing - 1)];
     uint32_t s0 = 0, s1 = 0;
     uint64_t k0 = 0, k1 = 0;
-    bool e0 = lane < n && dart_eval(m, r0, k, cthr, s0, k0);
-    bool e1 = lane + 32 < n && dart_eval(m, r1, k, cthr, s1, k1);
+    const bool e0 = lane < n && dart_eval<RHO0>(m, q.head + lane, k, cthr, s0, k0);
+    const bool e1 = lane + 32 < n && dart_eval<RHO0>(m, q.head + 32 + lane, k, cthr, s1, k1);
     if (e0) atomicMin(reinterpret_cast<unsigned long long *>(&m.slots[s0]), (unsigned long long)k0);
     if (e1) atomicMin(reinterpret_cast<unsigned long long *>(&m.slots[s1]), (unsigned long long)k1);
     if (COUNT) kept += (unsigned long long)e0 + (unsigned long long)e1;
-    q.d_head += (uint32_t)n;
+    q.head += (uint32_t)n;
     __syncwarp();
 }
 
-template <bool COUNT>
-__device__ __forceinline__ void drain_ready(Ring &q, const WarpMem &m, int lane, uint32_t k, uint32_t cthr,
-                                            unsigned long long &kept) {
-    while (q.d_tail - q.d_head >= 64) drain<COUNT>(64, q, m, lane, k, cthr, kept);
+// Emission state of one lane: the current area's remaining darts.
+struct Emit {
+    uint64_t c;       // counter of the next dart of the current area
+    uint64_t pv;
+    uint32_t meta;
+    int rem;          // darts of the current area not yet emitted
+};
+
+// One emission round: every lane with a pending dart appends it to the queue (slot = rank of
+// the lane among emitting lanes), then full batches are evaluated.
+template <bool COUNT, bool RHO0>
+__device__ __forceinline__ void emit_round(Emit &em, Queue &q, const WarpMem &m, int lane, unsigned lt_mask,
+                                           uint32_t k, uint32_t cthr, unsigned long long &kept) {
+    const bool has = em.rem > 0;
+    const unsigned bal = __ballot_sync(kFull, has);
+    if (has) {
+        const uint32_t i = (q.tail + __popc(bal & lt_mask)) & (kQueue - 1);
+        m.dq_c[i] = em.c;
+        m.dq_p[i] = em.pv;
+        m.dq_m[i] = (uint16_t)em.meta;
+        em.c += kGolden;
+        --em.rem;
+    }
+    q.tail += __popc(bal);
+    __syncwarp();
+    if (q.tail - q.head >= 64) drain<COUNT, RHO0>(64, q, m, lane, k, cthr, kept);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -170,9 +164,8 @@ __device__ __forceinline__ uint64_t publish_tile(const WarpMem &m, int lane, int
     uint64_t incl = warp_incl_scan(n_el, lane);
     m.te[lane] = e;
     m.tF[lane] = F;
-    m.tnu[lane] = nutop;
+    m.tnu[lane] = n_el ? nutop : -1;
     m.toff[lane] = incl - n_el;
-    m.tcnt[lane] = n_el;
     __syncwarp();
     return __shfl_sync(kFull, incl, 31);
 }
@@ -189,219 +182,217 @@ __device__ __forceinline__ int tile_element(const WarpMem &m, uint64_t idx) {
 
 // ------------------------------------------------------------------------------------------
 // Fast walk for passes whose limit is below 1 (rho_top = rho_lo = 0): every region is one
-// column (w = 0) of rows [rlo(nu), rhi(nu)), so an element's areas form a 1-D sequence.
-// ------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t r0_hi(const PassCut &pc, int nu) { return nu ? (pc.gm1 >> (64 - nu)) + 1 : 1; }
-__device__ __forceinline__ uint64_t r0_lo(const PassCut &pc, int nu) { return nu ? (pc.gfl_lo >> (64 - nu)) : 0; }
-
-// sum_{nu=1..n} floor(G / 2^(64-nu)) = 2H - popc(H), H = floor(G / 2^(64-n))
-__device__ __forceinline__ uint64_t shifted_sum(uint64_t G, int n) {
-    if (n <= 0) return 0;
-    uint64_t H = G >> (64 - n);
-    return 2 * H - (uint64_t)__popcll(H);
-}
-
-__device__ __forceinline__ uint64_t r0_count(int nutop, const PassCut &pc) {
-    return 1 + (uint64_t)nutop + shifted_sum(pc.gm1, nutop) - shifted_sum(pc.gfl_lo, nutop);
-}
-
-struct Walk0 {
+// column (w = 0) of rows [rlo(nu), rhi(nu)) with rlo = floor(g_prev 2^nu) (0 on the first
+// pass) and rhi = ceil(g 2^nu), so an element's areas form a 1-D sequence.  Tiles whose
+// elements all have nu_top <= 31 run it in 32-bit arithmetic: then
+// floor(G / 2^(64 - nu)) = hi32(G) >> (32 - nu), the element's area count is
+// 1 + nu_top + sum_{nu=1..nu_top} (floor(gm1 / 2^(64-nu)) - floor(gfl_prev / 2^(64-nu))) with
+// sum_{nu=1..n} floor(G / 2^(64-nu)) = 2H - popc(H), H = floor(G / 2^(64-n)), and the area
+// counter e + gamma (nu 2^58 + r + 1) = e + gamma + gamma r + ((21 nu mod 64) << 58)
+// (gamma mod 64 = 21).
+struct Walk0S {
     int el, nu, nutop;
-    uint64_t r, rhi, e, F, ctr;
-    uint32_t vmax;
-};
+    uint32_t r, rhi, vmax, g_hi, glo_hi;
+    uint64_t e, F, ctr;
 
-__device__ __forceinline__ void w0_region(Walk0 &s, const PassCut &pc) {
-    s.r = r0_lo(pc, s.nu);
-    s.rhi = r0_hi(pc, s.nu);
-    s.vmax = (s.nu == s.nutop) ? (uint32_t)(s.F >> 40) : kUMask;
-    s.ctr = s.e + kGolden * ((((uint64_t)s.nu << 58) | s.r) + 1);
-}
-
-template <bool COUNT>
-__device__ int pass_rho0(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc, const WarpMem &m,
-                         int lane, Ring &q, unsigned long long *cnt) {
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const uint32_t k = (uint32_t)p.k;
-    for (int64_t tile = beg; tile < end; tile += 32) {
-        int nutop;
-        uint64_t F, e;
-        bool ok = element_setup(p, tile + lane, end, nutop, F, e);
-        if (__any_sync(kFull, !ok)) return DM_ERANGE;
-        uint64_t total = publish_tile(m, lane, nutop, F, e, nutop >= 0 ? r0_count(nutop, pc) : 0);
-        if (total == 0) continue;
-        uint64_t share = (total + 31) >> 5;
-        uint64_t lo = share * lane, hi = min(lo + share, total);
-        Walk0 s;
-        if (lo < hi) {
-            s.el = tile_element(m, lo);
-            s.e = m.te[s.el];
-            s.F = m.tF[s.el];
-            s.nutop = m.tnu[s.el];
-            uint64_t li = lo - m.toff[s.el];
-            for (s.nu = 0;; ++s.nu) {
-                uint64_t rows = r0_hi(pc, s.nu) - r0_lo(pc, s.nu);
-                if (li < rows) break;
-                li -= rows;
-            }
-            w0_region(s, pc);
-            s.r += li;
-            s.ctr += kGolden * li;
-        }
-        for (uint64_t it = 0; it < share; ++it) {
-            bool active = lo + it < hi;
-            int X = 0;
-            uint64_t a = 0;
-            if (active) {
-                a = mix64(s.ctr);
-                X = poisson1((uint32_t)(a >> 32), c_pois);
-                if (COUNT) { cnt[0]++; cnt[1] += X; }
-            }
-            stage_area(q, m, lane, lt_mask, X, a, s.r << 24, pack_meta(s.vmax, 0, s.nu + 24));
-            drain_ready<COUNT>(q, m, lane, k, pc.cthr, cnt[2]);
-            if (active) {
-                ++s.r;
-                s.ctr += kGolden;
-                if (s.r == s.rhi) {
-                    if (++s.nu > s.nutop) {
-                        s.nu = 0;
-                        do { ++s.el; } while (s.el < 32 && m.tcnt[s.el] == 0);
-                        if (s.el < 32) {
-                            s.e = m.te[s.el];
-                            s.F = m.tF[s.el];
-                            s.nutop = m.tnu[s.el];
-                        }
-                    }
-                    if (s.el < 32) w0_region(s, pc);
-                }
-            }
-        }
-        __syncwarp();
+    __device__ static uint32_t rows_hi(uint32_t g_hi, int nu) { return nu ? (g_hi >> (32 - nu)) + 1u : 1u; }
+    __device__ static uint32_t rows_lo(uint32_t glo_hi, int nu) { return nu ? (glo_hi >> (32 - nu)) : 0u; }
+    __device__ static uint32_t ssum(uint32_t G_hi, int n) {
+        if (n <= 0) return 0;
+        uint32_t H = G_hi >> (32 - n);
+        return 2 * H - (uint32_t)__popc(H);
     }
-    return 0;
-}
+    __device__ static uint32_t count(int nutop, const PassCut &pc) {
+        return 1u + (uint32_t)nutop + ssum((uint32_t)(pc.gm1 >> 32), nutop) - ssum((uint32_t)(pc.gfl_lo >> 32), nutop);
+    }
+    __device__ void region() {
+        r = rows_lo(glo_hi, nu);
+        rhi = rows_hi(g_hi, nu);
+        vmax = (nu == nutop) ? (uint32_t)(F >> 40) : kUMask;
+        ctr = e + kGolden + kGolden * (uint64_t)r + ((uint64_t)((21u * (uint32_t)nu) & 63u) << 58);
+    }
+    __device__ void load(const WarpMem &m) {
+        e = m.te[el];
+        F = m.tF[el];
+        nutop = m.tnu[el];
+    }
+    __device__ void locate(uint32_t idx, const WarpMem &m, const PassCut &pc) {
+        g_hi = (uint32_t)(pc.gm1 >> 32);
+        glo_hi = (uint32_t)(pc.gfl_lo >> 32);
+        el = tile_element(m, idx);
+        load(m);
+        uint32_t li = idx - (uint32_t)m.toff[el];
+        for (nu = 0;; ++nu) {
+            uint32_t rows = rows_hi(g_hi, nu) - rows_lo(glo_hi, nu);
+            if (li < rows) break;
+            li -= rows;
+        }
+        region();
+        r += li;
+        ctr += kGolden * (uint64_t)li;
+    }
+    __device__ uint64_t pv() const { return ((uint64_t)r << 24) | vmax; }
+    __device__ uint32_t meta() const { return pack_meta(0, nu + 24); }
+    __device__ void advance(const WarpMem &m) {
+        ++r;
+        ctr += kGolden;
+        if (r != rhi) return;
+        if (++nu > nutop) {
+            nu = 0;
+            do { ++el; } while (el < 32 && m.tnu[el] < 0);
+            if (el >= 32) return;
+            load(m);
+        }
+        region();
+    }
+};
 
 // ------------------------------------------------------------------------------------------
 // General walk: regions (nu, rho), columns w and rows r.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t element_areas(int nutop, uint64_t F, const PassCut &pc) {
-    uint64_t total = 0;
-    for (int nu = 0; nu <= nutop; ++nu)
-        for (int rho = pc.rho_lo; rho <= pc.rho_top; ++rho)
-            total += cols(nu, rho, nutop, F) * (rows_hi(pc, nu, rho) - rows_lo(pc, nu, rho));
-    return total;
-}
-
-struct Walk {
+struct WalkG {
     int el, nu, rho, nutop;
     uint64_t w, r, ncols, rlo, rhi;
     uint64_t e, F, WT, rbase, packhi, ctr;
+
+    __device__ static uint64_t count(int nutop, uint64_t F, const PassCut &pc) {
+        uint64_t total = 0;
+        for (int n = 0; n <= nutop; ++n)
+            for (int h = pc.rho_lo; h <= pc.rho_top; ++h)
+                total += cols(n, h, nutop, F) * (rows_hi(pc, n, h) - rows_lo(pc, n, h));
+        return total;
+    }
+    __device__ void region(const PassCut &pc) {
+        ncols = cols(nu, rho, nutop, F);
+        rlo = rows_lo(pc, nu, rho);
+        rhi = rows_hi(pc, nu, rho);
+        WT = (nu == nutop) ? (F >> (40 - rho)) : ~0ull;
+        rbase = ((1ull << rho) - 1) << (62 - rho);
+        packhi = ((uint64_t)nu << 58) | ((uint64_t)rho << 52);
+    }
+    __device__ void set_ctr() { ctr = e + kGolden * ((packhi | (w << nu) | r) + 1); }
+    __device__ void load(const WarpMem &m) {
+        e = m.te[el];
+        F = m.tF[el];
+        nutop = m.tnu[el];
+    }
+    __device__ void locate(uint64_t idx, const WarpMem &m, const PassCut &pc) {
+        el = tile_element(m, idx);
+        load(m);
+        uint64_t li = idx - m.toff[el];
+        for (nu = 0; nu <= nutop; ++nu) {
+            bool found = false;
+            for (rho = pc.rho_lo; rho <= pc.rho_top; ++rho) {
+                region(pc);
+                uint64_t nrows = rhi - rlo, c = ncols * nrows;
+                if (li < c) {
+                    w = li / nrows;
+                    r = rlo + (li - w * nrows);
+                    found = true;
+                    break;
+                }
+                li -= c;
+            }
+            if (found) break;
+        }
+        set_ctr();
+    }
+    __device__ uint64_t pv() const {
+        return rbase + (r << (62 - nu)) + min(WT - (w << 24), (uint64_t)kUMask);
+    }
+    __device__ uint32_t meta() const { return pack_meta(38 - nu, 62 - rho); }
+    __device__ void advance(const WarpMem &m, const PassCut &pc) {
+        ++r;
+        ctr += kGolden;
+        if (r < rhi) return;
+        ++w;
+        if (w >= ncols) {
+            w = 0;
+            if (++rho > pc.rho_top) {
+                rho = pc.rho_lo;
+                if (++nu > nutop) {
+                    nu = 0;
+                    do { ++el; } while (el < 32 && m.tnu[el] < 0);
+                    if (el >= 32) return;         // past the tile: the lane is done
+                    load(m);
+                }
+            }
+            region(pc);
+        }
+        r = rlo;
+        set_ctr();
+    }
 };
 
-__device__ __forceinline__ void walk_region(Walk &s, const PassCut &pc) {
-    s.ncols = cols(s.nu, s.rho, s.nutop, s.F);
-    s.rlo = rows_lo(pc, s.nu, s.rho);
-    s.rhi = rows_hi(pc, s.nu, s.rho);
-    s.WT = (s.nu == s.nutop) ? (s.F >> (40 - s.rho)) : ~0ull;
-    s.rbase = ((1ull << s.rho) - 1) << (62 - s.rho);
-    s.packhi = ((uint64_t)s.nu << 58) | ((uint64_t)s.rho << 52);
-}
-
-__device__ __forceinline__ void walk_ctr(Walk &s) {
-    s.ctr = s.e + kGolden * ((s.packhi | (s.w << s.nu) | s.r) + 1);
-}
-
-__device__ __forceinline__ void walk_load_element(Walk &s, const WarpMem &m) {
-    s.e = m.te[s.el];
-    s.F = m.tF[s.el];
-    s.nutop = m.tnu[s.el];
-}
-
-__device__ __forceinline__ void walk_locate(Walk &s, uint64_t idx, const WarpMem &m, const PassCut &pc) {
-    s.el = tile_element(m, idx);
-    walk_load_element(s, m);
-    uint64_t li = idx - m.toff[s.el];
-    for (s.nu = 0; s.nu <= s.nutop; ++s.nu) {
-        bool found = false;
-        for (s.rho = pc.rho_lo; s.rho <= pc.rho_top; ++s.rho) {
-            walk_region(s, pc);
-            uint64_t nrows = s.rhi - s.rlo, c = s.ncols * nrows;
-            if (li < c) {
-                s.w = li / nrows;
-                s.r = s.rlo + (li - s.w * nrows);
-                found = true;
-                break;
-            }
-            li -= c;
+// Emission loop over one tile with walk W (W::locate positions the walk at a lane's first
+// area, W::advance moves to the next): each lane hashes its next area once the darts of the
+// previous one are emitted, and emits at most one dart per round.
+template <class W, class Idx, bool COUNT, bool RHO0, class Adv>
+__device__ __forceinline__ void run_tile(W &s, Idx left, Adv advance, Queue &q, const WarpMem &m, int lane,
+                                         unsigned lt_mask, uint32_t k, uint32_t cthr, unsigned long long *cnt) {
+    Emit em;
+    em.rem = 0;
+    while (__any_sync(kFull, left > 0 || em.rem > 0)) {
+        if (em.rem == 0 && left > 0) {
+            const uint64_t a = mix64(s.ctr);
+            em.rem = poisson1((uint32_t)(a >> 32), c_pois);
+            em.c = a + kGolden;
+            em.pv = s.pv();
+            em.meta = s.meta();
+            if (COUNT) { cnt[0]++; cnt[1] += em.rem; }
+            if (--left) advance(s);
         }
-        if (found) break;
+        emit_round<COUNT, RHO0>(em, q, m, lane, lt_mask, k, cthr, cnt[2]);
     }
-    walk_ctr(s);
 }
 
-__device__ __forceinline__ void walk_advance(Walk &s, const WarpMem &m, const PassCut &pc) {
-    ++s.r;
-    s.ctr += kGolden;
-    if (s.r < s.rhi) return;
-    ++s.w;
-    if (s.w >= s.ncols) {
-        s.w = 0;
-        if (++s.rho > pc.rho_top) {
-            s.rho = pc.rho_lo;
-            if (++s.nu > s.nutop) {
-                s.nu = 0;
-                do { ++s.el; } while (s.el < 32 && m.tcnt[s.el] == 0);
-                if (s.el >= 32) return;           // past the tile: the lane is done
-                walk_load_element(s, m);
-            }
-        }
-        walk_region(s, pc);
-    }
-    s.r = s.rlo;
-    walk_ctr(s);
-}
-
-template <bool COUNT>
-__device__ int pass_general(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc, const WarpMem &m,
-                            int lane, Ring &q, unsigned long long *cnt) {
+// One pass of DartHash over the row; RHO0 passes have a rank limit below 1.  Returns 0 or an
+// error code.
+template <bool RHO0, bool COUNT>
+__device__ int darthash_pass(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc,
+                             const WarpMem &m, int lane, unsigned long long *cnt) {
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint32_t k = (uint32_t)p.k;
+    Queue q = {0, 0};
     for (int64_t tile = beg; tile < end; tile += 32) {
         int nutop;
         uint64_t F, e;
-        bool ok = element_setup(p, tile + lane, end, nutop, F, e);
+        const bool ok = element_setup(p, tile + lane, end, nutop, F, e);
         if (__any_sync(kFull, !ok)) return DM_ERANGE;
-        uint64_t total = publish_tile(m, lane, nutop, F, e, nutop >= 0 ? element_areas(nutop, F, pc) : 0);
-        if (total == 0) continue;
-        uint64_t share = (total + 31) >> 5;
-        uint64_t lo = share * lane, hi = min(lo + share, total);
-        Walk s;
-        if (lo < hi) walk_locate(s, lo, m, pc);
-        for (uint64_t it = 0; it < share; ++it) {
-            bool active = lo + it < hi;
-            int X = 0;
-            uint64_t a = 0, pb = 0, meta = 0;
-            if (active) {
-                a = mix64(s.ctr);
-                X = poisson1((uint32_t)(a >> 32), c_pois);
-                uint64_t vmax = min(s.WT - (s.w << 24), (uint64_t)kUMask);
-                pb = s.rbase + (s.r << (62 - s.nu));
-                meta = pack_meta(vmax, 38 - s.nu, 62 - s.rho);
-                if (COUNT) { cnt[0]++; cnt[1] += X; }
-            }
-            stage_area(q, m, lane, lt_mask, X, a, pb, meta);
-            drain_ready<COUNT>(q, m, lane, k, pc.cthr, cnt[2]);
-            if (active) walk_advance(s, m, pc);
+        if (RHO0) {
+            // 32-bit walk; a tile outside its range sends the whole set to the general kernel
+            if (!__all_sync(kFull, nutop <= 31)) return kDefer;
+            const uint64_t total = publish_tile(m, lane, nutop, F, e, nutop >= 0 ? Walk0S::count(nutop, pc) : 0);
+            if (total == 0) continue;
+            if (total >= (1ull << 31)) return kDefer;
+            const uint32_t share = (uint32_t)((total + 31) >> 5);
+            const uint32_t lo = share * (uint32_t)lane;
+            uint32_t left = lo < (uint32_t)total ? min(share, (uint32_t)total - lo) : 0u;
+            Walk0S s;
+            if (left) s.locate(lo, m, pc);
+            run_tile<Walk0S, uint32_t, COUNT, RHO0>(s, left, [&](Walk0S &w) { w.advance(m); }, q, m, lane,
+                                                     lt_mask, k, pc.cthr, cnt);
+        } else {
+            const uint64_t total = publish_tile(m, lane, nutop, F, e, nutop >= 0 ? WalkG::count(nutop, F, pc) : 0);
+            if (total == 0) continue;
+            const uint64_t share = (total + 31) >> 5;
+            const uint64_t lo = share * lane;
+            uint64_t left = lo < total ? min(share, total - lo) : 0;
+            WalkG s;
+            if (left) s.locate(lo, m, pc);
+            run_tile<WalkG, uint64_t, COUNT, RHO0>(s, left, [&](WalkG &w) { w.advance(m, pc); }, q, m, lane,
+                                                    lt_mask, k, pc.cthr, cnt);
         }
-        __syncwarp();
     }
+    if (q.tail != q.head) drain<COUNT, RHO0>((int)(q.tail - q.head), q, m, lane, k, pc.cthr, cnt[2]);
     return 0;
 }
 
-// MODE 0 (fast): sets are taken in order; every pass whose rank limit is below 1 runs the 1-D
-// walk; a set needing a limit >= 1 is appended to the general queue and left to MODE 1.
+// MODE 0 (fast): every pass whose rank limit is below 1 runs the 1-D walk; a set needing a
+// limit >= 1 is appended to the general queue and left to MODE 1.
 // MODE 1 (general): sets are taken from the queue and computed from the first pass with the
 // general walk.  Both give the same bits for a set (the output does not depend on the limits).
+// Warps are persistent and claim work items from a global counter.
 template <bool BBIT, bool COUNT, int MODE>
 __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) sketch_kernel(const SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -410,15 +401,19 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) sketch_kernel(const Sk
     WarpMem m = carve(smem + (size_t)wib * p.warp_bytes, p.k);
     const uint32_t k = (uint32_t)p.k;
     const int64_t n_work = MODE == 0 ? p.n_sets : (int64_t)*p.queue_count;
-    for (int64_t wi = (int64_t)blockIdx.x * p.warps_per_block + wib; wi < n_work;
-         wi += (int64_t)gridDim.x * p.warps_per_block) {
-        const int64_t set = MODE == 0 ? wi : (int64_t)p.queue[wi];
+    unsigned int *next = p.work_next + MODE;
+    for (;;) {
+        unsigned int wi = 0;
+        if (lane == 0) wi = atomicAdd(next, 1u);
+        wi = __shfl_sync(kFull, wi, 0);
+        if ((int64_t)wi >= n_work) break;
+        const int64_t set = MODE == 0 ? (int64_t)wi : (int64_t)p.queue[wi];
         const int64_t beg = p.indptr[set], end = p.indptr[set + 1];
         // ||x||_1 and input validation
         float l1 = 0.f;
         bool bad = false;
-        for (int64_t q = beg + lane; q < end; q += 32) {
-            float x = p.weights[q];
+        for (int64_t i = beg + lane; i < end; i += 32) {
+            float x = p.weights[i];
             if (!(x >= 0.f) || isinf(x)) bad = true;
             else l1 += x;
         }
@@ -443,13 +438,13 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) sketch_kernel(const Sk
                 pc.gm1 = rc.gm1;
                 pc.cthr = th;
                 if (MODE == 0 && pc.rho_top != 0) { deferred = true; break; }
-                Ring q = {0, 0, 0};
-                err = MODE == 0 ? pass_rho0<COUNT>(p, beg, end, pc, m, lane, q, cnt)
-                                : pass_general<COUNT>(p, beg, end, pc, m, lane, q, cnt);
+                // the fast kernel only runs rank-region-0 passes; the general kernel runs the
+                // general walk on every pass (it is correct for any limit)
+                err = MODE == 0 ? darthash_pass<true, COUNT>(p, beg, end, pc, m, lane, cnt)
+                                : darthash_pass<false, COUNT>(p, beg, end, pc, m, lane, cnt);
                 ++passes;
+                if (err == kDefer) { err = 0; deferred = true; break; }
                 if (err) break;
-                if (q.d_tail != q.d_head)
-                    drain<COUNT>((int)(q.d_tail - q.d_head), q, m, lane, k, pc.cthr, cnt[2]);
                 bool empty = false;
                 for (uint32_t j = lane; j < k; j += 32) empty |= (m.slots[j] == ~0ull);
                 if (!__any_sync(kFull, empty)) break;
@@ -536,10 +531,23 @@ static cudaError_t launch_mode(const SketchParams &p, bool bbit, bool count, int
 
 cudaError_t launch_sketch(const SketchParams &p, bool bbit, bool count, int grid_fast, int grid_general,
                           cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(p.queue_count, 0, sizeof(unsigned int), st);
+    // queue count and the two work counters are contiguous
+    cudaError_t e = cudaMemsetAsync(p.queue_count, 0, 4 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     if ((e = launch_mode<0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
     return launch_mode<1>(p, bbit, count, grid_general, st);
 }
 
+}  // namespace dm
+
+namespace dm {
+int sketch_blocks_per_sm(int mode, bool bbit, int warps_per_block, size_t smem) {
+    int nb = 0;
+    const void *fn;
+    if (mode == 0) fn = bbit ? (const void *)sketch_kernel<true, false, 0> : (const void *)sketch_kernel<false, false, 0>;
+    else fn = bbit ? (const void *)sketch_kernel<true, false, 1> : (const void *)sketch_kernel<false, false, 1>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * warps_per_block, smem) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
 }  // namespace dm

@@ -90,6 +90,25 @@ def test_extreme_norms_parity(dmx, torch_mod, ctx, oracle_mod):
         assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 99), f"k={k}")
 
 
+def test_large_weights_parity(dmx, torch_mod, ctx, oracle_mod):
+    """Weights with t x_i >= 2^31 (weight regions above 31, handled by the general kernel)
+    beside ordinary rows, up to the 2^39 limit."""
+    rng = np.random.default_rng(12)
+    rows = []
+    for big in [1e7, 1e8, 3e8]:
+        for nnz in [1, 3, 33]:
+            idx = np.sort(rng.choice(1 << 30, nnz, replace=False)).astype(np.uint32)
+            w = rng.exponential(size=nnz).astype(np.float32)
+            w[0] = np.float32(big)
+            rows.append((idx, w))
+        rows.append((np.array([5, 6], np.uint32), np.array([0.5, 2.0], np.float32)))
+    b = workloads.csr_of(rows)
+    for k in (64, 256):
+        got, rc = gpu_sketch(dmx, torch_mod, ctx, b, k, 31)
+        assert rc == 0
+        assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 31), f"k={k}")
+
+
 def test_edge_cases_parity(dmx, torch_mod, ctx, oracle_mod):
     f = np.float32
     rows = [
