@@ -99,7 +99,7 @@ int cuda_fail(cudaError_t e) {
 }
 
 int auto_warps(int k) {
-    size_t per = dm::sketch_warp_bytes(k);
+    size_t per = dm::sketch_warp_bytes(k) > dm::fast_warp_bytes(k) ? dm::sketch_warp_bytes(k) : dm::fast_warp_bytes(k);
     int w = (int)((96 * 1024) / per);
     if (w > 8) w = 8;
     if (w < 1) w = 1;
@@ -167,14 +167,16 @@ int run_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, cons
     p.counters = ctx->counters;
     p.warps_per_block = ctx->warps_per_block > 0 ? ctx->warps_per_block : auto_warps(k);
     p.warp_bytes = (int32_t)dm::sketch_warp_bytes(k);
+    p.warp_bytes_fast = (int32_t)dm::fast_warp_bytes(k);
     p.queue = (int32_t *)queue;
     p.queue_count = (unsigned int *)((char *)queue + queue_bytes(n_sets) - 256);
     p.work_next = p.queue_count + 1;
     size_t smem = (size_t)p.warp_bytes * p.warps_per_block;
-    if (smem > 227 * 1024) return DM_EINVAL;
+    size_t smem_fast = (size_t)p.warp_bytes_fast * p.warps_per_block;
+    if (smem > 227 * 1024 || smem_fast > 227 * 1024) return DM_EINVAL;
     // persistent grids: as many blocks as can be resident, never more than there are sets
     int64_t blocks = (n_sets + p.warps_per_block - 1) / p.warps_per_block;
-    int64_t cap0 = (int64_t)ctx->sm_count * dm::sketch_blocks_per_sm(0, bbit, p.warps_per_block, smem);
+    int64_t cap0 = (int64_t)ctx->sm_count * dm::sketch_blocks_per_sm(0, bbit, p.warps_per_block, smem_fast);
     int64_t cap1 = (int64_t)ctx->sm_count * dm::sketch_blocks_per_sm(1, bbit, p.warps_per_block, smem);
     int grid = (int)(blocks < cap0 ? blocks : cap0);
     int grid_general = (int)(blocks < cap1 ? blocks : cap1);

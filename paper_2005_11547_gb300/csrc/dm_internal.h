@@ -25,15 +25,17 @@ struct SketchParams {
     uint32_t *out_lsh;    // LSH values (LSH mode only)
     int *status;          // first device-detected error
     unsigned long long *counters;   // optional work counters (4)
-    int32_t warp_bytes;   // dynamic shared memory per warp
+    int32_t warp_bytes;   // dynamic shared memory per warp (general kernel)
+    int32_t warp_bytes_fast;  // dynamic shared memory per warp (fast kernel)
     int32_t warps_per_block;
     int32_t *queue;             // sets deferred to the general kernel (capacity n_sets)
     unsigned int *queue_count;  // number of queued sets; followed by the two work counters
     unsigned int *work_next;    // = queue_count + 1: next work item of the fast / general kernel
 };
 
-// Per-warp shared memory for the sketch kernel (k slots + staging rings + tile arrays).
+// Per-warp shared memory of the general and fast sketch kernels.
 size_t sketch_warp_bytes(int k);
+size_t fast_warp_bytes(int k);
 
 cudaError_t upload_poisson_table(const uint32_t *T);
 // Resident blocks per SM of the fast (mode 0) or general (mode 1) kernel.

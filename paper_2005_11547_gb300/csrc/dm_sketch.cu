@@ -248,6 +248,212 @@ struct Walk0S {
 };
 
 // ------------------------------------------------------------------------------------------
+// Fast-kernel batch emission.  Per tile, every lane walks an equal share of the areas; in each
+// iteration every lane hashes one area, and the darts of all 32 areas are written to the
+// queue at once (positions from a ballot prefix sum of X < 16), so the warp spends exactly one
+// iteration per area slot.  A record is 16 bytes: the dart counter c and
+// pvs = r << 24 | vmax | S << 57 (r < 2^31 in the 32-bit walk), rank = (r 2^24 + u) 2^-S.
+// ------------------------------------------------------------------------------------------
+constexpr int kFastQueue = 128;
+constexpr int kRowTab = 40;                       // nu = 0..38 (+1 pad)
+constexpr uint64_t kRMask = ((1ull << 55) - 1) & ~(uint64_t)kUMask;
+
+struct FastMem {
+    uint64_t *slots, *fq_c, *fq_p, *te;
+    uint32_t *tv, *toff, *rlo, *rhi;
+    int *tnu;
+};
+
+size_t fast_warp_bytes(int k) {
+    size_t b = (size_t)k * 8 + 2 * kFastQueue * 8 + 32 * 8 + 3 * 32 * 4 + 2 * kRowTab * 4;
+    return (b + 15) & ~(size_t)15;
+}
+
+__device__ __forceinline__ FastMem carve_fast(unsigned char *base, int k) {
+    FastMem m;
+    m.slots = reinterpret_cast<uint64_t *>(base);
+    m.fq_c = m.slots + k;
+    m.fq_p = m.fq_c + kFastQueue;
+    m.te = m.fq_p + kFastQueue;
+    m.tv = reinterpret_cast<uint32_t *>(m.te + 32);
+    m.toff = m.tv + 32;
+    m.tnu = reinterpret_cast<int *>(m.toff + 32);
+    m.rlo = reinterpret_cast<uint32_t *>(m.tnu + 32);
+    m.rhi = m.rlo + kRowTab;
+    return m;
+}
+
+__device__ __forceinline__ bool fast_eval(const FastMem &m, uint32_t pos, uint32_t k, uint32_t cthr,
+                                          uint32_t &slot, uint64_t &key) {
+    const uint32_t i = pos & (kFastQueue - 1);
+    const uint64_t pvs = m.fq_p[i];
+    const uint64_t d = mix64(m.fq_c[i]);
+    const uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
+    const uint64_t P = (pvs & kRMask) | u;
+    const uint32_t code = P ? __float_as_uint(__ull2float_rz(P)) - ((uint32_t)(pvs >> 57) << 23) : 0u;
+    if (v > ((uint32_t)pvs & kUMask) || code >= cthr) return false;
+    const uint64_t qh = mix64(d ^ kSlotSalt);
+    slot = fastrange32((uint32_t)(qh >> 32), k);
+    key = ((uint64_t)code << 32) | (uint32_t)qh;
+    return true;
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void fast_drain(int n, Queue &q, const FastMem &m, int lane, uint32_t k, uint32_t cthr,
+                                           unsigned long long &kept) {
+    uint32_t s0 = 0, s1 = 0;
+    uint64_t k0 = 0, k1 = 0;
+    const bool e0 = lane < n && fast_eval(m, q.head + lane, k, cthr, s0, k0);
+    const bool e1 = lane + 32 < n && fast_eval(m, q.head + 32 + lane, k, cthr, s1, k1);
+    if (e0) atomicMin(reinterpret_cast<unsigned long long *>(&m.slots[s0]), (unsigned long long)k0);
+    if (e1) atomicMin(reinterpret_cast<unsigned long long *>(&m.slots[s1]), (unsigned long long)k1);
+    if (COUNT) kept += (unsigned long long)e0 + (unsigned long long)e1;
+    q.head += (uint32_t)n;
+    __syncwarp();
+}
+
+// The 1-D walk of a rank-region-0 pass in 32-bit arithmetic (element nu_top <= 31): region nu
+// has rows [rlo[nu], rhi[nu]) from the pass table; the area counter is
+// e + gamma (nu 2^58 + r + 1) = e + gamma + gamma r + ((21 nu mod 64) << 58) (gamma mod 64 = 21).
+struct WalkF {
+    int el, nu, nutop;
+    uint32_t r, rhi, vtop;
+    uint64_t e, ctr, pvr;     // pvr = vmax | S << 57 of the current region
+
+    __device__ void region(const FastMem &m) {
+        r = m.rlo[nu];
+        rhi = m.rhi[nu];
+        pvr = (uint64_t)(nu == nutop ? vtop : kUMask) | ((uint64_t)(nu + 24) << 57);
+        ctr = e + kGolden + kGolden * (uint64_t)r + ((uint64_t)((21u * (uint32_t)nu) & 63u) << 58);
+    }
+    __device__ void load(const FastMem &m) {
+        e = m.te[el];
+        vtop = m.tv[el];
+        nutop = m.tnu[el];
+    }
+    __device__ void locate(uint32_t idx, const FastMem &m) {
+        el = 0;                                   // last element whose offset is <= idx
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+            int c = el + step;
+            if (c < 32 && m.toff[c] <= idx) el = c;
+        }
+        load(m);
+        uint32_t li = idx - m.toff[el];
+        for (nu = 0;; ++nu) {
+            uint32_t rows = m.rhi[nu] - m.rlo[nu];
+            if (li < rows) break;
+            li -= rows;
+        }
+        region(m);
+        r += li;
+        ctr += kGolden * (uint64_t)li;
+    }
+    __device__ uint64_t pvs() const { return pvr | ((uint64_t)r << 24); }
+    __device__ void advance(const FastMem &m) {
+        ++r;
+        ctr += kGolden;
+        if (r != rhi) return;
+        if (++nu > nutop) {
+            nu = 0;
+            do { ++el; } while (el < 32 && m.tnu[el] < 0);
+            if (el >= 32) return;
+            load(m);
+        }
+        region(m);
+    }
+};
+
+// One rank-region-0 pass of DartHash over the row in the fast kernel.  Returns 0, an error
+// code, or kDefer when a tile is outside the 32-bit walk's range.
+template <bool COUNT>
+__device__ int fast_pass(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc, const FastMem &m,
+                         int lane, unsigned long long *cnt) {
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t k = (uint32_t)p.k;
+    // rows of region nu in this pass: [floor(g_prev 2^nu), ceil(g 2^nu))
+    for (int nu = lane; nu < kRowTab; nu += 32) {
+        int n = nu > kMaxRegion ? kMaxRegion : nu;
+        m.rlo[nu] = n ? (uint32_t)min(pc.gfl_lo >> (64 - n), (uint64_t)0xFFFFFFFFu) : 0u;
+        m.rhi[nu] = n ? (uint32_t)min((pc.gm1 >> (64 - n)) + 1, (uint64_t)0xFFFFFFFFu) : 1u;
+    }
+    const uint32_t g_hi = (uint32_t)(pc.gm1 >> 32), glo_hi = (uint32_t)(pc.gfl_lo >> 32);
+    Queue q = {0, 0};
+    for (int64_t tile = beg; tile < end; tile += 32) {
+        const int64_t pos = tile + lane;
+        int nutop = -1;
+        uint64_t F = 0, e = 0;
+        if (pos < end) {
+            nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F);
+            if (nutop >= 0) e = mix64(p.sigma + kGolden * ((uint64_t)p.indices[pos] + 1));
+        }
+        if (__any_sync(kFull, nutop == -2)) return DM_ERANGE;
+        if (!__all_sync(kFull, nutop <= 31)) return kDefer;
+        // element area count: 1 + nu_top + sum_{nu=1..nu_top} (hi32(gm1) >> (32-nu)) - (hi32(gfl) >> (32-nu)),
+        // each sum = 2H - popc(H) with H = hi32(G) >> (32 - nu_top)
+        uint64_t n_el = 0;
+        if (nutop >= 0) {
+            n_el = 1 + (uint64_t)nutop;
+            if (nutop > 0) {
+                uint32_t H = g_hi >> (32 - nutop), Hl = glo_hi >> (32 - nutop);
+                n_el += (2 * (uint64_t)H - __popc(H)) - (2 * (uint64_t)Hl - __popc(Hl));
+            }
+        }
+        uint64_t incl = warp_incl_scan(n_el, lane);
+        const uint64_t total = __shfl_sync(kFull, incl, 31);
+        if (total >= (1ull << 31)) return kDefer;
+        m.te[lane] = e;
+        m.tv[lane] = (uint32_t)(F >> 40);
+        m.tnu[lane] = n_el ? nutop : -1;
+        m.toff[lane] = (uint32_t)(incl - n_el);
+        __syncwarp();
+        if (total == 0) continue;
+        const uint32_t share = (uint32_t)((total + 31) >> 5);
+        const uint32_t lo = share * (uint32_t)lane;
+        const uint32_t mine = lo < (uint32_t)total ? min(share, (uint32_t)total - lo) : 0u;
+        WalkF s;
+        if (mine) s.locate(lo, m);
+        for (uint32_t it = 0; it < share; ++it) {
+            int X = 0;
+            uint64_t a = 0, pv = 0;
+            if (it < mine) {
+                a = mix64(s.ctr);
+                X = poisson1((uint32_t)(a >> 32), c_pois);
+                pv = s.pvs();
+                if (COUNT) { cnt[0]++; cnt[1] += X; }
+                if (it + 1 < mine) s.advance(m);
+            }
+            // prefix sum of X (< 16) over the lanes from four ballots
+            const unsigned b0 = __ballot_sync(kFull, X & 1), b1 = __ballot_sync(kFull, X & 2);
+            const unsigned b2 = __ballot_sync(kFull, X & 4), b3 = __ballot_sync(kFull, X & 8);
+            const uint32_t T = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2) + 8 * __popc(b3);
+            if (T == 0) continue;
+            const uint32_t ex = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt) + 8 * __popc(b3 & lt);
+            // write the darts in queue-sized pieces (one piece unless T is far above its mean)
+            for (uint32_t done = 0; done < T;) {
+                const uint32_t room = kFastQueue - (q.tail - q.head);
+                const uint32_t lim = min(T - done, room);
+                uint32_t jlo = done > ex ? done - ex : 0u;
+                uint32_t jhi = done + lim > ex ? done + lim - ex : 0u;
+                if (jhi > (uint32_t)X) jhi = (uint32_t)X;
+                uint64_t c = a + kGolden * (uint64_t)(jlo + 1);
+                for (uint32_t j = jlo; j < jhi; ++j, c += kGolden) {
+                    const uint32_t i = (q.tail + ex + j - done) & (kFastQueue - 1);
+                    m.fq_c[i] = c;
+                    m.fq_p[i] = pv;
+                }
+                q.tail += lim;
+                done += lim;
+                __syncwarp();
+                while (q.tail - q.head >= 64) fast_drain<COUNT>(64, q, m, lane, k, pc.cthr, cnt[2]);
+            }
+        }
+    }
+    if (q.tail != q.head) fast_drain<COUNT>((int)(q.tail - q.head), q, m, lane, k, pc.cthr, cnt[2]);
+    return 0;
+}
+
+// ------------------------------------------------------------------------------------------
 // General walk: regions (nu, rho), columns w and rows r.
 // ------------------------------------------------------------------------------------------
 struct WalkG {
@@ -398,7 +604,9 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) sketch_kernel(const Sk
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    WarpMem m = carve(smem + (size_t)wib * p.warp_bytes, p.k);
+    const int wbytes = MODE == 0 ? p.warp_bytes_fast : p.warp_bytes;
+    WarpMem m = carve(smem + (size_t)wib * wbytes, p.k);
+    FastMem fm = carve_fast(smem + (size_t)wib * wbytes, p.k);
     const uint32_t k = (uint32_t)p.k;
     const int64_t n_work = MODE == 0 ? p.n_sets : (int64_t)*p.queue_count;
     unsigned int *next = p.work_next + MODE;
@@ -440,7 +648,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) sketch_kernel(const Sk
                 if (MODE == 0 && pc.rho_top != 0) { deferred = true; break; }
                 // the fast kernel only runs rank-region-0 passes; the general kernel runs the
                 // general walk on every pass (it is correct for any limit)
-                err = MODE == 0 ? darthash_pass<true, COUNT>(p, beg, end, pc, m, lane, cnt)
+                err = MODE == 0 ? fast_pass<COUNT>(p, beg, end, pc, fm, lane, cnt)
                                 : darthash_pass<false, COUNT>(p, beg, end, pc, m, lane, cnt);
                 ++passes;
                 if (err == kDefer) { err = 0; deferred = true; break; }
@@ -513,7 +721,7 @@ cudaError_t upload_poisson_table(const uint32_t *T) {
 
 template <bool BBIT, bool COUNT, int MODE>
 static cudaError_t launch_t(const SketchParams &p, int grid, cudaStream_t st) {
-    size_t smem = (size_t)p.warp_bytes * p.warps_per_block;
+    size_t smem = (size_t)(MODE == 0 ? p.warp_bytes_fast : p.warp_bytes) * p.warps_per_block;
     auto fn = sketch_kernel<BBIT, COUNT, MODE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
