@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dm", "reference"], default="dm")
-    ap.add_argument("--sets", type=int, default=1_000_000, help="prefix of W1 (profiling only)")
+    ap.add_argument("--sets", type=int, default=None, help="prefix of the workload (profiling only)")
+    ap.add_argument("--workload", choices=["W1", "W2", "W3"], default="W1",
+                    help="W1 (default, the headline): k=256 keys + 1-bit words; W2: k=1024 heavy-tailed batch; "
+                         "W3: (L, K) = (64, 8) LSH")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -186,7 +189,7 @@ def reference_arm(args):
     if rank != 0:
         return
     import workloads
-    b = workloads.workload1(min(args.sets, 200_000))
+    b = workloads.workload1(min(args.sets or 1_000_000, 200_000))
     cores = os.cpu_count() or 1
     per_step = 4000 * cores
     sets = []
@@ -231,25 +234,44 @@ def gpu_arm(args):
     dmx.load()
     props = torch.cuda.get_device_properties(local)
 
-    b = workloads.workload1(args.sets)
+    wl = args.workload
+    if wl == "W1":
+        b = workloads.workload1(args.sets or 1_000_000)
+    elif wl == "W2":
+        b = workloads.workload2(args.sets or 200_000)
+    else:
+        b = workloads.workload3(args.sets or 1_000_000)
     n = b.n_sets
+    kk = {"W1": K_SLOTS, "W2": 1024, "W3": 64}[wl]
     words = (K_SLOTS * B_BITS + 63) // 64
     ip = torch.from_numpy(b.indptr).cuda()
     ix = torch.from_numpy(b.indices.view(np.int32)).cuda()
     w = torch.from_numpy(b.weights).cuda()
-    keys = torch.empty((n, K_SLOTS), dtype=torch.int64, device="cuda")
-    outw = torch.empty((n, words), dtype=torch.int64, device="cuda")
+    if wl == "W3":
+        keys = torch.empty((n, 64), dtype=torch.int32, device="cuda")
+        outw = None
+    else:
+        keys = torch.empty((n, kk), dtype=torch.int64, device="cuda")
+        outw = torch.empty((n, words), dtype=torch.int64, device="cuda") if wl == "W1" else None
     ctx = dmx.dm_create(local)
     stream = torch.cuda.current_stream()
 
+    def launch(c):
+        if wl == "W1":
+            dmx.dm_sketch_bbit(c, ip, ix, w, K_SLOTS, B_BITS, SEED, out_words=outw, out_keys=keys, stream=stream)
+        elif wl == "W2":
+            dmx.dm_sketch(c, ip, ix, w, 1024, SEED, out=keys, stream=stream)
+        else:
+            dmx.dm_lsh(c, ip, ix, w, 64, 8, SEED, out=keys, stream=stream)
+
     def step():
-        dmx.dm_sketch_bbit(ctx, ip, ix, w, K_SLOTS, B_BITS, SEED, out_words=outw, out_keys=keys, stream=stream)
+        launch(ctx)
 
     # work units of one launch (untimed counting launch; counters never change output bits)
     cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
     cctx = dmx.dm_create(local)
     dmx.dm_set_option(cctx, dmx.OPT_COUNTERS, cnt.data_ptr())
-    dmx.dm_sketch_bbit(cctx, ip, ix, w, K_SLOTS, B_BITS, SEED, out_words=outw, out_keys=keys, stream=stream)
+    launch(cctx)
     dmx.dm_sync_status(cctx)
     areas, darts, kept, passes = [int(v) for v in cnt.cpu().tolist()]
     cctx.close()
@@ -280,7 +302,7 @@ def gpu_arm(args):
 
     # end to end through the host-buffer C-ABI entry (copies inside the timed region)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and wl == "W1":
         hip = torch.from_numpy(b.indptr).pin_memory()
         hix = torch.from_numpy(b.indices.view(np.int32)).pin_memory()
         hw = torch.from_numpy(b.weights).pin_memory()
@@ -305,6 +327,7 @@ def gpu_arm(args):
     # roofline of the dominant (only) kernel of the step
     mean_launch_s = sum(per_launch_ms) / len(per_launch_ms) / 1e3
     ops = areas * OPS_PER_AREA + darts * OPS_PER_DART + kept * OPS_PER_KEPT
+    out_bytes = keys.numel() * keys.element_size() + (outw.numel() * 8 if outw is not None else 0)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak_ops = props.multi_processor_count * INT_LANES_PER_SM * sm_max * 1e6
     achieved = ops / mean_launch_s
@@ -314,26 +337,32 @@ def gpu_arm(args):
                 "ops_per_launch": ops, "units_per_launch": {"areas": areas, "darts": darts, "kept": kept,
                                                             "passes": passes},
                 "hbm_gbs_algorithmic": (b.indptr.nbytes + b.indices.nbytes + b.weights.nbytes
-                                        + keys.numel() * 8 + outw.numel() * 8) / mean_launch_s / 1e9,
+                                        + out_bytes) / mean_launch_s / 1e9,
                 "peak_source": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int32 lanes x "
                                f"{sm_max:.0f} MHz (max SM clock)"}
 
     cpu_baseline = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl == "W1":
         cores = os.cpu_count() or 1
         v, ns, dt = time_oracle(b, 16000 * cores // 4, cores)
         cpu_baseline = {"value": v, "unit": "sets/s", "cores": cores, "kind": "oracle",
                         "sample": f"first {ns} sets of W1 ({dt:.1f} s wall on {cores} threads)"}
 
+    desc = {"W1": "W1: 1,000,000 sets x 256 distinct elements (d=2^20), Exp(1) fp32 weights; "
+                  "k=256 uint64 keys + 1-bit words",
+            "W2": "W2: 200,000 heavy-tailed sets (nnz log-normal median 100, sigma 1.5; ||x||_1 log-uniform "
+                  "1e-3..1e3), d=2^24; k=1024 uint64 keys",
+            "W3": "W3: 1,000,000 tf-idf-like sets (Zipf(1.1) tokens, nnz U{200..2000}), d=2^20; (L, K) = (64, 8) "
+                  "LSH uint32 values"}[wl]
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": world, "steps": args.steps,
+            "metric": METRIC if wl == "W1" else f"weighted sets/s ({wl})",
+            "value": value, "unit": "sets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "minhashes_per_s": value * K_SLOTS,
-            "config": {"workload": "W1: 1,000,000 sets x 256 distinct elements (d=2^20), Exp(1) fp32 weights; "
-                                   "k=256 uint64 keys + 1-bit words" if n == 1_000_000 else f"W1 prefix of {n} sets",
-                       "n_sets": n, "k": K_SLOTS, "b": B_BITS, "seed": SEED,
+            "minhashes_per_s": value * kk,
+            "config": {"workload": desc if args.sets is None else f"{wl} prefix of {n} sets",
+                       "n_sets": n, "k": kk, "b": B_BITS if wl == "W1" else None, "seed": SEED,
                        "form": "plain: one warp per set (fast kernel) + general kernel over its queue",
                        "l2": "inputs 2 GB and outputs 2 GB per step, > 129 MB L2: no flush needed"},
             "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,

@@ -11,8 +11,10 @@
  *   - Sets come as CSR: indptr int64[n_sets + 1] (indptr[0] = 0, non-decreasing), indices
  *     uint32[indptr[n_sets]] (element ids i), weights float32[indptr[n_sets]] (x_i).
  *     Weights must be finite and >= 0 (the domain R^d_{>=0} of Section 1); zero weights are
- *     skipped (Algorithm 1 visits only {i | x_i > 0}); a repeated index acts as the largest of
- *     its weights; element order inside a row does not matter.
+ *     skipped (Algorithm 1 visits only {i | x_i > 0}); element order inside a row does not
+ *     matter.  A repeated index acts as the largest of its weights for dm_sketch and
+ *     dm_sketch_bbit (a minimum ignores repeated darts); for dm_lsh it contributes its darts once
+ *     per occurrence, so rows passed to dm_lsh should not repeat an index.
  *   - Unless a call says otherwise, every array argument is a DEVICE pointer owned by the
  *     caller; the library reads/writes it only on `stream` and keeps no reference after the
  *     work queued on `stream` completes.  `stream` is a cudaStream_t passed as void* (NULL =
@@ -85,8 +87,9 @@ int dm_sketch_bbit(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
  * L buckets, the rank limit doubled until every bucket holds >= K darts; table l's value is
  * the high 32 bits of the chain h <- SplitMix64out(h XOR key_m) over the bucket's K smallest
  * keys in increasing order, from h = 0x082EFA98EC4E6C89.  Two sets collide in a table with
- * probability J^K, independently across tables.  out: uint32[n_sets * L]; a set with no
- * positive weight gets 0xFFFFFFFF.  1 <= L <= 1024, 1 <= K <= 32. */
+ * probability J^K, independently across tables.  out: uint32[n_sets * L] (row-major); a set
+ * with no positive weight gets 0xFFFFFFFF.  1 <= L <= 1024, 1 <= K <= 32, and a set's bucket
+ * state (about 8 L (2K + 1.5) bytes) must fit in shared memory, else DM_EINVAL. */
 int dm_lsh(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
            int64_t n_sets, int32_t L, int32_t K, uint64_t seed, uint32_t *out, void *stream);
 
@@ -114,7 +117,8 @@ enum dm_option {
     DM_OPT_COUNTERS = 2,    /* device pointer to uint64[4] accumulating areas inspected, darts
                                generated, darts kept and passes (0 = off) */
     DM_OPT_FORM = 3,        /* launch form: 0 = plain (one warp per set), 1 = batched persistent */
-    DM_OPT_WARPS_PER_BLOCK = 4  /* 1..8 warps (sets) per thread block, 0 = automatic */
+    DM_OPT_WARPS_PER_BLOCK = 4, /* 1..8 warps (sets) per thread block, 0 = automatic */
+    DM_OPT_LSH_PHI0 = 5         /* initial phi of dm_lsh's loop, as value/1024 (default 4096 = 4.0) */
 };
 int dm_set_option(dm_ctx *ctx, int option, int64_t value);
 

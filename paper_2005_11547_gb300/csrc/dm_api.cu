@@ -21,7 +21,8 @@ struct dm_ctx {
     int sm_count = 0;
     int *d_status = nullptr;
     int *h_status = nullptr;       // pinned
-    float phi0 = 1.0f;
+    float phi0 = 1.0f;             // initial phi of the sketch loop (Theorem 1)
+    float phi0_lsh = 4.0f;         // initial phi of the LSH loop (every bucket needs K darts)
     unsigned long long *counters = nullptr;
     int form = 0;
     int warps_per_block = 0;       // 0 = automatic
@@ -98,8 +99,11 @@ int cuda_fail(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? DM_ENOMEM : DM_ECUDA;
 }
 
-int auto_warps(int k) {
-    size_t per = dm::sketch_warp_bytes(k) > dm::fast_warp_bytes(k) ? dm::sketch_warp_bytes(k) : dm::fast_warp_bytes(k);
+// Warps per block: as many as fit 96 KB of shared memory (so two or more blocks are resident),
+// at most 8.
+int auto_warps(bool lsh, int k, int K) {
+    size_t a = dm::warp_bytes(lsh, k, K, 0), b = dm::warp_bytes(lsh, k, K, 1);
+    size_t per = a > b ? a : b;
     int w = (int)((96 * 1024) / per);
     if (w > 8) w = 8;
     if (w < 1) w = 1;
@@ -128,21 +132,32 @@ int ensure_queue(dm_ctx *ctx, int64_t n_sets) {
     return DM_OK;
 }
 
-int run_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
-               int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_words,
-               uint64_t *out_keys, cudaStream_t st, void *queue = nullptr) {
+// One batched call: sketches (lsh = false: k minhashes, optional b-bit words) or (L, K) LSH
+// (lsh = true: k = L).  queue: scratch for the general kernel's work queue (null = context's).
+int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+             int64_t n_sets, bool lsh, int32_t k, int32_t K, int32_t b, uint64_t seed, uint64_t *out_words,
+             uint64_t *out_keys, uint32_t *out_lsh, cudaStream_t st, void *queue = nullptr) {
     if (!ctx) return DM_EINVAL;
     int rc = check_csr(indptr, indices, weights, n_sets);
     if (rc) return rc;
-    if (k < 1 || k > 8192) return DM_EINVAL;
-    int64_t t = t_of_k(k);
-    if (t <= 0) return DM_EINVAL;
+    int64_t t;
+    if (lsh) {
+        if (k < 1 || k > 1024 || K < 1 || K > 32 || !out_lsh) return DM_EINVAL;
+        t = (int64_t)k * K;
+    } else {
+        if (k < 1 || k > 8192) return DM_EINVAL;
+        t = t_of_k(k);
+        if (t <= 0) return DM_EINVAL;
+    }
     bool bbit = b > 0;
     if (bbit && !(b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32)) return DM_EINVAL;
-    if (!bbit && !out_keys) return DM_EINVAL;
+    if (!lsh && !bbit && !out_keys) return DM_EINVAL;
     if (bbit && !out_words) return DM_EINVAL;
     if (n_sets == 0) return DM_OK;
     if (n_sets > 0x7FFFFFFF) return DM_EINVAL;
+    const int wpb = ctx->warps_per_block > 0 ? ctx->warps_per_block : auto_warps(lsh, k, K);
+    const size_t smem_fast = dm::warp_bytes(lsh, k, K, 0) * wpb, smem = dm::warp_bytes(lsh, k, K, 1) * wpb;
+    if (smem > 227 * 1024 || smem_fast > 227 * 1024) return DM_EINVAL;     // L and K too large for LSH
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e);
     if (!queue) {
@@ -156,31 +171,38 @@ int run_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, cons
     p.weights = weights;
     p.n_sets = n_sets;
     p.k = k;
+    p.K = lsh ? K : 0;
     p.t = (uint32_t)t;
     p.sigma = dm::mix64(seed ^ dm::kSeedSalt);
-    p.phi0 = ctx->phi0;
+    p.phi0 = lsh ? ctx->phi0_lsh : ctx->phi0;
     p.b = bbit ? b : 0;
     p.words = bbit ? (int32_t)(((int64_t)k * b + 63) / 64) : 0;
     p.out_keys = out_keys;
     p.out_words = out_words;
+    p.out_lsh = out_lsh;
     p.status = ctx->d_status;
     p.counters = ctx->counters;
-    p.warps_per_block = ctx->warps_per_block > 0 ? ctx->warps_per_block : auto_warps(k);
-    p.warp_bytes = (int32_t)dm::sketch_warp_bytes(k);
-    p.warp_bytes_fast = (int32_t)dm::fast_warp_bytes(k);
+    p.warps_per_block = wpb;
+    p.warp_bytes = (int32_t)dm::warp_bytes(lsh, k, K, 1);
+    p.warp_bytes_fast = (int32_t)dm::warp_bytes(lsh, k, K, 0);
+    p.sink_bytes = (int32_t)dm::sink_bytes(lsh, k, K);
     p.queue = (int32_t *)queue;
     p.queue_count = (unsigned int *)((char *)queue + queue_bytes(n_sets) - 256);
     p.work_next = p.queue_count + 1;
-    size_t smem = (size_t)p.warp_bytes * p.warps_per_block;
-    size_t smem_fast = (size_t)p.warp_bytes_fast * p.warps_per_block;
-    if (smem > 227 * 1024 || smem_fast > 227 * 1024) return DM_EINVAL;
     // persistent grids: as many blocks as can be resident, never more than there are sets
-    int64_t blocks = (n_sets + p.warps_per_block - 1) / p.warps_per_block;
-    int64_t cap0 = (int64_t)ctx->sm_count * dm::sketch_blocks_per_sm(0, bbit, p.warps_per_block, smem_fast);
-    int64_t cap1 = (int64_t)ctx->sm_count * dm::sketch_blocks_per_sm(1, bbit, p.warps_per_block, smem);
+    int64_t blocks = (n_sets + wpb - 1) / wpb;
+    int64_t cap0 = (int64_t)ctx->sm_count * dm::blocks_per_sm(lsh, 0, bbit, wpb, smem_fast);
+    int64_t cap1 = (int64_t)ctx->sm_count * dm::blocks_per_sm(lsh, 1, bbit, wpb, smem);
     int grid = (int)(blocks < cap0 ? blocks : cap0);
     int grid_general = (int)(blocks < cap1 ? blocks : cap1);
-    return cuda_fail(dm::launch_sketch(p, bbit, ctx->counters != nullptr, grid, grid_general, st));
+    return cuda_fail(dm::launch_sets(p, lsh, bbit, ctx->counters != nullptr, grid, grid_general, st));
+}
+
+int run_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+               int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_words,
+               uint64_t *out_keys, cudaStream_t st, void *queue = nullptr) {
+    return run_sets(ctx, indptr, indices, weights, n_sets, false, k, 0, b, seed, out_words, out_keys, nullptr,
+                    st, queue);
 }
 
 }  // namespace
@@ -243,9 +265,8 @@ int dm_sketch_bbit(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
 
 int dm_lsh(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
            int64_t n_sets, int32_t L, int32_t K, uint64_t seed, uint32_t *out, void *stream) {
-    (void)ctx; (void)indptr; (void)indices; (void)weights; (void)n_sets; (void)L; (void)K;
-    (void)seed; (void)out; (void)stream;
-    return DM_EINVAL;   // not built yet
+    return run_sets(ctx, indptr, indices, weights, n_sets, true, L, K, 0, seed, nullptr, nullptr, out,
+                    (cudaStream_t)stream);
 }
 
 int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
@@ -371,6 +392,10 @@ int dm_set_option(dm_ctx *ctx, int option, int64_t value) {
         case DM_OPT_FORM:
             if (value < 0 || value > 1) return DM_EINVAL;
             ctx->form = (int)value;
+            return DM_OK;
+        case DM_OPT_LSH_PHI0:
+            if (value < 1 || value > 1024 * 1024) return DM_EINVAL;
+            ctx->phi0_lsh = (float)value / 1024.0f;
             return DM_OK;
         case DM_OPT_WARPS_PER_BLOCK:
             if (value < 0 || value > 8) return DM_EINVAL;   // kernels are built for <= 256 threads

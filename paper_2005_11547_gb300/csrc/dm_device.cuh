@@ -114,6 +114,7 @@ struct PassCut {
     uint64_t gm1;      // of theta_p
     uint64_t gfl_lo;   // of theta_{p-1} (0 on the first pass)
     uint32_t cthr;     // bits(theta_p): kept iff code(rank) < cthr
+    uint32_t cthr_lo;  // bits(theta_{p-1}) (0 on the first pass): darts below it were seen before
 };
 
 // Rows [rlo, rhi) of region (nu, rho) that the pass visits.

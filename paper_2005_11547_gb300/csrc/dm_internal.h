@@ -27,23 +27,26 @@ struct SketchParams {
     unsigned long long *counters;   // optional work counters (4)
     int32_t warp_bytes;   // dynamic shared memory per warp (general kernel)
     int32_t warp_bytes_fast;  // dynamic shared memory per warp (fast kernel)
+    int32_t sink_bytes;   // leading part of a warp's shared memory that holds the sink
     int32_t warps_per_block;
     int32_t *queue;             // sets deferred to the general kernel (capacity n_sets)
     unsigned int *queue_count;  // number of queued sets; followed by the two work counters
     unsigned int *work_next;    // = queue_count + 1: next work item of the fast / general kernel
 };
 
-// Per-warp shared memory of the general and fast sketch kernels.
-size_t sketch_warp_bytes(int k);
-size_t fast_warp_bytes(int k);
+// Shared memory per warp of the fast (mode 0) or general (mode 1) kernel, and of its sink
+// (k buckets of minima, or L buckets of bottom-K candidates for LSH).
+size_t warp_bytes(bool lsh, int k, int K, int mode);
+size_t sink_bytes(bool lsh, int k, int K);
+
+// Resident blocks per SM of a kernel.
+int blocks_per_sm(bool lsh, int mode, bool bbit, int warps_per_block, size_t smem);
 
 cudaError_t upload_poisson_table(const uint32_t *T);
-// Resident blocks per SM of the fast (mode 0) or general (mode 1) kernel.
-int sketch_blocks_per_sm(int mode, bool bbit, int warps_per_block, size_t smem);
 
-// Zeroes the queue and work counters, then launches the fast kernel over all sets and the general
-// kernel over the sets it queued, all on stream st.
-cudaError_t launch_sketch(const SketchParams &p, bool bbit, bool count, int grid_fast, int grid_general,
-                          cudaStream_t st);
+// Zeroes the queue and work counters, then launches the fast kernel over all sets and the
+// general kernel over the sets it queued, all on stream st.
+cudaError_t launch_sets(const SketchParams &p, bool lsh, bool bbit, bool count, int grid_fast, int grid_general,
+                        cudaStream_t st);
 
 }  // namespace dm

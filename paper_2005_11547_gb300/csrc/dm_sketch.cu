@@ -1,22 +1,28 @@
-// DartMinHash sketch kernel for sm_103a: one warp per weighted set.
+// DartMinHash kernels for sm_103a: one warp per weighted set.
 //
-// Per set (Theorem 1 of Christiani, arXiv 2005.11547): compute ||x||_1, set the rank limit
-// theta = phi0 / ||x||_1, run DartHash (Algorithm 1) for darts of rank < theta, hash each
-// kept dart to one of k buckets and keep the minimum key per bucket; while a bucket is
-// empty, double theta and enumerate only the areas that reach above the previous limit.
+// Per set (Christiani, arXiv 2005.11547, Theorem 1): compute ||x||_1, set the rank limit
+// theta = phi0 / ||x||_1, run DartHash (Algorithm 1) for darts of rank < theta and hand every
+// kept dart to a sink; while the sink is not filled, double theta and enumerate only the areas
+// that reach above the previous limit (the band).
+//   * SketchSink: the dart is hashed to one of k buckets, the bucket keeps the minimum key
+//     (Theorem 1's k independent minhashes; b-bit packing in the epilogue, Section 1.1).
+//   * LshSink: the dart is hashed to one of L buckets, the bucket keeps its K smallest keys,
+//     and table l's value is a hash of them in increasing order ((L, K) LSH, Section 3).
 //
 // GPU mapping
 //  * Persistent warps claim sets from a global counter, so a set that needs a second pass
 //    never holds idle warps of its block.
+//  * Two kernels per call.  The fast kernel runs passes whose limit is below 1 (rank region 0
+//    only: each element's areas are a 1-D sequence of rows) in 32-bit arithmetic; a set that
+//    needs anything else is appended to a device queue that the general kernel (all regions,
+//    64-bit) then computes from its first pass.  The output does not depend on the limits, so
+//    both give the same bits.
 //  * Elements are taken 32 at a time (a tile, one lane each).  Each lane computes its
-//    element's area count for this pass in closed form; a warp scan flattens the tile's
-//    areas and every lane walks a contiguous, equal share of them, so lanes stay busy no
-//    matter how unequal the element weights are.
-//  * Each area costs one hash (its Poisson count X).  A lane then emits the area's darts one
-//    per iteration into a 128-entry shared-memory dart queue (position = rank of the lane
-//    in a ballot), and whenever 32 or more darts are queued the warp evaluates them
-//    together, so the variable Poisson counts never diverge the warp.
-//  * A kept dart's key is atomically min-ed into the set's k buckets in shared memory.
+//    element's area count for the pass in closed form; a warp scan flattens the tile's areas
+//    and every lane walks a contiguous, equal share of them.
+//  * Each area costs one hash (its Poisson count X).  Darts are written to a 128-entry
+//    shared-memory queue of self-contained records and evaluated 64 at a time (two per lane),
+//    so the variable Poisson counts do not diverge the warp.
 #include "dm_device.cuh"
 #include "dm_internal.h"
 
@@ -28,34 +34,9 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kQueue = 128;        // dart records per warp
 constexpr int kMaxPasses = 21;     // phi0 * 2^20 at most (Theorem 1's loop limit)
 constexpr int kDefer = -1;         // a pass the fast kernel leaves to the general kernel
-
-size_t sketch_warp_bytes(int k) {
-    size_t b = (size_t)k * 8          // bucket minima
-             + 2 * kQueue * 8         // dart queue: dart counter, rank base | vmax
-             + 3 * 32 * 8             // tile: element hash, F, offset
-             + 32 * 4                 // tile: nu_top
-             + kQueue * 2;            // dart queue: shift and scale of the rank
-    return (b + 15) & ~(size_t)15;
-}
-
-struct WarpMem {
-    uint64_t *slots, *dq_c, *dq_p, *te, *tF, *toff;
-    int *tnu;
-    uint16_t *dq_m;
-};
-
-__device__ __forceinline__ WarpMem carve(unsigned char *base, int k) {
-    WarpMem m;
-    m.slots = reinterpret_cast<uint64_t *>(base);
-    m.dq_c = m.slots + k;
-    m.dq_p = m.dq_c + kQueue;
-    m.te = m.dq_p + kQueue;
-    m.tF = m.te + 32;
-    m.toff = m.tF + 32;
-    m.tnu = reinterpret_cast<int *>(m.toff + 32);
-    m.dq_m = reinterpret_cast<uint16_t *>(m.tnu + 32);
-    return m;
-}
+constexpr int kRowTab = 40;        // fast path: rows of nu = 0..38 (+1 pad)
+constexpr int kOverflow = 64;      // LSH: appends past a full bucket within one batch
+constexpr uint64_t kRMask = ((1ull << 55) - 1) & ~(uint64_t)kUMask;
 
 __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
 #pragma unroll
@@ -66,215 +47,216 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
     return v;
 }
 
-// ------------------------------------------------------------------------------------------
-// Dart queue.  A record holds the dart counter c = a + gamma (j + 1) of dart j of area a,
-// pv = pb | vmax (the rank base pb is a multiple of 2^24, so its low 24 bits carry the weight
-// threshold) and meta = sh | S << 6, so that the dart has
-//   d = mix64(c),  u = d >> 40,  v = (d >> 16) & (2^24 - 1),
-//   rank = (pb + (u << sh)) 2^-S,  weight test v <= vmax.
-// ------------------------------------------------------------------------------------------
 struct Queue {
     uint32_t tail, head;
 };
 
-__device__ __forceinline__ uint32_t pack_meta(int sh, int S) { return (uint32_t)sh | ((uint32_t)S << 6); }
+// ==========================================================================================
+// Sinks
+// ==========================================================================================
+size_t sketch_sink_bytes(int k) { return ((size_t)k * 8 + 15) & ~(size_t)15; }
 
-// Evaluate one queued dart; returns whether it is kept, with its bucket and key.  RHO0: every
-// queued dart has rank shift sh = 0 (rank region 0), so P = pb | u.
-template <bool RHO0>
-__device__ __forceinline__ bool dart_eval(const WarpMem &m, uint32_t pos, uint32_t k, uint32_t cthr,
-                                          uint32_t &slot, uint64_t &key) {
-    const uint32_t i = pos & (kQueue - 1);
-    const uint64_t pv = m.dq_p[i];
-    const uint32_t meta = m.dq_m[i];
-    const uint64_t d = mix64(m.dq_c[i]);
-    const uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
-    const uint64_t P = RHO0 ? ((pv & ~(uint64_t)kUMask) | u)
-                            : (pv & ~(uint64_t)kUMask) + ((uint64_t)u << (meta & 63));
-    // binary32 code of rank = P 2^-S rounded toward zero: exact u64 -> f32 conversion in
-    // round-toward-zero mode, then the exponent lowered by S
-    const uint32_t code = P ? __float_as_uint(__ull2float_rz(P)) - ((meta >> 6) << 23) : 0u;
-    if (v > ((uint32_t)pv & kUMask) || code >= cthr) return false;
-    const uint64_t qh = mix64(d ^ kSlotSalt);
-    slot = fastrange32((uint32_t)(qh >> 32), k);
-    key = ((uint64_t)code << 32) | (uint32_t)qh;
-    return true;
+size_t lsh_sink_bytes(int L, int K) {
+    size_t B = 2 * (size_t)K;
+    size_t b = (size_t)L * 8 * (B + 1)           // candidate buffers and thresholds
+             + (size_t)kOverflow * 8               // overflow keys
+             + (size_t)L * 4                       // counts
+             + 16                                  // overflow count
+             + (size_t)kOverflow * 2;              // overflow buckets
+    return (b + 15) & ~(size_t)15;
 }
 
-// Evaluate up to 64 queued darts, two per lane.
-template <bool COUNT, bool RHO0>
-__device__ __forceinline__ void drain(int n, Queue &q, const WarpMem &m, int lane, uint32_t k, uint32_t cthr,
-                                      unsigned long long &kept) {
-    uint32_t s0 = 0, s1 = 0;
-    uint64_t k0 = 0, k1 = 0;
-    const bool e0 = lane < n && dart_eval<RHO0>(m, q.head + lane, k, cthr, s0, k0);
-    const bool e1 = lane + 32 < n && dart_eval<RHO0>(m, q.head + 32 + lane, k, cthr, s1, k1);
-    if (e0) atomicMin(reinterpret_cast<unsigned long long *>(&m.slots[s0]), (unsigned long long)k0);
-    if (e1) atomicMin(reinterpret_cast<unsigned long long *>(&m.slots[s1]), (unsigned long long)k1);
-    if (COUNT) kept += (unsigned long long)e0 + (unsigned long long)e1;
-    q.head += (uint32_t)n;
-    __syncwarp();
-}
+// k buckets, each the minimum key of the darts hashed to it (Theorem 1).
+struct SketchSink {
+    uint64_t *slots;
+    uint32_t k;
+    static constexpr bool kLowerCut = false;      // min is idempotent: band overlap is harmless
 
-// Emission state of one lane: the current area's remaining darts.
-struct Emit {
-    uint64_t c;       // counter of the next dart of the current area
-    uint64_t pv;
-    uint32_t meta;
-    int rem;          // darts of the current area not yet emitted
+    __device__ void bind(unsigned char *base, const SketchParams &p) {
+        slots = reinterpret_cast<uint64_t *>(base);
+        k = (uint32_t)p.k;
+    }
+    __device__ void reset(int lane) {
+        for (uint32_t j = lane; j < k; j += 32) slots[j] = ~0ull;
+        __syncwarp();
+    }
+    __device__ __forceinline__ void put(uint64_t qh, uint32_t code) {
+        const uint32_t slot = fastrange32((uint32_t)(qh >> 32), k);
+        atomicMin(reinterpret_cast<unsigned long long *>(&slots[slot]),
+                  (unsigned long long)(((uint64_t)code << 32) | (uint32_t)qh));
+    }
+    __device__ __forceinline__ void after_batch(int) {}
+    __device__ bool filled(int lane) {
+        bool empty = false;
+        for (uint32_t j = lane; j < k; j += 32) empty |= (slots[j] == ~0ull);
+        return !__any_sync(kFull, empty);
+    }
+    __device__ void clear_to_error(int lane) {
+        for (uint32_t j = lane; j < k; j += 32) slots[j] = ~0ull;
+        __syncwarp();
+    }
+    template <bool BBIT>
+    __device__ void finish(const SketchParams &p, int64_t set, bool err, int lane) {
+        if (p.out_keys)
+            for (uint32_t j = lane; j < k; j += 32) p.out_keys[set * (int64_t)k + j] = slots[j];
+        if (!BBIT) return;
+        const int b = p.b;
+        const uint64_t bmask = (1ull << b) - 1;
+        uint64_t *ow = p.out_words + set * (int64_t)p.words;
+        if (err) {
+            for (int wd = lane; wd < p.words; wd += 32) ow[wd] = ~0ull;   // error rows are all ones
+        } else if (b == 1) {
+            for (uint32_t j0 = 0; j0 < k; j0 += 64) {
+                uint32_t j1 = j0 + lane, j2 = j0 + 32 + lane;
+                bool b1 = j1 < k && (mix64(slots[j1] ^ kBbitSalt) & 1);
+                bool b2 = j2 < k && (mix64(slots[j2] ^ kBbitSalt) & 1);
+                unsigned lo = __ballot_sync(kFull, b1), hi = __ballot_sync(kFull, b2);
+                if (lane == 0) ow[j0 >> 6] = (uint64_t)lo | ((uint64_t)hi << 32);
+            }
+        } else {
+            const int g = 64 / b;                    // slots per word, 2..32
+            for (uint32_t j0 = 0; j0 < k; j0 += 32) {
+                uint32_t j = j0 + lane;
+                uint64_t v = 0;
+                if (j < k) v = (mix64(slots[j] ^ kBbitSalt) & bmask) << ((j * (uint32_t)b) & 63);
+                for (int o = 1; o < g; o <<= 1) v |= __shfl_xor_sync(kFull, v, o);
+                if ((lane & (g - 1)) == 0 && j < k) ow[(j * (uint32_t)b) >> 6] = v;
+            }
+        }
+    }
 };
 
-// One emission round: every lane with a pending dart appends it to the queue (slot = rank of
-// the lane among emitting lanes), then full batches are evaluated.
-template <bool COUNT, bool RHO0>
-__device__ __forceinline__ void emit_round(Emit &em, Queue &q, const WarpMem &m, int lane, unsigned lt_mask,
-                                           uint32_t k, uint32_t cthr, unsigned long long &kept) {
-    const bool has = em.rem > 0;
-    const unsigned bal = __ballot_sync(kFull, has);
-    if (has) {
-        const uint32_t i = (q.tail + __popc(bal & lt_mask)) & (kQueue - 1);
-        m.dq_c[i] = em.c;
-        m.dq_p[i] = em.pv;
-        m.dq_m[i] = (uint16_t)em.meta;
-        em.c += kGolden;
-        --em.rem;
+// L buckets, each the K smallest keys of the darts hashed to it ((L, K) LSH).  A bucket keeps
+// up to B = 2K candidates and a threshold tau (its K-th smallest key after the last
+// compaction; keys >= tau can never enter the bottom K).  Appends past B go to an overflow
+// list; after each batch, buckets that filled up are compacted to their K smallest keys.
+// Band passes must not add a dart twice, so darts below the previous limit are cut.
+struct LshSink {
+    uint64_t *buf, *tau, *ovf_k;
+    uint32_t *cnt, *ovf_n;
+    uint16_t *ovf_b;
+    uint32_t L, K, B;
+    static constexpr bool kLowerCut = true;
+
+    __device__ void bind(unsigned char *base, const SketchParams &p) {
+        L = (uint32_t)p.k;
+        K = (uint32_t)p.K;
+        B = 2 * K;
+        buf = reinterpret_cast<uint64_t *>(base);
+        tau = buf + (size_t)L * B;
+        ovf_k = tau + L;
+        cnt = reinterpret_cast<uint32_t *>(ovf_k + kOverflow);
+        ovf_n = cnt + L;
+        ovf_b = reinterpret_cast<uint16_t *>(ovf_n + 4);
     }
-    q.tail += __popc(bal);
-    __syncwarp();
-    if (q.tail - q.head >= 64) drain<COUNT, RHO0>(64, q, m, lane, k, cthr, kept);
-}
-
-// ------------------------------------------------------------------------------------------
-// Element setup shared by both walks: weight geometry and element hash for one tile.
-// ------------------------------------------------------------------------------------------
-__device__ __forceinline__ bool element_setup(const SketchParams &p, int64_t pos, int64_t end, int &nutop,
-                                              uint64_t &F, uint64_t &e) {
-    nutop = -1;
-    F = 0;
-    e = 0;
-    if (pos >= end) return true;
-    nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F);
-    if (nutop == -2) return false;
-    if (nutop >= 0) e = mix64(p.sigma + kGolden * ((uint64_t)p.indices[pos] + 1));
-    return true;
-}
-
-__device__ __forceinline__ uint64_t publish_tile(const WarpMem &m, int lane, int nutop, uint64_t F, uint64_t e,
-                                                 uint64_t n_el) {
-    uint64_t incl = warp_incl_scan(n_el, lane);
-    m.te[lane] = e;
-    m.tF[lane] = F;
-    m.tnu[lane] = n_el ? nutop : -1;
-    m.toff[lane] = incl - n_el;
-    __syncwarp();
-    return __shfl_sync(kFull, incl, 31);
-}
-
-__device__ __forceinline__ int tile_element(const WarpMem &m, uint64_t idx) {
-    int el = 0;                               // last element whose offset is <= idx
-#pragma unroll
-    for (int step = 16; step; step >>= 1) {
-        int c = el + step;
-        if (c < 32 && m.toff[c] <= idx) el = c;
+    __device__ void reset(int lane) {
+        for (uint32_t b = lane; b < L; b += 32) {
+            cnt[b] = 0;
+            tau[b] = ~0ull;
+        }
+        if (lane == 0) *ovf_n = 0;
+        __syncwarp();
     }
-    return el;
-}
+    __device__ __forceinline__ void put(uint64_t qh, uint32_t code) {
+        const uint32_t b = fastrange32((uint32_t)(qh >> 32), L);
+        const uint64_t key = ((uint64_t)code << 32) | (uint32_t)qh;
+        if (key >= tau[b]) return;
+        const uint32_t pos = atomicAdd(&cnt[b], 1u);
+        if (pos < B) {
+            buf[(size_t)b * B + pos] = key;
+        } else {
+            const uint32_t o = atomicAdd(ovf_n, 1u);       // < kOverflow: a batch has <= 64 darts
+            ovf_k[o] = key;
+            ovf_b[o] = (uint16_t)b;
+        }
+    }
+    // Sort a bucket's candidates, merge its overflow entries and keep the K smallest.
+    __device__ void compact(uint32_t b, uint32_t no) {
+        uint64_t *v = buf + (size_t)b * B;
+        uint32_t n = min(cnt[b], B);
+        for (uint32_t i = 1; i < n; ++i) {               // insertion sort
+            uint64_t x = v[i];
+            uint32_t j = i;
+            while (j > 0 && v[j - 1] > x) { v[j] = v[j - 1]; --j; }
+            v[j] = x;
+        }
+        if (n > K) n = K;
+        for (uint32_t o = 0; o < no; ++o) {
+            if (ovf_b[o] != b) continue;
+            uint64_t x = ovf_k[o];
+            if (n == K && x >= v[K - 1]) continue;
+            uint32_t j = n < K ? n++ : K - 1;
+            while (j > 0 && v[j - 1] > x) { v[j] = v[j - 1]; --j; }
+            v[j] = x;
+        }
+        cnt[b] = n;
+        if (n == K) tau[b] = v[K - 1];
+    }
+    __device__ void after_batch(int lane) {
+        const uint32_t no = *ovf_n;
+        bool need = no > 0;
+        for (uint32_t b = lane; b < L && !need; b += 32) need = cnt[b] >= B;
+        if (!__any_sync(kFull, need)) return;
+        for (uint32_t b = lane; b < L; b += 32) {
+            bool hit = cnt[b] >= B;
+            for (uint32_t o = 0; o < no && !hit; ++o) hit = ovf_b[o] == b;
+            if (hit) compact(b, no);
+        }
+        __syncwarp();
+        if (lane == 0) *ovf_n = 0;
+        __syncwarp();
+    }
+    __device__ bool filled(int lane) {
+        bool lack = false;
+        for (uint32_t b = lane; b < L; b += 32) lack |= cnt[b] < K;
+        return !__any_sync(kFull, lack);
+    }
+    __device__ void clear_to_error(int) {}
+    template <bool BBIT>
+    __device__ void finish(const SketchParams &p, int64_t set, bool err, int lane) {
+        uint32_t *o = p.out_lsh + set * (int64_t)L;
+        for (uint32_t b = lane; b < L; b += 32) {
+            if (err || cnt[b] < K) {                     // error, or a set with no positive weight
+                o[b] = 0xFFFFFFFFu;
+                continue;
+            }
+            compact(b, 0);                               // sorted, exactly K
+            const uint64_t *v = buf + (size_t)b * B;
+            uint64_t h = kLshInit;
+            for (uint32_t m = 0; m < K; ++m) h = mix64(h ^ v[m]);
+            o[b] = (uint32_t)(h >> 32);
+        }
+    }
+};
 
-// ------------------------------------------------------------------------------------------
-// Fast walk for passes whose limit is below 1 (rho_top = rho_lo = 0): every region is one
-// column (w = 0) of rows [rlo(nu), rhi(nu)) with rlo = floor(g_prev 2^nu) (0 on the first
-// pass) and rhi = ceil(g 2^nu), so an element's areas form a 1-D sequence.  Tiles whose
-// elements all have nu_top <= 31 run it in 32-bit arithmetic: then
-// floor(G / 2^(64 - nu)) = hi32(G) >> (32 - nu), the element's area count is
+// ==========================================================================================
+// Fast path: passes with a rank limit below 1.  Every region (nu, 0) is one column of rows
+// [rlo(nu), rhi(nu)) with rlo = floor(g_prev 2^nu) (0 on the first pass) and rhi =
+// ceil(g 2^nu), so an element's areas form a 1-D sequence.  For tiles whose elements all have
+// nu_top <= 31, floor(G / 2^(64 - nu)) = hi32(G) >> (32 - nu), the element's area count is
 // 1 + nu_top + sum_{nu=1..nu_top} (floor(gm1 / 2^(64-nu)) - floor(gfl_prev / 2^(64-nu))) with
 // sum_{nu=1..n} floor(G / 2^(64-nu)) = 2H - popc(H), H = floor(G / 2^(64-n)), and the area
 // counter e + gamma (nu 2^58 + r + 1) = e + gamma + gamma r + ((21 nu mod 64) << 58)
-// (gamma mod 64 = 21).
-struct Walk0S {
-    int el, nu, nutop;
-    uint32_t r, rhi, vmax, g_hi, glo_hi;
-    uint64_t e, F, ctr;
-
-    __device__ static uint32_t rows_hi(uint32_t g_hi, int nu) { return nu ? (g_hi >> (32 - nu)) + 1u : 1u; }
-    __device__ static uint32_t rows_lo(uint32_t glo_hi, int nu) { return nu ? (glo_hi >> (32 - nu)) : 0u; }
-    __device__ static uint32_t ssum(uint32_t G_hi, int n) {
-        if (n <= 0) return 0;
-        uint32_t H = G_hi >> (32 - n);
-        return 2 * H - (uint32_t)__popc(H);
-    }
-    __device__ static uint32_t count(int nutop, const PassCut &pc) {
-        return 1u + (uint32_t)nutop + ssum((uint32_t)(pc.gm1 >> 32), nutop) - ssum((uint32_t)(pc.gfl_lo >> 32), nutop);
-    }
-    __device__ void region() {
-        r = rows_lo(glo_hi, nu);
-        rhi = rows_hi(g_hi, nu);
-        vmax = (nu == nutop) ? (uint32_t)(F >> 40) : kUMask;
-        ctr = e + kGolden + kGolden * (uint64_t)r + ((uint64_t)((21u * (uint32_t)nu) & 63u) << 58);
-    }
-    __device__ void load(const WarpMem &m) {
-        e = m.te[el];
-        F = m.tF[el];
-        nutop = m.tnu[el];
-    }
-    __device__ void locate(uint32_t idx, const WarpMem &m, const PassCut &pc) {
-        g_hi = (uint32_t)(pc.gm1 >> 32);
-        glo_hi = (uint32_t)(pc.gfl_lo >> 32);
-        el = tile_element(m, idx);
-        load(m);
-        uint32_t li = idx - (uint32_t)m.toff[el];
-        for (nu = 0;; ++nu) {
-            uint32_t rows = rows_hi(g_hi, nu) - rows_lo(glo_hi, nu);
-            if (li < rows) break;
-            li -= rows;
-        }
-        region();
-        r += li;
-        ctr += kGolden * (uint64_t)li;
-    }
-    __device__ uint64_t pv() const { return ((uint64_t)r << 24) | vmax; }
-    __device__ uint32_t meta() const { return pack_meta(0, nu + 24); }
-    __device__ void advance(const WarpMem &m) {
-        ++r;
-        ctr += kGolden;
-        if (r != rhi) return;
-        if (++nu > nutop) {
-            nu = 0;
-            do { ++el; } while (el < 32 && m.tnu[el] < 0);
-            if (el >= 32) return;
-            load(m);
-        }
-        region();
-    }
-};
-
-// ------------------------------------------------------------------------------------------
-// Fast-kernel batch emission.  Per tile, every lane walks an equal share of the areas; in each
-// iteration every lane hashes one area, and the darts of all 32 areas are written to the
-// queue at once (positions from a ballot prefix sum of X < 16), so the warp spends exactly one
-// iteration per area slot.  A record is 16 bytes: the dart counter c and
-// pvs = r << 24 | vmax | S << 57 (r < 2^31 in the 32-bit walk), rank = (r 2^24 + u) 2^-S.
-// ------------------------------------------------------------------------------------------
-constexpr int kFastQueue = 128;
-constexpr int kRowTab = 40;                       // nu = 0..38 (+1 pad)
-constexpr uint64_t kRMask = ((1ull << 55) - 1) & ~(uint64_t)kUMask;
-
+// (gamma mod 64 = 21).  Other tiles send the set to the general kernel.
+//
+// In each iteration every lane hashes one area and the darts of all 32 areas are written to
+// the queue at once (positions from a ballot prefix sum of X < 16), so the warp spends one
+// iteration per area slot.  A record is 16 bytes: the dart counter c = a + gamma (j + 1) and
+// pvs = r << 24 | vmax | S << 57 (r < 2^31), rank = (r 2^24 + u) 2^-S.
+// ==========================================================================================
 struct FastMem {
-    uint64_t *slots, *fq_c, *fq_p, *te;
+    uint64_t *fq_c, *fq_p, *te;
     uint32_t *tv, *toff, *rlo, *rhi;
     int *tnu;
 };
 
-size_t fast_warp_bytes(int k) {
-    size_t b = (size_t)k * 8 + 2 * kFastQueue * 8 + 32 * 8 + 3 * 32 * 4 + 2 * kRowTab * 4;
-    return (b + 15) & ~(size_t)15;
-}
+constexpr size_t kFastPathBytes = 2 * kQueue * 8 + 32 * 8 + 3 * 32 * 4 + 2 * kRowTab * 4;
 
-__device__ __forceinline__ FastMem carve_fast(unsigned char *base, int k) {
+__device__ __forceinline__ FastMem carve_fast(unsigned char *base) {
     FastMem m;
-    m.slots = reinterpret_cast<uint64_t *>(base);
-    m.fq_c = m.slots + k;
-    m.fq_p = m.fq_c + kFastQueue;
-    m.te = m.fq_p + kFastQueue;
+    m.fq_c = reinterpret_cast<uint64_t *>(base);
+    m.fq_p = m.fq_c + kQueue;
+    m.te = m.fq_p + kQueue;
     m.tv = reinterpret_cast<uint32_t *>(m.te + 32);
     m.toff = m.tv + 32;
     m.tnu = reinterpret_cast<int *>(m.toff + 32);
@@ -283,38 +265,40 @@ __device__ __forceinline__ FastMem carve_fast(unsigned char *base, int k) {
     return m;
 }
 
-__device__ __forceinline__ bool fast_eval(const FastMem &m, uint32_t pos, uint32_t k, uint32_t cthr,
-                                          uint32_t &slot, uint64_t &key) {
-    const uint32_t i = pos & (kFastQueue - 1);
+// Evaluate one queued dart: weight test, rank code, rank cut; returns the kept dart's code and
+// bucket/fingerprint hash.
+template <bool LOWER>
+__device__ __forceinline__ bool fast_eval(const FastMem &m, uint32_t pos, const PassCut &pc, uint32_t &code,
+                                          uint64_t &qh) {
+    const uint32_t i = pos & (kQueue - 1);
     const uint64_t pvs = m.fq_p[i];
     const uint64_t d = mix64(m.fq_c[i]);
     const uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
     const uint64_t P = (pvs & kRMask) | u;
-    const uint32_t code = P ? __float_as_uint(__ull2float_rz(P)) - ((uint32_t)(pvs >> 57) << 23) : 0u;
-    if (v > ((uint32_t)pvs & kUMask) || code >= cthr) return false;
-    const uint64_t qh = mix64(d ^ kSlotSalt);
-    slot = fastrange32((uint32_t)(qh >> 32), k);
-    key = ((uint64_t)code << 32) | (uint32_t)qh;
+    // binary32 code of rank = P 2^-S rounded toward zero: exact u64 -> f32 conversion in
+    // round-toward-zero mode, then the exponent lowered by S
+    code = P ? __float_as_uint(__ull2float_rz(P)) - ((uint32_t)(pvs >> 57) << 23) : 0u;
+    if (v > ((uint32_t)pvs & kUMask) || code >= pc.cthr) return false;
+    if (LOWER && code < pc.cthr_lo) return false;
+    qh = mix64(d ^ kSlotSalt);
     return true;
 }
 
-template <bool COUNT>
-__device__ __forceinline__ void fast_drain(int n, Queue &q, const FastMem &m, int lane, uint32_t k, uint32_t cthr,
-                                           unsigned long long &kept) {
-    uint32_t s0 = 0, s1 = 0;
-    uint64_t k0 = 0, k1 = 0;
-    const bool e0 = lane < n && fast_eval(m, q.head + lane, k, cthr, s0, k0);
-    const bool e1 = lane + 32 < n && fast_eval(m, q.head + 32 + lane, k, cthr, s1, k1);
-    if (e0) atomicMin(reinterpret_cast<unsigned long long *>(&m.slots[s0]), (unsigned long long)k0);
-    if (e1) atomicMin(reinterpret_cast<unsigned long long *>(&m.slots[s1]), (unsigned long long)k1);
+template <class Sink, bool COUNT>
+__device__ __forceinline__ void fast_drain(int n, Queue &q, const FastMem &m, Sink &sink, int lane,
+                                           const PassCut &pc, unsigned long long &kept) {
+    uint32_t c0 = 0, c1 = 0;
+    uint64_t q0 = 0, q1 = 0;
+    const bool e0 = lane < n && fast_eval<Sink::kLowerCut>(m, q.head + lane, pc, c0, q0);
+    const bool e1 = lane + 32 < n && fast_eval<Sink::kLowerCut>(m, q.head + 32 + lane, pc, c1, q1);
+    if (e0) sink.put(q0, c0);
+    if (e1) sink.put(q1, c1);
     if (COUNT) kept += (unsigned long long)e0 + (unsigned long long)e1;
     q.head += (uint32_t)n;
     __syncwarp();
+    sink.after_batch(lane);
 }
 
-// The 1-D walk of a rank-region-0 pass in 32-bit arithmetic (element nu_top <= 31): region nu
-// has rows [rlo[nu], rhi[nu]) from the pass table; the area counter is
-// e + gamma (nu 2^58 + r + 1) = e + gamma + gamma r + ((21 nu mod 64) << 58) (gamma mod 64 = 21).
 struct WalkF {
     int el, nu, nutop;
     uint32_t r, rhi, vtop;
@@ -364,14 +348,11 @@ struct WalkF {
     }
 };
 
-// One rank-region-0 pass of DartHash over the row in the fast kernel.  Returns 0, an error
-// code, or kDefer when a tile is outside the 32-bit walk's range.
-template <bool COUNT>
+// One rank-region-0 pass over the row.  Returns 0, an error code, or kDefer.
+template <class Sink, bool COUNT>
 __device__ int fast_pass(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc, const FastMem &m,
-                         int lane, unsigned long long *cnt) {
+                         Sink &sink, int lane, unsigned long long *cnt) {
     const unsigned lt = (1u << lane) - 1u;
-    const uint32_t k = (uint32_t)p.k;
-    // rows of region nu in this pass: [floor(g_prev 2^nu), ceil(g 2^nu))
     for (int nu = lane; nu < kRowTab; nu += 32) {
         int n = nu > kMaxRegion ? kMaxRegion : nu;
         m.rlo[nu] = n ? (uint32_t)min(pc.gfl_lo >> (64 - n), (uint64_t)0xFFFFFFFFu) : 0u;
@@ -389,8 +370,6 @@ __device__ int fast_pass(const SketchParams &p, int64_t beg, int64_t end, const 
         }
         if (__any_sync(kFull, nutop == -2)) return DM_ERANGE;
         if (!__all_sync(kFull, nutop <= 31)) return kDefer;
-        // element area count: 1 + nu_top + sum_{nu=1..nu_top} (hi32(gm1) >> (32-nu)) - (hi32(gfl) >> (32-nu)),
-        // each sum = 2H - popc(H) with H = hi32(G) >> (32 - nu_top)
         uint64_t n_el = 0;
         if (nutop >= 0) {
             n_el = 1 + (uint64_t)nutop;
@@ -431,31 +410,98 @@ __device__ int fast_pass(const SketchParams &p, int64_t beg, int64_t end, const 
             const uint32_t ex = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt) + 8 * __popc(b3 & lt);
             // write the darts in queue-sized pieces (one piece unless T is far above its mean)
             for (uint32_t done = 0; done < T;) {
-                const uint32_t room = kFastQueue - (q.tail - q.head);
+                const uint32_t room = kQueue - (q.tail - q.head);
                 const uint32_t lim = min(T - done, room);
                 uint32_t jlo = done > ex ? done - ex : 0u;
                 uint32_t jhi = done + lim > ex ? done + lim - ex : 0u;
                 if (jhi > (uint32_t)X) jhi = (uint32_t)X;
                 uint64_t c = a + kGolden * (uint64_t)(jlo + 1);
                 for (uint32_t j = jlo; j < jhi; ++j, c += kGolden) {
-                    const uint32_t i = (q.tail + ex + j - done) & (kFastQueue - 1);
+                    const uint32_t i = (q.tail + ex + j - done) & (kQueue - 1);
                     m.fq_c[i] = c;
                     m.fq_p[i] = pv;
                 }
                 q.tail += lim;
                 done += lim;
                 __syncwarp();
-                while (q.tail - q.head >= 64) fast_drain<COUNT>(64, q, m, lane, k, pc.cthr, cnt[2]);
+                while (q.tail - q.head >= 64) fast_drain<Sink, COUNT>(64, q, m, sink, lane, pc, cnt[2]);
             }
         }
     }
-    if (q.tail != q.head) fast_drain<COUNT>((int)(q.tail - q.head), q, m, lane, k, pc.cthr, cnt[2]);
+    if (q.tail != q.head) fast_drain<Sink, COUNT>((int)(q.tail - q.head), q, m, sink, lane, pc, cnt[2]);
     return 0;
 }
 
-// ------------------------------------------------------------------------------------------
-// General walk: regions (nu, rho), columns w and rows r.
-// ------------------------------------------------------------------------------------------
+// ==========================================================================================
+// General path: every region (nu, rho), columns w and rows r, in 64-bit arithmetic.  Each
+// lane hashes its next area once the darts of its previous one are queued and queues at most
+// one dart per round (slot = rank of the lane in a ballot).  A record holds the dart counter,
+// pv = pb | vmax (the rank base pb is a multiple of 2^24) and meta = sh | S << 6:
+// rank = (pb + (u << sh)) 2^-S.
+// ==========================================================================================
+struct GenMem {
+    uint64_t *dq_c, *dq_p, *te, *tF, *toff;
+    int *tnu;
+    uint16_t *dq_m;
+};
+
+constexpr size_t kGenPathBytes = 2 * kQueue * 8 + 3 * 32 * 8 + 32 * 4 + kQueue * 2;
+
+__device__ __forceinline__ GenMem carve_gen(unsigned char *base) {
+    GenMem m;
+    m.dq_c = reinterpret_cast<uint64_t *>(base);
+    m.dq_p = m.dq_c + kQueue;
+    m.te = m.dq_p + kQueue;
+    m.tF = m.te + 32;
+    m.toff = m.tF + 32;
+    m.tnu = reinterpret_cast<int *>(m.toff + 32);
+    m.dq_m = reinterpret_cast<uint16_t *>(m.tnu + 32);
+    return m;
+}
+
+__device__ __forceinline__ uint32_t pack_meta(int sh, int S) { return (uint32_t)sh | ((uint32_t)S << 6); }
+
+template <bool LOWER>
+__device__ __forceinline__ bool gen_eval(const GenMem &m, uint32_t pos, const PassCut &pc, uint32_t &code,
+                                         uint64_t &qh) {
+    const uint32_t i = pos & (kQueue - 1);
+    const uint64_t pv = m.dq_p[i];
+    const uint32_t meta = m.dq_m[i];
+    const uint64_t d = mix64(m.dq_c[i]);
+    const uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
+    const uint64_t P = (pv & ~(uint64_t)kUMask) + ((uint64_t)u << (meta & 63));
+    code = P ? __float_as_uint(__ull2float_rz(P)) - ((meta >> 6) << 23) : 0u;
+    if (v > ((uint32_t)pv & kUMask) || code >= pc.cthr) return false;
+    if (LOWER && code < pc.cthr_lo) return false;
+    qh = mix64(d ^ kSlotSalt);
+    return true;
+}
+
+template <class Sink, bool COUNT>
+__device__ __forceinline__ void gen_drain(int n, Queue &q, const GenMem &m, Sink &sink, int lane,
+                                          const PassCut &pc, unsigned long long &kept) {
+    uint32_t c0 = 0, c1 = 0;
+    uint64_t q0 = 0, q1 = 0;
+    const bool e0 = lane < n && gen_eval<Sink::kLowerCut>(m, q.head + lane, pc, c0, q0);
+    const bool e1 = lane + 32 < n && gen_eval<Sink::kLowerCut>(m, q.head + 32 + lane, pc, c1, q1);
+    if (e0) sink.put(q0, c0);
+    if (e1) sink.put(q1, c1);
+    if (COUNT) kept += (unsigned long long)e0 + (unsigned long long)e1;
+    q.head += (uint32_t)n;
+    __syncwarp();
+    sink.after_batch(lane);
+}
+
+__device__ __forceinline__ int tile_element(const GenMem &m, uint64_t idx) {
+    int el = 0;                               // last element whose offset is <= idx
+#pragma unroll
+    for (int step = 16; step; step >>= 1) {
+        int c = el + step;
+        if (c < 32 && m.toff[c] <= idx) el = c;
+    }
+    return el;
+}
+
 struct WalkG {
     int el, nu, rho, nutop;
     uint64_t w, r, ncols, rlo, rhi;
@@ -477,12 +523,12 @@ struct WalkG {
         packhi = ((uint64_t)nu << 58) | ((uint64_t)rho << 52);
     }
     __device__ void set_ctr() { ctr = e + kGolden * ((packhi | (w << nu) | r) + 1); }
-    __device__ void load(const WarpMem &m) {
+    __device__ void load(const GenMem &m) {
         e = m.te[el];
         F = m.tF[el];
         nutop = m.tnu[el];
     }
-    __device__ void locate(uint64_t idx, const WarpMem &m, const PassCut &pc) {
+    __device__ void locate(uint64_t idx, const GenMem &m, const PassCut &pc) {
         el = tile_element(m, idx);
         load(m);
         uint64_t li = idx - m.toff[el];
@@ -507,7 +553,7 @@ struct WalkG {
         return rbase + (r << (62 - nu)) + min(WT - (w << 24), (uint64_t)kUMask);
     }
     __device__ uint32_t meta() const { return pack_meta(38 - nu, 62 - rho); }
-    __device__ void advance(const WarpMem &m, const PassCut &pc) {
+    __device__ void advance(const GenMem &m, const PassCut &pc) {
         ++r;
         ctr += kGolden;
         if (r < rhi) return;
@@ -530,84 +576,82 @@ struct WalkG {
     }
 };
 
-// Emission loop over one tile with walk W (W::locate positions the walk at a lane's first
-// area, W::advance moves to the next): each lane hashes its next area once the darts of the
-// previous one are emitted, and emits at most one dart per round.
-template <class W, class Idx, bool COUNT, bool RHO0, class Adv>
-__device__ __forceinline__ void run_tile(W &s, Idx left, Adv advance, Queue &q, const WarpMem &m, int lane,
-                                         unsigned lt_mask, uint32_t k, uint32_t cthr, unsigned long long *cnt) {
-    Emit em;
-    em.rem = 0;
-    while (__any_sync(kFull, left > 0 || em.rem > 0)) {
-        if (em.rem == 0 && left > 0) {
-            const uint64_t a = mix64(s.ctr);
-            em.rem = poisson1((uint32_t)(a >> 32), c_pois);
-            em.c = a + kGolden;
-            em.pv = s.pv();
-            em.meta = s.meta();
-            if (COUNT) { cnt[0]++; cnt[1] += em.rem; }
-            if (--left) advance(s);
-        }
-        emit_round<COUNT, RHO0>(em, q, m, lane, lt_mask, k, cthr, cnt[2]);
-    }
-}
-
-// One pass of DartHash over the row; RHO0 passes have a rank limit below 1.  Returns 0 or an
-// error code.
-template <bool RHO0, bool COUNT>
-__device__ int darthash_pass(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc,
-                             const WarpMem &m, int lane, unsigned long long *cnt) {
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const uint32_t k = (uint32_t)p.k;
+// One pass over the row with the general walk.  Returns 0 or an error code.
+template <class Sink, bool COUNT>
+__device__ int gen_pass(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc, const GenMem &m,
+                        Sink &sink, int lane, unsigned long long *cnt) {
+    const unsigned lt = (1u << lane) - 1u;
     Queue q = {0, 0};
     for (int64_t tile = beg; tile < end; tile += 32) {
-        int nutop;
-        uint64_t F, e;
-        const bool ok = element_setup(p, tile + lane, end, nutop, F, e);
-        if (__any_sync(kFull, !ok)) return DM_ERANGE;
-        if (RHO0) {
-            // 32-bit walk; a tile outside its range sends the whole set to the general kernel
-            if (!__all_sync(kFull, nutop <= 31)) return kDefer;
-            const uint64_t total = publish_tile(m, lane, nutop, F, e, nutop >= 0 ? Walk0S::count(nutop, pc) : 0);
-            if (total == 0) continue;
-            if (total >= (1ull << 31)) return kDefer;
-            const uint32_t share = (uint32_t)((total + 31) >> 5);
-            const uint32_t lo = share * (uint32_t)lane;
-            uint32_t left = lo < (uint32_t)total ? min(share, (uint32_t)total - lo) : 0u;
-            Walk0S s;
-            if (left) s.locate(lo, m, pc);
-            run_tile<Walk0S, uint32_t, COUNT, RHO0>(s, left, [&](Walk0S &w) { w.advance(m); }, q, m, lane,
-                                                     lt_mask, k, pc.cthr, cnt);
-        } else {
-            const uint64_t total = publish_tile(m, lane, nutop, F, e, nutop >= 0 ? WalkG::count(nutop, F, pc) : 0);
-            if (total == 0) continue;
-            const uint64_t share = (total + 31) >> 5;
-            const uint64_t lo = share * lane;
-            uint64_t left = lo < total ? min(share, total - lo) : 0;
-            WalkG s;
-            if (left) s.locate(lo, m, pc);
-            run_tile<WalkG, uint64_t, COUNT, RHO0>(s, left, [&](WalkG &w) { w.advance(m, pc); }, q, m, lane,
-                                                    lt_mask, k, pc.cthr, cnt);
+        const int64_t pos = tile + lane;
+        int nutop = -1;
+        uint64_t F = 0, e = 0;
+        if (pos < end) {
+            nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F);
+            if (nutop >= 0) e = mix64(p.sigma + kGolden * ((uint64_t)p.indices[pos] + 1));
+        }
+        if (__any_sync(kFull, nutop == -2)) return DM_ERANGE;
+        const uint64_t n_el = nutop >= 0 ? WalkG::count(nutop, F, pc) : 0;
+        const uint64_t incl = warp_incl_scan(n_el, lane);
+        m.te[lane] = e;
+        m.tF[lane] = F;
+        m.tnu[lane] = n_el ? nutop : -1;
+        m.toff[lane] = incl - n_el;
+        __syncwarp();
+        const uint64_t total = __shfl_sync(kFull, incl, 31);
+        if (total == 0) continue;
+        const uint64_t share = (total + 31) >> 5;
+        const uint64_t lo = share * lane;
+        uint64_t left = lo < total ? min(share, total - lo) : 0;   // areas this lane still has to hash
+        WalkG s;
+        if (left) s.locate(lo, m, pc);
+        uint64_t c = 0, pv = 0;
+        uint32_t meta = 0;
+        int rem = 0;                                   // darts of the current area not yet queued
+        while (__any_sync(kFull, left > 0 || rem > 0)) {
+            if (rem == 0 && left > 0) {
+                const uint64_t a = mix64(s.ctr);
+                rem = poisson1((uint32_t)(a >> 32), c_pois);
+                c = a + kGolden;
+                pv = s.pv();
+                meta = s.meta();
+                if (COUNT) { cnt[0]++; cnt[1] += rem; }
+                if (--left) s.advance(m, pc);
+            }
+            const bool has = rem > 0;
+            const unsigned bal = __ballot_sync(kFull, has);
+            if (has) {
+                const uint32_t i = (q.tail + __popc(bal & lt)) & (kQueue - 1);
+                m.dq_c[i] = c;
+                m.dq_p[i] = pv;
+                m.dq_m[i] = (uint16_t)meta;
+                c += kGolden;
+                --rem;
+            }
+            q.tail += __popc(bal);
+            __syncwarp();
+            if (q.tail - q.head >= 64) gen_drain<Sink, COUNT>(64, q, m, sink, lane, pc, cnt[2]);
         }
     }
-    if (q.tail != q.head) drain<COUNT, RHO0>((int)(q.tail - q.head), q, m, lane, k, pc.cthr, cnt[2]);
+    if (q.tail != q.head) gen_drain<Sink, COUNT>((int)(q.tail - q.head), q, m, sink, lane, pc, cnt[2]);
     return 0;
 }
 
-// MODE 0 (fast): every pass whose rank limit is below 1 runs the 1-D walk; a set needing a
-// limit >= 1 is appended to the general queue and left to MODE 1.
-// MODE 1 (general): sets are taken from the queue and computed from the first pass with the
-// general walk.  Both give the same bits for a set (the output does not depend on the limits).
-// Warps are persistent and claim work items from a global counter.
-template <bool BBIT, bool COUNT, int MODE>
-__global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) sketch_kernel(const SketchParams p) {
+// ==========================================================================================
+// Kernel.  MODE 0 (fast): sets in order; passes with a limit >= 1, and tiles outside the
+// 32-bit walk, send the set to the queue.  MODE 1 (general): sets from the queue, every pass
+// with the general walk.  Warps are persistent and claim work items from a global counter.
+// ==========================================================================================
+template <class Sink, bool BBIT, bool COUNT, int MODE>
+__global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) set_kernel(const SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int wbytes = MODE == 0 ? p.warp_bytes_fast : p.warp_bytes;
-    WarpMem m = carve(smem + (size_t)wib * wbytes, p.k);
-    FastMem fm = carve_fast(smem + (size_t)wib * wbytes, p.k);
-    const uint32_t k = (uint32_t)p.k;
+    unsigned char *wbase = smem + (size_t)wib * (MODE == 0 ? p.warp_bytes_fast : p.warp_bytes);
+    Sink sink;
+    sink.bind(wbase, p);
+    const FastMem fm = carve_fast(wbase + p.sink_bytes);
+    const GenMem gm = carve_gen(wbase + p.sink_bytes);
     const int64_t n_work = MODE == 0 ? p.n_sets : (int64_t)*p.queue_count;
     unsigned int *next = p.work_next + MODE;
     for (;;) {
@@ -628,8 +672,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) sketch_kernel(const Sk
 #pragma unroll
         for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(kFull, l1, o);
         int err = __any_sync(kFull, bad) ? DM_EINVAL : 0;
-        for (uint32_t j = lane; j < k; j += 32) m.slots[j] = ~0ull;
-        __syncwarp();
+        sink.reset(lane);
         unsigned long long cnt[3] = {0, 0, 0};
         unsigned long long passes = 0;
         bool deferred = false;
@@ -638,6 +681,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) sketch_kernel(const Sk
             PassCut pc;
             pc.rho_lo = 0;
             pc.gfl_lo = 0;
+            pc.cthr_lo = 0;
             for (int pass = 0;; ++pass) {
                 if (pass == kMaxPasses) { err = DM_EOVERFLOW; break; }
                 RankCut rc;
@@ -646,19 +690,16 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) sketch_kernel(const Sk
                 pc.gm1 = rc.gm1;
                 pc.cthr = th;
                 if (MODE == 0 && pc.rho_top != 0) { deferred = true; break; }
-                // the fast kernel only runs rank-region-0 passes; the general kernel runs the
-                // general walk on every pass (it is correct for any limit)
-                err = MODE == 0 ? fast_pass<COUNT>(p, beg, end, pc, fm, lane, cnt)
-                                : darthash_pass<false, COUNT>(p, beg, end, pc, m, lane, cnt);
+                err = MODE == 0 ? fast_pass<Sink, COUNT>(p, beg, end, pc, fm, sink, lane, cnt)
+                                : gen_pass<Sink, COUNT>(p, beg, end, pc, gm, sink, lane, cnt);
                 ++passes;
                 if (err == kDefer) { err = 0; deferred = true; break; }
                 if (err) break;
-                bool empty = false;
-                for (uint32_t j = lane; j < k; j += 32) empty |= (m.slots[j] == ~0ull);
-                if (!__any_sync(kFull, empty)) break;
+                if (sink.filled(lane)) break;
                 // next band starts where this limit ended
                 pc.rho_lo = rc.g_one ? rc.rho_top + 1 : rc.rho_top;
                 pc.gfl_lo = rc.g_one ? 0 : rc.gfl;
+                pc.cthr_lo = th;
                 th = __float_as_uint(2.0f * __uint_as_float(th));
             }
         }
@@ -679,38 +720,9 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) sketch_kernel(const Sk
         }
         if (err) {
             if (lane == 0) set_status(p.status, err);
-            for (uint32_t j = lane; j < k; j += 32) m.slots[j] = ~0ull;
-            __syncwarp();
+            sink.clear_to_error(lane);
         }
-        // epilogue: keys and/or b-bit words
-        if (p.out_keys)
-            for (uint32_t j = lane; j < k; j += 32) p.out_keys[set * (int64_t)k + j] = m.slots[j];
-        if (BBIT) {
-            const int b = p.b;
-            const uint64_t bmask = (1ull << b) - 1;
-            uint64_t *ow = p.out_words + set * (int64_t)p.words;
-            if (err) {
-                // error rows are all ones, like the key rows
-                for (int wd = lane; wd < p.words; wd += 32) ow[wd] = ~0ull;
-            } else if (b == 1) {
-                for (uint32_t j0 = 0; j0 < k; j0 += 64) {
-                    uint32_t j1 = j0 + lane, j2 = j0 + 32 + lane;
-                    bool b1 = j1 < k && (mix64(m.slots[j1] ^ kBbitSalt) & 1);
-                    bool b2 = j2 < k && (mix64(m.slots[j2] ^ kBbitSalt) & 1);
-                    unsigned lo = __ballot_sync(kFull, b1), hi = __ballot_sync(kFull, b2);
-                    if (lane == 0) ow[j0 >> 6] = (uint64_t)lo | ((uint64_t)hi << 32);
-                }
-            } else {
-                const int g = 64 / b;                  // slots per word, 2..32
-                for (uint32_t j0 = 0; j0 < k; j0 += 32) {
-                    uint32_t j = j0 + lane;
-                    uint64_t v = 0;
-                    if (j < k) v = (mix64(m.slots[j] ^ kBbitSalt) & bmask) << ((j * (uint32_t)b) & 63);
-                    for (int o = 1; o < g; o <<= 1) v |= __shfl_xor_sync(kFull, v, o);
-                    if ((lane & (g - 1)) == 0 && j < k) ow[(j * (uint32_t)b) >> 6] = v;
-                }
-            }
-        }
+        sink.template finish<BBIT>(p, set, err != 0, lane);
         __syncwarp();
     }
 }
@@ -719,10 +731,15 @@ cudaError_t upload_poisson_table(const uint32_t *T) {
     return cudaMemcpyToSymbol(c_pois, T, 12 * sizeof(uint32_t));
 }
 
-template <bool BBIT, bool COUNT, int MODE>
+template <class Sink, bool BBIT, bool COUNT, int MODE>
+static const void *kernel_fn() {
+    return (const void *)set_kernel<Sink, BBIT, COUNT, MODE>;
+}
+
+template <class Sink, bool BBIT, bool COUNT, int MODE>
 static cudaError_t launch_t(const SketchParams &p, int grid, cudaStream_t st) {
     size_t smem = (size_t)(MODE == 0 ? p.warp_bytes_fast : p.warp_bytes) * p.warps_per_block;
-    auto fn = sketch_kernel<BBIT, COUNT, MODE>;
+    auto fn = set_kernel<Sink, BBIT, COUNT, MODE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -731,31 +748,41 @@ static cudaError_t launch_t(const SketchParams &p, int grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int MODE>
+template <class Sink, int MODE>
 static cudaError_t launch_mode(const SketchParams &p, bool bbit, bool count, int grid, cudaStream_t st) {
-    if (bbit) return count ? launch_t<true, true, MODE>(p, grid, st) : launch_t<true, false, MODE>(p, grid, st);
-    return count ? launch_t<false, true, MODE>(p, grid, st) : launch_t<false, false, MODE>(p, grid, st);
+    if (bbit) return count ? launch_t<Sink, true, true, MODE>(p, grid, st) : launch_t<Sink, true, false, MODE>(p, grid, st);
+    return count ? launch_t<Sink, false, true, MODE>(p, grid, st) : launch_t<Sink, false, false, MODE>(p, grid, st);
 }
 
-cudaError_t launch_sketch(const SketchParams &p, bool bbit, bool count, int grid_fast, int grid_general,
-                          cudaStream_t st) {
+cudaError_t launch_sets(const SketchParams &p, bool lsh, bool bbit, bool count, int grid_fast, int grid_general,
+                        cudaStream_t st) {
     // queue count and the two work counters are contiguous
     cudaError_t e = cudaMemsetAsync(p.queue_count, 0, 4 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    if ((e = launch_mode<0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
-    return launch_mode<1>(p, bbit, count, grid_general, st);
+    if (lsh) {
+        if ((e = launch_mode<LshSink, 0>(p, false, count, grid_fast, st)) != cudaSuccess) return e;
+        return launch_mode<LshSink, 1>(p, false, count, grid_general, st);
+    }
+    if ((e = launch_mode<SketchSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
+    return launch_mode<SketchSink, 1>(p, bbit, count, grid_general, st);
 }
 
-}  // namespace dm
+size_t warp_bytes(bool lsh, int k, int K, int mode) {
+    const size_t sink = lsh ? lsh_sink_bytes(k, K) : sketch_sink_bytes(k);
+    return sink + (mode == 0 ? kFastPathBytes : kGenPathBytes);
+}
 
-namespace dm {
-int sketch_blocks_per_sm(int mode, bool bbit, int warps_per_block, size_t smem) {
-    int nb = 0;
+size_t sink_bytes(bool lsh, int k, int K) { return lsh ? lsh_sink_bytes(k, K) : sketch_sink_bytes(k); }
+
+int blocks_per_sm(bool lsh, int mode, bool bbit, int warps_per_block, size_t smem) {
     const void *fn;
-    if (mode == 0) fn = bbit ? (const void *)sketch_kernel<true, false, 0> : (const void *)sketch_kernel<false, false, 0>;
-    else fn = bbit ? (const void *)sketch_kernel<true, false, 1> : (const void *)sketch_kernel<false, false, 1>;
+    if (lsh) fn = mode == 0 ? kernel_fn<LshSink, false, false, 0>() : kernel_fn<LshSink, false, false, 1>();
+    else if (mode == 0) fn = bbit ? kernel_fn<SketchSink, true, false, 0>() : kernel_fn<SketchSink, false, false, 0>();
+    else fn = bbit ? kernel_fn<SketchSink, true, false, 1>() : kernel_fn<SketchSink, false, false, 1>();
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * warps_per_block, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }
+
 }  // namespace dm

@@ -267,3 +267,15 @@ def test_golden_tiny_sketches(oracle_mod):
         for j, h in enumerate(c["keys"]):
             if h is not None:
                 assert int(out[j]) == int(h, 16), (c, j)
+
+
+def test_zipf_generator_is_deterministic_and_distinct():
+    b = workloads.zipf_batch(300, 5, 50, 1 << 16, 1.1, seed=7, threads=3)
+    b2 = workloads.zipf_batch(300, 5, 50, 1 << 16, 1.1, seed=7, threads=1)
+    assert (b.indices == b2.indices).all() and (b.weights == b2.weights).all()
+    lens = np.diff(b.indptr)
+    assert lens.min() >= 5 and lens.max() <= 50
+    for s in range(300):
+        row = b.indices[b.indptr[s]:b.indptr[s + 1]]
+        assert len(set(row.tolist())) == len(row)
+    assert (b.weights > 0.69).all() and (b.weights < 10 * np.log(1 + 1e6)).all()

@@ -11,6 +11,9 @@ same arrays.
                                                                    k = 256 and 1-bit
   W2  200,000 sets, d = 2^24, nnz = round(exp(ln 100 + 1.5 z)) clipped to [1, 100,000],
       weights lognormal(0, 1) rescaled per set so ||x||_1 = 10^U(-3, 3).          k = 1024
+  W3  1,000,000 tf-idf-like sets over d = 2^20: nnz ~ Uniform{200..2000}; tokens drawn from
+      Zipf(1.1) over the universe until nnz distinct elements appear; weight = log(1 + count)
+      x Uniform(1, 10) (token sampling in zipf_gen.c).                         L = 64, K = 8
   W4  request stream: Poisson arrivals at 50,000/s; nnz = min(100,000, floor(Pareto(1.2)))
       with x_m = 1; d = 2^24; weights Uniform(0, 5]; k uniform over {64, 256, 1024}.
 
@@ -19,9 +22,16 @@ and y_j = 1 - b on one fresh element j, with ||x||_1 = 1, so J(x, y) = b / (2 - 
 """
 from __future__ import annotations
 
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 @dataclass
@@ -123,6 +133,74 @@ def workload2(n: int = 200_000) -> Batch:
     sums = np.add.reduceat(z, ip[:-1])
     w = (z * np.repeat(target / sums, lens)).astype(np.float32)
     return Batch(ip, idx, w, "W2", dict(n=n, d=1 << 24, seed=1002))
+
+
+_gen_lock = threading.Lock()
+_gen_lib = None
+_alias_cache = {}
+
+
+def _zipf_lib():
+    """The tf-idf token sampler (zipf_gen.c), compiled in-tree on first use."""
+    global _gen_lib
+    with _gen_lock:
+        if _gen_lib is None:
+            src = os.path.join(_HERE, "zipf_gen.c")
+            out = os.path.join(_HERE, "_build", "libzipfgen.so")
+            os.makedirs(os.path.dirname(out), exist_ok=True)
+            if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+                tmp = out + f".tmp{os.getpid()}"
+                subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+                os.replace(tmp, out)
+            lib = ctypes.CDLL(out)
+            P = ctypes.c_void_p
+            lib.zipf_alias.argtypes = [ctypes.c_int64, ctypes.c_double, P, P]
+            lib.zipf_sets.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, ctypes.c_int64, P, P, P, P]
+            _gen_lib = lib
+        return _gen_lib
+
+
+def _zipf_tables(d: int, s: float):
+    key = (d, s)
+    if key not in _alias_cache:
+        prob = np.empty(d, dtype=np.float64)
+        alias = np.empty(d, dtype=np.int32)
+        assert _zipf_lib().zipf_alias(d, s, prob.ctypes.data, alias.ctypes.data) == 0
+        _alias_cache[key] = (prob, alias)
+    return _alias_cache[key]
+
+
+def zipf_batch(n: int, nnz_lo: int, nnz_hi: int, d: int, s: float, seed: int, threads: int | None = None,
+               name: str = "zipf") -> Batch:
+    """Sets of nnz ~ U{nnz_lo..nnz_hi} distinct elements drawn from Zipf(s) token streams,
+    weight = log(1 + count) x U(1, 10)."""
+    rng = _rng(seed)
+    lens = rng.integers(nnz_lo, nnz_hi + 1, size=n).astype(np.int64)
+    seeds = rng.integers(1, 2 ** 63, size=(n, 4), dtype=np.int64).view(np.uint64)
+    ip = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=ip[1:])
+    idx = np.empty(int(ip[-1]), dtype=np.uint32)
+    w = np.empty(int(ip[-1]), dtype=np.float32)
+    prob, alias = _zipf_tables(d, s)
+    lib = _zipf_lib()
+    threads = threads or os.cpu_count() or 1
+    bounds = np.linspace(0, n, 4 * threads + 1).astype(np.int64)
+
+    def run(c):
+        a, b = int(bounds[c]), int(bounds[c + 1])
+        if b > a:
+            return lib.zipf_sets(a, b, ip.ctypes.data, seeds.ctypes.data, d, prob.ctypes.data, alias.ctypes.data,
+                                 idx.ctypes.data, w.ctypes.data)
+        return 0
+
+    with ThreadPoolExecutor(threads) as ex:
+        assert all(rc == 0 for rc in ex.map(run, range(len(bounds) - 1)))
+    return Batch(ip, idx, w, name, dict(n=n, d=d, zipf=s, seed=seed))
+
+
+def workload3(n: int = 1_000_000, threads: int | None = None) -> Batch:
+    """W3: tf-idf-like sets for (L, K) = (64, 8) LSH (see the module docstring)."""
+    return zipf_batch(n, 200, 2000, 1 << 20, 1.1, 1003, threads, "W3")
 
 
 def workload4_requests(rate: float = 50_000.0, seconds: float = 60.0, max_requests: int | None = None):
