@@ -104,6 +104,24 @@ int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
                    int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_keys,
                    uint64_t *out_words, void *stream);
 
+/* Largest n_sets that dm_sketch_noalloc accepts. */
+#define DM_NOALLOC_MAX_SETS 262144
+
+/* dm_sketch without a context and without any device allocation.  (The paper has no
+ * counterpart: this exists for host programs that do not allow a library to allocate, such as a
+ * framework that hands all device memory to its own caching allocator, or a process that
+ * reserved the whole device.)  Same arguments, outputs and bits as dm_sketch, with phi0 = 1 and
+ * automatic launch shape, on the current CUDA device.  The library's scratch for this call
+ * (work queue, counters, status) is a fixed device array of about 1 MiB that every GPU loading
+ * the library holds until the process exits; n_sets above DM_NOALLOC_MAX_SETS is rejected with
+ * DM_EINVAL before any GPU work.  All calls share that array, so calls whose work overlaps on a
+ * GPU (other streams or host threads) race and may return wrong keys.  The first call on a
+ * device performs a one-time set-up (finding the array's device address, loading the Poisson
+ * table); make that first call before any stream capture.  The call waits for `stream` and
+ * returns the first error the kernels recorded (DM_EINVAL for a bad weight, DM_ERANGE ...). */
+int dm_sketch_noalloc(const int64_t *indptr, const uint32_t *indices, const float *weights,
+                      int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream);
+
 /* Wait for `stream`, then return (and clear) the first error recorded by a kernel of this
  * context, or DM_ECUDA if the stream itself failed. */
 int dm_sync_status(dm_ctx *ctx, void *stream);

@@ -20,7 +20,7 @@ from .build import LIB, build
 
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
            "dm_sketch_host", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
-           "dm_poisson_thresholds", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
+           "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
            "OPT_WARPS_PER_BLOCK"]
 
 OPT_PHI0, OPT_COUNTERS, OPT_FORM, OPT_WARPS_PER_BLOCK = 1, 2, 3, 4
@@ -58,6 +58,7 @@ def load(path: str | None = None):
             "dm_set_option": ([P, ctypes.c_int, i64], ctypes.c_int),
             "dm_t_of_k": ([i32], i64),
             "dm_poisson_thresholds": ([P], None),
+            "dm_sketch_noalloc": ([P, P, P, i64, i32, u64, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -193,6 +194,21 @@ def dm_sketch_host(ctx: Context, indptr, indices, weights, k: int, seed: int, ou
                                  P(out_words.data_ptr()) if out_words is not None else None,
                                  _stream(stream)), "dm_sketch_host")
     return out_keys, out_words
+
+
+def dm_sketch_noalloc(indptr, indices, weights, k: int, seed: int, out, stream=None):
+    """dm_sketch for programs that forbid the library's own device allocations: no context, the
+    scratch is a fixed array inside the library (at most DM_NOALLOC_MAX_SETS sets per call;
+    overlapping calls race).  `out` must be given.  Synchronous; raises on any error."""
+    n, ip, ix, w = _csr_ptrs(indptr, indices, weights)
+    if out.numel() != n * k:
+        raise ValueError("out must hold n_sets * k keys")
+    _check(load().dm_sketch_noalloc(ip, ix, w, n, int(k), int(seed) & (2**64 - 1),
+                                    _dev_ptr(out, "uint64", "out"), _stream(stream)), "dm_sketch_noalloc")
+    return out
+
+
+NOALLOC_MAX_SETS = 262144
 
 
 def dm_sync_status(ctx: Context, stream=None, raise_on_error: bool = True) -> int:
