@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--workload", choices=["W1", "W2", "W3"], default="W1",
                     help="W1 (default, the headline): k=256 keys + 1-bit words; W2: k=1024 heavy-tailed batch; "
                          "W3: (L, K) = (64, 8) LSH")
+    ap.add_argument("--form", choices=["batched", "plain", "persistent"], default="batched",
+                    help="launch form (the plain form is the one-warp-per-set reference)")
+    ap.add_argument("--large-nnz", type=int, default=None, help="batched form: element count of a large set")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -253,7 +256,11 @@ def gpu_arm(args):
     else:
         keys = torch.empty((n, kk), dtype=torch.int64, device="cuda")
         outw = torch.empty((n, words), dtype=torch.int64, device="cuda") if wl == "W1" else None
+    form_id = {"batched": dmx.FORM_BATCHED, "plain": dmx.FORM_PLAIN, "persistent": dmx.FORM_PERSISTENT}[args.form]
     ctx = dmx.dm_create(local)
+    dmx.dm_set_option(ctx, dmx.OPT_FORM, form_id)
+    if args.large_nnz is not None:
+        dmx.dm_set_option(ctx, dmx.OPT_LARGE_NNZ, args.large_nnz)
     stream = torch.cuda.current_stream()
 
     def launch(c):
@@ -271,6 +278,7 @@ def gpu_arm(args):
     cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
     cctx = dmx.dm_create(local)
     dmx.dm_set_option(cctx, dmx.OPT_COUNTERS, cnt.data_ptr())
+    dmx.dm_set_option(cctx, dmx.OPT_FORM, form_id)
     launch(cctx)
     dmx.dm_sync_status(cctx)
     areas, darts, kept, passes = [int(v) for v in cnt.cpu().tolist()]
@@ -363,10 +371,11 @@ def gpu_arm(args):
             "minhashes_per_s": value * kk,
             "config": {"workload": desc if args.sets is None else f"{wl} prefix of {n} sets",
                        "n_sets": n, "k": kk, "b": B_BITS if wl == "W1" else None, "seed": SEED,
-                       "form": "plain: one warp per set (fast kernel) + general kernel over its queue",
+                       "form": args.form,
                        "l2": "inputs 2 GB and outputs 2 GB per step, > 129 MB L2: no flush needed"},
             "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": 2 * args.steps, "wall_s_timed": t_wall,
+            "gpu_launches": (2 if args.form != "batched" else (5 if wl == "W3" else 6)) * args.steps,
+            "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -21,9 +21,11 @@ from .build import LIB, build
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
            "dm_sketch_host", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
            "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
-           "OPT_WARPS_PER_BLOCK"]
+           "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "FORM_BATCHED", "FORM_PLAIN",
+           "FORM_PERSISTENT"]
 
-OPT_PHI0, OPT_COUNTERS, OPT_FORM, OPT_WARPS_PER_BLOCK = 1, 2, 3, 4
+OPT_PHI0, OPT_COUNTERS, OPT_FORM, OPT_WARPS_PER_BLOCK, OPT_LSH_PHI0, OPT_LARGE_NNZ = 1, 2, 3, 4, 5, 6
+FORM_BATCHED, FORM_PLAIN, FORM_PERSISTENT = 0, 1, 2
 _lock = threading.Lock()
 _lib = None
 

@@ -24,8 +24,9 @@ struct dm_ctx {
     float phi0 = 1.0f;             // initial phi of the sketch loop (Theorem 1)
     float phi0_lsh = 4.0f;         // initial phi of the LSH loop (every bucket needs K darts)
     unsigned long long *counters = nullptr;
-    int form = 0;
+    int form = 0;                  // 0 batched, 1 plain, 2 persistent in input order
     int warps_per_block = 0;       // 0 = automatic
+    int large_nnz = 2048;          // batched form: sets with this many elements get a block
     // staging for the host-buffer entry points
     void *d_stage = nullptr;
     size_t d_stage_bytes = 0;
@@ -116,8 +117,8 @@ int check_csr(const int64_t *indptr, const uint32_t *indices, const float *weigh
     return DM_OK;
 }
 
-// Queue scratch for a call of n_sets sets: int32[n_sets] followed by the counter.
-size_t queue_bytes(int64_t n_sets) { return ((size_t)n_sets * 4 + 255) / 256 * 256 + 256; }
+// Scratch of a call of n_sets sets: work queue, order, classes and counters.
+size_t queue_bytes(int64_t n_sets) { return dm::call_scratch_bytes(n_sets); }
 
 int ensure_queue(dm_ctx *ctx, int64_t n_sets) {
     if (n_sets <= ctx->queue_cap) return DM_OK;
@@ -186,16 +187,30 @@ int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const 
     p.warp_bytes = (int32_t)dm::warp_bytes(lsh, k, K, 1);
     p.warp_bytes_fast = (int32_t)dm::warp_bytes(lsh, k, K, 0);
     p.sink_bytes = (int32_t)dm::sink_bytes(lsh, k, K);
-    p.queue = (int32_t *)queue;
-    p.queue_count = (unsigned int *)((char *)queue + queue_bytes(n_sets) - 256);
-    p.work_next = p.queue_count + 1;
+    dm::carve_call_scratch(queue, n_sets, p);
+    const bool count = ctx->counters != nullptr;
+    const int64_t blocks = (n_sets + wpb - 1) / wpb;
+    if (ctx->form == 1) {
+        // plain form: one warp per set in input order, a block per wpb sets
+        p.sched = 1;
+        return cuda_fail(dm::launch_sets(p, lsh, bbit, count, (int)blocks, (int)blocks, st));
+    }
     // persistent grids: as many blocks as can be resident, never more than there are sets
-    int64_t blocks = (n_sets + wpb - 1) / wpb;
-    int64_t cap0 = (int64_t)ctx->sm_count * dm::blocks_per_sm(lsh, 0, bbit, wpb, smem_fast);
-    int64_t cap1 = (int64_t)ctx->sm_count * dm::blocks_per_sm(lsh, 1, bbit, wpb, smem);
-    int grid = (int)(blocks < cap0 ? blocks : cap0);
-    int grid_general = (int)(blocks < cap1 ? blocks : cap1);
-    return cuda_fail(dm::launch_sets(p, lsh, bbit, ctx->counters != nullptr, grid, grid_general, st));
+    const int64_t cap0 = (int64_t)ctx->sm_count * dm::blocks_per_sm(lsh, 0, bbit, wpb, smem_fast);
+    const int64_t cap1 = (int64_t)ctx->sm_count * dm::blocks_per_sm(lsh, 1, bbit, wpb, smem);
+    const int grid = (int)(blocks < cap0 ? blocks : cap0);
+    const int grid_general = (int)(blocks < cap1 ? blocks : cap1);
+    if (ctx->form == 2) return cuda_fail(dm::launch_sets(p, lsh, bbit, count, grid, grid_general, st));
+    // batched form (default): large sets get a block of 8 warps
+    p.large_warps = 8;
+    p.large_nnz = lsh ? 0 : ctx->large_nnz;
+    int grid_large = 0;
+    if (p.large_nnz > 0) {
+        const size_t lb = dm::large_block_bytes(k, p.large_warps);
+        if (lb <= 227 * 1024) grid_large = ctx->sm_count * dm::large_blocks_per_sm(bbit, p.large_warps, lb);
+        else p.large_nnz = 0;
+    }
+    return cuda_fail(dm::launch_batched(p, lsh, bbit, count, grid, grid_general, grid_large, st));
 }
 
 int run_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
@@ -390,8 +405,12 @@ int dm_set_option(dm_ctx *ctx, int option, int64_t value) {
             ctx->counters = (unsigned long long *)(uintptr_t)value;
             return DM_OK;
         case DM_OPT_FORM:
-            if (value < 0 || value > 1) return DM_EINVAL;
+            if (value < 0 || value > 2) return DM_EINVAL;
             ctx->form = (int)value;
+            return DM_OK;
+        case DM_OPT_LARGE_NNZ:
+            if (value < 0 || value > 0x7FFFFFFF) return DM_EINVAL;
+            ctx->large_nnz = (int)value;
             return DM_OK;
         case DM_OPT_LSH_PHI0:
             if (value < 1 || value > 1024 * 1024) return DM_EINVAL;

@@ -29,9 +29,17 @@ struct SketchParams {
     int32_t warp_bytes_fast;  // dynamic shared memory per warp (fast kernel)
     int32_t sink_bytes;   // leading part of a warp's shared memory that holds the sink
     int32_t warps_per_block;
-    int32_t *queue;             // sets deferred to the general kernel (capacity n_sets)
-    unsigned int *queue_count;  // number of queued sets; followed by the two work counters
-    unsigned int *work_next;    // = queue_count + 1: next work item of the fast / general kernel
+    int32_t *queue;             // sets for the general kernel (capacity n_sets)
+    unsigned int *queue_count;  // number of queued sets; followed by the work counters
+    unsigned int *work_next;    // = queue_count + 1: next work item of the fast / general / large kernel
+    // 0: persistent warps over the sets in input order; 1: one warp per set, static (the plain
+    // form); 2: batched (classified into fast, general and large sets, largest first)
+    int32_t sched;
+    int32_t *order;             // fast sets, then large sets, each largest first (capacity n_sets)
+    uint8_t *cls;               // per set: class * 32 + descending size bin
+    unsigned int *hist;         // 3 x 32 bin counts, then 3 x 32 bin cursors, then class totals
+    int32_t large_nnz;          // sets with at least this many elements go to the block kernel
+    int32_t large_warps;        // warps per block of the large-set kernel
 };
 
 // Shared memory per warp of the fast (mode 0) or general (mode 1) kernel, and of its sink
@@ -44,9 +52,23 @@ int blocks_per_sm(bool lsh, int mode, bool bbit, int warps_per_block, size_t sme
 
 cudaError_t upload_poisson_table(const uint32_t *T);
 
-// Zeroes the queue and work counters, then launches the fast kernel over all sets and the
-// general kernel over the sets it queued, all on stream st.
+// Plain form: zeroes the queue and work counters, then launches the fast kernel over all sets
+// (one warp each, in input order) and the general kernel over the sets it queued.
 cudaError_t launch_sets(const SketchParams &p, bool lsh, bool bbit, bool count, int grid_fast, int grid_general,
                         cudaStream_t st);
+
+// Batched form: classification (fast / general / large, largest first), then the persistent
+// fast kernel, the persistent general kernel (general sets and those the fast kernel defers)
+// and, for sketches, the block-per-set kernel over large sets.  grid_large = 0: no large class.
+cudaError_t launch_batched(const SketchParams &p, bool lsh, bool bbit, bool count, int grid_fast,
+                           int grid_general, int grid_large, cudaStream_t st);
+
+// Shared memory of the large-set kernel's blocks.
+size_t large_block_bytes(int k, int warps);
+int large_blocks_per_sm(bool bbit, int warps, size_t smem);
+
+// Scratch of one call: queue, order, classes and the small header (counters, histogram).
+size_t call_scratch_bytes(int64_t n_sets);
+void carve_call_scratch(void *base, int64_t n_sets, SketchParams &p);
 
 }  // namespace dm

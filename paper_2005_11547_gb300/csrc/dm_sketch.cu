@@ -37,6 +37,9 @@ constexpr int kDefer = -1;         // a pass the fast kernel leaves to the gener
 constexpr int kRowTab = 40;        // fast path: rows of nu = 0..38 (+1 pad)
 constexpr int kOverflow = 64;      // LSH: appends past a full bucket within one batch
 constexpr uint64_t kRMask = ((1ull << 55) - 1) & ~(uint64_t)kUMask;
+// batched form: hist[0..96) bin counts, [96..192) bin cursors, [192..195) class totals
+constexpr int kClasses = 3, kBins = 32, kCursors = kClasses * kBins, kTotals = 2 * kClasses * kBins;
+constexpr size_t kHeaderBytes = 1024;   // queue count, 3 work counters, histogram, totals
 
 __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
 #pragma unroll
@@ -54,7 +57,7 @@ struct Queue {
 // ==========================================================================================
 // Sinks
 // ==========================================================================================
-size_t sketch_sink_bytes(int k) { return ((size_t)k * 8 + 15) & ~(size_t)15; }
+__host__ __device__ size_t sketch_sink_bytes(int k) { return ((size_t)k * 8 + 15) & ~(size_t)15; }
 
 size_t lsh_sink_bytes(int L, int K) {
     size_t B = 2 * (size_t)K;
@@ -348,10 +351,11 @@ struct WalkF {
     }
 };
 
-// One rank-region-0 pass over the row.  Returns 0, an error code, or kDefer.
+// One rank-region-0 pass over tiles first, first + stride, ... of the row [.., end).  Returns 0,
+// an error code, or kDefer.
 template <class Sink, bool COUNT>
-__device__ int fast_pass(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc, const FastMem &m,
-                         Sink &sink, int lane, unsigned long long *cnt) {
+__device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, int64_t end, const PassCut &pc,
+                         const FastMem &m, Sink &sink, int lane, unsigned long long *cnt) {
     const unsigned lt = (1u << lane) - 1u;
     for (int nu = lane; nu < kRowTab; nu += 32) {
         int n = nu > kMaxRegion ? kMaxRegion : nu;
@@ -360,7 +364,7 @@ __device__ int fast_pass(const SketchParams &p, int64_t beg, int64_t end, const 
     }
     const uint32_t g_hi = (uint32_t)(pc.gm1 >> 32), glo_hi = (uint32_t)(pc.gfl_lo >> 32);
     Queue q = {0, 0};
-    for (int64_t tile = beg; tile < end; tile += 32) {
+    for (int64_t tile = first; tile < end; tile += stride) {
         const int64_t pos = tile + lane;
         int nutop = -1;
         uint64_t F = 0, e = 0;
@@ -576,13 +580,14 @@ struct WalkG {
     }
 };
 
-// One pass over the row with the general walk.  Returns 0 or an error code.
+// One pass with the general walk over tiles first, first + stride, ... of the row [.., end).
+// Returns 0 or an error code.
 template <class Sink, bool COUNT>
-__device__ int gen_pass(const SketchParams &p, int64_t beg, int64_t end, const PassCut &pc, const GenMem &m,
-                        Sink &sink, int lane, unsigned long long *cnt) {
+__device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, int64_t end, const PassCut &pc,
+                        const GenMem &m, Sink &sink, int lane, unsigned long long *cnt) {
     const unsigned lt = (1u << lane) - 1u;
     Queue q = {0, 0};
-    for (int64_t tile = beg; tile < end; tile += 32) {
+    for (int64_t tile = first; tile < end; tile += stride) {
         const int64_t pos = tile + lane;
         int nutop = -1;
         uint64_t F = 0, e = 0;
@@ -652,14 +657,22 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) set_kernel(const Sketc
     sink.bind(wbase, p);
     const FastMem fm = carve_fast(wbase + p.sink_bytes);
     const GenMem gm = carve_gen(wbase + p.sink_bytes);
-    const int64_t n_work = MODE == 0 ? p.n_sets : (int64_t)*p.queue_count;
+    const int64_t n_work = MODE == 1 ? (int64_t)*p.queue_count
+                                     : (p.sched == 2 ? (int64_t)p.hist[kTotals] : p.n_sets);
     unsigned int *next = p.work_next + MODE;
-    for (;;) {
-        unsigned int wi = 0;
-        if (lane == 0) wi = atomicAdd(next, 1u);
-        wi = __shfl_sync(kFull, wi, 0);
-        if ((int64_t)wi >= n_work) break;
-        const int64_t set = MODE == 0 ? (int64_t)wi : (int64_t)p.queue[wi];
+    const int64_t static_wi = (int64_t)blockIdx.x * p.warps_per_block + wib;
+    for (int round = 0;; ++round) {
+        int64_t wi;
+        if (p.sched == 1) {                        // plain form: one set per warp
+            if (round) break;
+            wi = static_wi;
+        } else {
+            unsigned int c = 0;
+            if (lane == 0) c = atomicAdd(next, 1u);
+            wi = (int64_t)__shfl_sync(kFull, c, 0);
+        }
+        if (wi >= n_work) break;
+        const int64_t set = MODE == 1 ? (int64_t)p.queue[wi] : (p.sched == 2 ? (int64_t)p.order[wi] : wi);
         const int64_t beg = p.indptr[set], end = p.indptr[set + 1];
         // ||x||_1 and input validation
         float l1 = 0.f;
@@ -690,8 +703,8 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) set_kernel(const Sketc
                 pc.gm1 = rc.gm1;
                 pc.cthr = th;
                 if (MODE == 0 && pc.rho_top != 0) { deferred = true; break; }
-                err = MODE == 0 ? fast_pass<Sink, COUNT>(p, beg, end, pc, fm, sink, lane, cnt)
-                                : gen_pass<Sink, COUNT>(p, beg, end, pc, gm, sink, lane, cnt);
+                err = MODE == 0 ? fast_pass<Sink, COUNT>(p, beg, 32, end, pc, fm, sink, lane, cnt)
+                                : gen_pass<Sink, COUNT>(p, beg, 32, end, pc, gm, sink, lane, cnt);
                 ++passes;
                 if (err == kDefer) { err = 0; deferred = true; break; }
                 if (err) break;
@@ -727,6 +740,189 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) set_kernel(const Sketc
     }
 }
 
+// ==========================================================================================
+// Batched form.  classify: per set, class (0 fast: first limit below 1; 1 general; 2 large:
+// >= large_nnz elements, sketches only) and a size bin that sorts larger sets first
+// (bin = 31 - floor(log2(nnz + 1))); scan: bin offsets per class; scatter: fast sets to
+// order[0..nF), general sets to queue[0..nG) (the general kernel's list; the fast kernel
+// appends the sets it defers after them), large sets to order[nF..nF+nL).
+// ==========================================================================================
+__global__ void __launch_bounds__(256) classify_kernel(const SketchParams p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < p.n_sets; s += nw) {
+        const int64_t beg = p.indptr[s], end = p.indptr[s + 1], nnz = end - beg;
+        float l1 = 0.f;
+        for (int64_t i = beg + lane; i < end; i += 32) l1 += p.weights[i];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(kFull, l1, o);
+        if (lane == 0) {
+            int c;
+            if (p.large_nnz > 0 && nnz >= p.large_nnz) c = 2;
+            else c = (!(l1 > 0.f) || __fdiv_rn(p.phi0, l1) < 1.0f) ? 0 : 1;   // zero/invalid rows: fast
+            const int bin = 31 - (63 - __clzll((long long)(nnz + 1)));
+            p.cls[s] = (uint8_t)(c * kBins + (bin < 0 ? 0 : bin));
+            atomicAdd(&p.hist[c * kBins + (bin < 0 ? 0 : bin)], 1u);
+        }
+    }
+}
+
+__global__ void scan_kernel(const SketchParams p) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int c = 0; c < kClasses; ++c) {
+        unsigned int off = 0;
+        for (int b = 0; b < kBins; ++b) {
+            p.hist[kCursors + c * kBins + b] = off;
+            off += p.hist[c * kBins + b];
+        }
+        p.hist[kTotals + c] = off;
+    }
+    *p.queue_count = p.hist[kTotals + 1];
+}
+
+__global__ void __launch_bounds__(256) scatter_kernel(const SketchParams p) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < p.n_sets; s += stride) {
+        const int cb = p.cls[s], c = cb / kBins;
+        const unsigned int pos = atomicAdd(&p.hist[kCursors + cb], 1u);
+        if (c == 0) p.order[pos] = (int32_t)s;
+        else if (c == 1) p.queue[pos] = (int32_t)s;
+        else p.order[p.hist[kTotals] + pos] = (int32_t)s;
+    }
+}
+
+// Large sets: a block per set.  The block's warps share the set's k bucket minima in shared
+// memory (atomicMin works across warps) and take the set's tiles round-robin, each with its
+// own dart queue; passes are separated by block barriers.  A pass runs the fast walk when the
+// limit is below 1 and every tile allows it, else the general walk over all tiles (a dart seen
+// twice does not change a minimum).
+size_t large_block_bytes(int k, int warps) {
+    const size_t per = kFastPathBytes > kGenPathBytes ? kFastPathBytes : kGenPathBytes;
+    return sketch_sink_bytes(k) + (size_t)warps * per + 64;
+}
+
+template <bool BBIT, bool COUNT>
+__global__ void __launch_bounds__(256, 2) large_kernel(const SketchParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const size_t per = kFastPathBytes > kGenPathBytes ? kFastPathBytes : kGenPathBytes;
+    SketchSink sink;
+    sink.bind(smem, p);
+    unsigned char *wbase = smem + sketch_sink_bytes(p.k) + (size_t)wid * per;
+    const FastMem fm = carve_fast(wbase);
+    const GenMem gm = carve_gen(wbase);
+    int *flags = reinterpret_cast<int *>(smem + sketch_sink_bytes(p.k) + (size_t)nwarps * per);
+    float *wsum = reinterpret_cast<float *>(flags + 4);
+    const int64_t n_work = p.hist[kTotals + 2], base = p.hist[kTotals];
+    for (;;) {
+        if (threadIdx.x == 0) flags[0] = (int)atomicAdd(p.work_next + 2, 1u);
+        __syncthreads();
+        const int64_t wi = flags[0];
+        if (wi >= n_work) break;
+        const int64_t set = p.order[base + wi];
+        const int64_t beg = p.indptr[set], end = p.indptr[set + 1];
+        float l1 = 0.f;
+        int bad = 0;
+        for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+            float x = p.weights[i];
+            if (!(x >= 0.f) || isinf(x)) bad = 1;
+            else l1 += x;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(kFull, l1, o);
+        if (lane == 0) wsum[wid] = l1;
+        if (wid == 0) sink.reset(lane);
+        int err = __syncthreads_or(bad) ? DM_EINVAL : 0;
+        l1 = 0.f;
+        for (int w = 0; w < nwarps; ++w) l1 += wsum[w];
+        unsigned long long cnt[3] = {0, 0, 0};
+        unsigned long long passes = 0;
+        if (!err && l1 > 0.f) {
+            uint32_t th = __float_as_uint(__fdiv_rn(p.phi0, l1));
+            PassCut pc;
+            pc.rho_lo = 0;
+            pc.gfl_lo = 0;
+            pc.cthr_lo = 0;
+            for (int pass = 0;; ++pass) {
+                if (pass == kMaxPasses) { err = DM_EOVERFLOW; break; }
+                RankCut rc;
+                if (!rank_cut(th, rc)) { err = DM_ERANGE; break; }
+                pc.rho_top = rc.rho_top;
+                pc.gm1 = rc.gm1;
+                pc.cthr = th;
+                int e = kDefer;
+                if (pc.rho_top == 0) e = fast_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, fm, sink, lane, cnt);
+                const int any_defer = __syncthreads_or(e == kDefer);
+                if (any_defer) e = gen_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, gm, sink, lane, cnt);
+                ++passes;
+                if (__syncthreads_or(e == DM_ERANGE)) { err = DM_ERANGE; break; }
+                int empty = 0;
+                for (uint32_t j = threadIdx.x; j < (uint32_t)p.k; j += blockDim.x) empty |= (sink.slots[j] == ~0ull);
+                if (!__syncthreads_or(empty)) break;
+                pc.rho_lo = rc.g_one ? rc.rho_top + 1 : rc.rho_top;
+                pc.gfl_lo = rc.g_one ? 0 : rc.gfl;
+                pc.cthr_lo = th;
+                th = __float_as_uint(2.0f * __uint_as_float(th));
+            }
+        }
+        if (COUNT) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                unsigned long long v = cnt[c];
+#pragma unroll
+                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+                if (lane == 0 && p.counters) atomicAdd(&p.counters[c], v);
+            }
+            if (threadIdx.x == 0 && p.counters) atomicAdd(&p.counters[3], passes);
+        }
+        __syncthreads();
+        if (wid == 0) {
+            if (err) {
+                if (lane == 0) set_status(p.status, err);
+                sink.clear_to_error(lane);
+            }
+            sink.template finish<BBIT>(p, set, err != 0, lane);
+        }
+        __syncthreads();
+    }
+}
+
+template <bool BBIT, bool COUNT>
+static cudaError_t launch_large(const SketchParams &p, int grid, cudaStream_t st) {
+    const size_t smem = large_block_bytes(p.k, p.large_warps);
+    auto fn = large_kernel<BBIT, COUNT>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    fn<<<grid, 32 * p.large_warps, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+int large_blocks_per_sm(bool bbit, int warps, size_t smem) {
+    const void *fn = bbit ? (const void *)large_kernel<true, false> : (const void *)large_kernel<false, false>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * warps, smem) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+size_t call_scratch_bytes(int64_t n_sets) {
+    const size_t a = ((size_t)n_sets * 4 + 255) / 256 * 256, c = ((size_t)n_sets + 255) / 256 * 256;
+    return 2 * a + c + kHeaderBytes;
+}
+
+void carve_call_scratch(void *base, int64_t n_sets, SketchParams &p) {
+    const size_t a = ((size_t)n_sets * 4 + 255) / 256 * 256, c = ((size_t)n_sets + 255) / 256 * 256;
+    char *b = (char *)base;
+    p.queue = (int32_t *)b;
+    p.order = (int32_t *)(b + a);
+    p.cls = (uint8_t *)(b + 2 * a);
+    p.queue_count = (unsigned int *)(b + 2 * a + c);
+    p.work_next = p.queue_count + 1;
+    p.hist = p.queue_count + 4;
+}
+
 cudaError_t upload_poisson_table(const uint32_t *T) {
     return cudaMemcpyToSymbol(c_pois, T, 12 * sizeof(uint32_t));
 }
@@ -759,6 +955,34 @@ cudaError_t launch_sets(const SketchParams &p, bool lsh, bool bbit, bool count, 
     // queue count and the two work counters are contiguous
     cudaError_t e = cudaMemsetAsync(p.queue_count, 0, 4 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
+    if (lsh) {
+        if ((e = launch_mode<LshSink, 0>(p, false, count, grid_fast, st)) != cudaSuccess) return e;
+        return launch_mode<LshSink, 1>(p, false, count, grid_general, st);
+    }
+    if ((e = launch_mode<SketchSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
+    return launch_mode<SketchSink, 1>(p, bbit, count, grid_general, st);
+}
+
+cudaError_t launch_batched(const SketchParams &p0, bool lsh, bool bbit, bool count, int grid_fast,
+                           int grid_general, int grid_large, cudaStream_t st) {
+    SketchParams p = p0;
+    p.sched = 2;
+    if (lsh || grid_large <= 0) p.large_nnz = 0;
+    cudaError_t e = cudaMemsetAsync(p.queue_count, 0, kHeaderBytes, st);
+    if (e != cudaSuccess) return e;
+    const int cgrid = (int)((p.n_sets + 7) / 8 < 4096 ? (p.n_sets + 7) / 8 : 4096);
+    classify_kernel<<<cgrid, 256, 0, st>>>(p);
+    scan_kernel<<<1, 32, 0, st>>>(p);
+    const int sgrid = (int)((p.n_sets + 255) / 256 < 4096 ? (p.n_sets + 255) / 256 : 4096);
+    scatter_kernel<<<sgrid, 256, 0, st>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the largest sets first: their blocks become resident before the fast kernel's
+    if (!lsh && grid_large > 0) {
+        if ((e = count ? (bbit ? launch_large<true, true>(p, grid_large, st) : launch_large<false, true>(p, grid_large, st))
+                       : (bbit ? launch_large<true, false>(p, grid_large, st) : launch_large<false, false>(p, grid_large, st)))
+            != cudaSuccess)
+            return e;
+    }
     if (lsh) {
         if ((e = launch_mode<LshSink, 0>(p, false, count, grid_fast, st)) != cudaSuccess) return e;
         return launch_mode<LshSink, 1>(p, false, count, grid_general, st);

@@ -75,6 +75,18 @@ def test_lsh_phi0_does_not_change_bits(dmx, torch_mod, ctx):
         assert_same(got, ref, f"phi0={v / 1024}")
 
 
+@pytest.mark.parametrize("form", [1, 2])
+def test_lsh_forms(dmx, torch_mod, ctx, form):
+    b = workloads.random_sets(300, 0, 300, 1 << 24, seed=19)
+    ref, _ = gpu_lsh(dmx, torch_mod, ctx, b, 32, 4, 8)
+    c2 = dmx.dm_create(0)
+    dmx.dm_set_option(c2, dmx.OPT_FORM, form)
+    got, rc = gpu_lsh(dmx, torch_mod, c2, b, 32, 4, 8)
+    c2.close()
+    assert rc == 0
+    assert_same(got, ref, f"form {form}")
+
+
 def test_lsh_rejects_oversized_buckets(dmx, torch_mod, ctx):
     b = workloads.random_sets(4, 1, 10, 1 << 20, seed=1)
     with pytest.raises(dmx.DartMinHashError):

@@ -189,13 +189,37 @@ def test_options_do_not_change_bits(dmx, torch_mod, ctx):
     again, _ = gpu_sketch(dmx, torch_mod, ctx, b, 256, 77)
     assert_same(again, ref, "repeat")
     for opt, val in [(dmx.OPT_PHI0, 512), (dmx.OPT_PHI0, 4096), (dmx.OPT_PHI0, 1024 * 3),
-                     (dmx.OPT_WARPS_PER_BLOCK, 1), (dmx.OPT_WARPS_PER_BLOCK, 3)]:
+                     (dmx.OPT_WARPS_PER_BLOCK, 1), (dmx.OPT_WARPS_PER_BLOCK, 3),
+                     (dmx.OPT_FORM, dmx.FORM_PLAIN), (dmx.OPT_FORM, dmx.FORM_PERSISTENT),
+                     (dmx.OPT_LARGE_NNZ, 0), (dmx.OPT_LARGE_NNZ, 40), (dmx.OPT_LARGE_NNZ, 150)]:
         c2 = dmx.dm_create(0)
         dmx.dm_set_option(c2, opt, val)
         got, rc = gpu_sketch(dmx, torch_mod, c2, b, 256, 77)
         c2.close()
         assert rc == 0
         assert_same(got, ref, f"option {opt}={val}")
+
+
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_forms_on_heavy_tailed_batch(dmx, torch_mod, oracle_mod, form):
+    """Batched (large sets on blocks of 8 warps, largest first), plain and persistent forms on a
+    heavy-tailed batch: same bits as the oracle."""
+    rng = np.random.default_rng(66)
+    rows = []
+    for s in range(400):
+        nnz = int(min(20000, max(1, np.exp(np.log(60) + 1.5 * rng.standard_normal()))))
+        idx = np.sort(rng.choice(1 << 24, nnz, replace=False)).astype(np.uint32)
+        z = rng.lognormal(size=nnz)
+        rows.append((idx, (z / z.sum() * 10 ** rng.uniform(-3, 3)).astype(np.float32)))
+    b = workloads.csr_of(rows)
+    c2 = dmx.dm_create(0)
+    dmx.dm_set_option(c2, dmx.OPT_FORM, form)
+    dmx.dm_set_option(c2, dmx.OPT_LARGE_NNZ, 500)
+    for k in (64, 1024):
+        got, rc = gpu_sketch(dmx, torch_mod, c2, b, k, 17)
+        assert rc == 0
+        assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 17, threads=THREADS), f"form {form} k={k}")
+    c2.close()
 
 
 def test_counters_and_streams(dmx, torch_mod, ctx, oracle_mod):
