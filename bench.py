@@ -155,12 +155,12 @@ def summarize_clocks(rows):
 # traffic from the committed ncu capture (valid only for the kernel source it was taken on)
 # ------------------------------------------------------------------------------------------
 def kernel_fingerprint() -> str:
+    """Hash of the kernel sources (device code only)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2005_11547_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in ("dm_sketch.cu", "dm_device.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
