@@ -437,10 +437,9 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
 }
 
 // ==========================================================================================
-// General path: every region (nu, rho), columns w and rows r, in 64-bit arithmetic.  Each
-// lane hashes its next area once the darts of its previous one are queued and queues at most
-// one dart per round (slot = rank of the lane in a ballot).  A record holds the dart counter,
-// pv = pb | vmax (the rank base pb is a multiple of 2^24) and meta = sh | S << 6:
+// General path: every region (nu, rho), columns w and rows r, in 64-bit arithmetic, with the
+// same one-iteration-per-area batched emission as the fast path.  A record holds the dart
+// counter, pv = pb | vmax (the rank base pb is a multiple of 2^24) and meta = sh | S << 6:
 // rank = (pb + (u << sh)) 2^-S.
 // ==========================================================================================
 struct GenMem {
@@ -607,35 +606,46 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
         if (total == 0) continue;
         const uint64_t share = (total + 31) >> 5;
         const uint64_t lo = share * lane;
-        uint64_t left = lo < total ? min(share, total - lo) : 0;   // areas this lane still has to hash
+        const uint64_t mine = lo < total ? min(share, total - lo) : 0;   // areas of this lane
         WalkG s;
-        if (left) s.locate(lo, m, pc);
-        uint64_t c = 0, pv = 0;
-        uint32_t meta = 0;
-        int rem = 0;                                   // darts of the current area not yet queued
-        while (__any_sync(kFull, left > 0 || rem > 0)) {
-            if (rem == 0 && left > 0) {
-                const uint64_t a = mix64(s.ctr);
-                rem = poisson1((uint32_t)(a >> 32), c_pois);
-                c = a + kGolden;
+        if (mine) s.locate(lo, m, pc);
+        // one iteration per area slot: every lane hashes one area, then the darts of all 32
+        // areas are written at once (positions from a ballot prefix sum of X < 16)
+        for (uint64_t it = 0; it < share; ++it) {
+            int X = 0;
+            uint64_t a = 0, pv = 0;
+            uint32_t meta = 0;
+            if (it < mine) {
+                a = mix64(s.ctr);
+                X = poisson1((uint32_t)(a >> 32), c_pois);
                 pv = s.pv();
                 meta = s.meta();
-                if (COUNT) { cnt[0]++; cnt[1] += rem; }
-                if (--left) s.advance(m, pc);
+                if (COUNT) { cnt[0]++; cnt[1] += X; }
+                if (it + 1 < mine) s.advance(m, pc);
             }
-            const bool has = rem > 0;
-            const unsigned bal = __ballot_sync(kFull, has);
-            if (has) {
-                const uint32_t i = (q.tail + __popc(bal & lt)) & (kQueue - 1);
-                m.dq_c[i] = c;
-                m.dq_p[i] = pv;
-                m.dq_m[i] = (uint16_t)meta;
-                c += kGolden;
-                --rem;
+            const unsigned b0 = __ballot_sync(kFull, X & 1), b1 = __ballot_sync(kFull, X & 2);
+            const unsigned b2 = __ballot_sync(kFull, X & 4), b3 = __ballot_sync(kFull, X & 8);
+            const uint32_t T = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2) + 8 * __popc(b3);
+            if (T == 0) continue;
+            const uint32_t ex = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt) + 8 * __popc(b3 & lt);
+            for (uint32_t done = 0; done < T;) {
+                const uint32_t room = kQueue - (q.tail - q.head);
+                const uint32_t lim = min(T - done, room);
+                uint32_t jlo = done > ex ? done - ex : 0u;
+                uint32_t jhi = done + lim > ex ? done + lim - ex : 0u;
+                if (jhi > (uint32_t)X) jhi = (uint32_t)X;
+                uint64_t c = a + kGolden * (uint64_t)(jlo + 1);
+                for (uint32_t j = jlo; j < jhi; ++j, c += kGolden) {
+                    const uint32_t i = (q.tail + ex + j - done) & (kQueue - 1);
+                    m.dq_c[i] = c;
+                    m.dq_p[i] = pv;
+                    m.dq_m[i] = (uint16_t)meta;
+                }
+                q.tail += lim;
+                done += lim;
+                __syncwarp();
+                while (q.tail - q.head >= 64) gen_drain<Sink, COUNT>(64, q, m, sink, lane, pc, cnt[2]);
             }
-            q.tail += __popc(bal);
-            __syncwarp();
-            if (q.tail - q.head >= 64) gen_drain<Sink, COUNT>(64, q, m, sink, lane, pc, cnt[2]);
         }
     }
     if (q.tail != q.head) gen_drain<Sink, COUNT>((int)(q.tail - q.head), q, m, sink, lane, pc, cnt[2]);
