@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dm", "reference"], default="dm")
     ap.add_argument("--sets", type=int, default=None, help="prefix of the workload (profiling only)")
-    ap.add_argument("--workload", choices=["W1", "W2", "W3"], default="W1",
+    ap.add_argument("--workload", choices=["W1", "W2", "W3", "W4"], default="W1",
                     help="W1 (default, the headline): k=256 keys + 1-bit words; W2: k=1024 heavy-tailed batch; "
-                         "W3: (L, K) = (64, 8) LSH")
+                         "W3: (L, K) = (64, 8) LSH; W4: serving loop on a Poisson request trace")
+    ap.add_argument("--duration", type=float, default=20.0, help="W4: seconds of 50,000/s arrivals to replay")
     ap.add_argument("--form", choices=["batched", "plain", "persistent"], default="batched",
                     help="launch form (the plain form is the one-warp-per-set reference)")
     ap.add_argument("--large-nnz", type=int, default=None, help="batched form: element count of a large set")
@@ -383,10 +384,119 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------------------------------
+# W4: the serving loop on a request trace
+# ------------------------------------------------------------------------------------------
+def serve_arm(args):
+    """Requests of one set each (nnz = min(1e5, floor(Pareto(1.2) + 1)), weights U(0, 5],
+    d = 2^24, k uniform over {64, 256, 1024}) arriving as a Poisson process at 50,000/s, played in
+    real time through dm_server_replay from host memory (copies in and out are part of every
+    request's latency).  Reported: latency percentiles from arrival to result ready and the
+    sustained rate at that load, the closed-loop capacity (all requests queued at once), and the
+    same for the plain per-request form (one request per launch on one stream)."""
+    import numpy as np
+    import torch
+
+    import paper_2005_11547_gb300 as dmx
+    import workloads
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dmx.build()
+    dmx.load()
+    arrivals, b, ks = workloads.workload4_requests(rate=50_000.0, seconds=args.duration)
+    n = b.n_sets
+    arr_ns = np.ascontiguousarray((arrivals - arrivals[0]) * 1e9, dtype=np.int64)
+    seeds = np.full(n, SEED, dtype=np.uint64)
+    ip = b.indptr
+
+    def prefix(m):
+        return np.ascontiguousarray(ip[: m + 1])
+
+    # sample check: the server's keys equal dm_sketch's on the same rows (device entry, one call per k)
+    m = min(n, 20000)
+    srv = dmx.Server(local, lanes=4)
+    out, _, st = srv.replay(prefix(m), b.indices, b.weights, ks[:m], seeds[:m], np.zeros(m, np.int64))
+    srv.close()
+    if np.any(st != 0):
+        raise RuntimeError("serving sample: a request failed")
+    ctx = dmx.dm_create(local)
+    off = np.concatenate([[0], np.cumsum(ks[:m].astype(np.int64))])
+    for k in (64, 256, 1024):
+        sel = np.nonzero(ks[:m] == k)[0]
+        sub = b.rows(sel)
+        d_ip = torch.from_numpy(sub.indptr).cuda()
+        d_ix = torch.from_numpy(sub.indices.view(np.int32)).cuda()
+        d_w = torch.from_numpy(sub.weights).cuda()
+        ref = dmx.dm_sketch(ctx, d_ip, d_ix, d_w, k, SEED).cpu().numpy().view(np.uint64)
+        got = np.stack([out[off[i]:off[i + 1]] for i in sel])
+        if not np.array_equal(got, ref):
+            raise RuntimeError(f"serving sample: keys differ from dm_sketch (k={k})")
+    ctx.close()
+
+    def pct(lat_ns):
+        v = np.sort(lat_ns) / 1e3
+        return {"p50_us": float(np.percentile(v, 50)), "p99_us": float(np.percentile(v, 99)),
+                "max_us": float(v[-1])}
+
+    def run(per_request, lanes, m_open, m_closed):
+        srv = dmx.Server(local, lanes=lanes, mem_budget_bytes=8 << 30, per_request=per_request)
+        w0 = min(n, 3000)                                     # warm-up: lanes, contexts, kernels
+        srv.replay(prefix(w0), b.indices, b.weights, ks[:w0], seeds[:w0], np.zeros(w0, np.int64), deliver=False)
+        srv.reset_stats()
+        sampler = ClockSampler(local)
+        sampler.start()
+        t0 = time.perf_counter()
+        _, lat, st = srv.replay(prefix(m_open), b.indices, b.weights, ks[:m_open], seeds[:m_open],
+                                arr_ns[:m_open], deliver=False)
+        wall_open = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.reset_stats()
+        t0 = time.perf_counter()
+        srv.replay(prefix(m_closed), b.indices, b.weights, ks[:m_closed], seeds[:m_closed],
+                   np.zeros(m_closed, np.int64), deliver=False)
+        wall_closed = time.perf_counter() - t0
+        stats_closed = srv.stats()
+        clocks = sampler.stop()
+        srv.close()
+        if np.any(st != 0):
+            raise RuntimeError("serving run: a request failed")
+        nnz = int(ip[m_open])
+        return {"requests": m_open, "offered_per_s": 50_000.0, "sustained_per_s": m_open / wall_open,
+                **pct(lat), "mean_batch": stats["mean_batch"], "batches": stats["batches"],
+                "gpu_launches": stats["kernel_launches"] + stats_closed["kernel_launches"],
+                "capacity_per_s": m_closed / wall_closed, "capacity_requests": m_closed,
+                "h2d_bytes": 8 * (m_open + 1) + 8 * nnz, "d2h_bytes": 8 * int(ks[:m_open].astype(np.int64).sum()),
+                "clocks": clocks}
+
+    batched = run(False, 4, n, min(n, 500_000))
+    plain = run(True, 1, min(n, 250_000), min(n, 100_000))
+    line = {
+        "metric": "W4 serving: requests/s sustained at 50,000/s Poisson arrivals (p50/p99 latency)",
+        "value": batched["sustained_per_s"], "unit": "requests/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": 1e3 * n / batched["sustained_per_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"W4: {n} requests over {args.duration:g} s (Poisson 50,000/s), nnz = min(1e5, "
+                               "floor(Pareto(1.2)+1)), weights U(0,5], d=2^24, k uniform {64,256,1024}; 8 GiB "
+                               "admission budget, 4 lanes", "l2": "host-resident trace; no reuse across requests"},
+        "latency_us": {k: batched[k] for k in ("p50_us", "p99_us", "max_us")},
+        "capacity_requests_per_s": batched["capacity_per_s"],
+        "batched": batched, "plain_per_request": plain,
+        "e2e": {"value": batched["sustained_per_s"], "unit": "requests/s",
+                "h2d_bytes_per_step": batched["h2d_bytes"], "d2h_bytes_per_step": batched["d2h_bytes"]},
+        "gpu_launches": batched["gpu_launches"], "clocks": batched["clocks"], "cpu_baseline": None, "roofline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "W4":
+        serve_arm(args)
     else:
         gpu_arm(args)
 

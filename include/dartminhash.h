@@ -53,7 +53,8 @@ enum dm_status {
     DM_ECUDA = 3,      /* a CUDA runtime call failed */
     DM_ETIMEOUT = 4,   /* a bounded device wait gave up */
     DM_ERANGE = 5,     /* input outside the supported numeric range (see above) */
-    DM_EOVERFLOW = 6   /* the doubling loop of Theorem 1 reached its limit */
+    DM_EOVERFLOW = 6,  /* the doubling loop of Theorem 1 reached its limit */
+    DM_EAGAIN = 7      /* dm_server_submit: the admission budget is full now; retry later */
 };
 
 /* Create a context on CUDA device `device`.  `mem_budget_bytes` caps the device scratch the
@@ -134,17 +135,52 @@ enum dm_option {
     DM_OPT_PHI0 = 1,        /* initial phi of Theorem 1's loop, as value/1024 (default 1024 = 1.0) */
     DM_OPT_COUNTERS = 2,    /* device pointer to uint64[4] accumulating areas inspected, darts
                                generated, darts kept and passes (0 = off) */
-    DM_OPT_FORM = 3,        /* launch form: 0 = batched (default: sets classified by size and
-                               first rank limit, largest first, persistent warps claiming work,
+    DM_OPT_FORM = 3,        /* launch form: 0 = batched (default: sets classified by first rank
+                               limit and binned by a Lemma 2 estimate of their work, costliest
+                               first, persistent warps claiming work,
                                a block of 8 warps for each set of >= DM_OPT_LARGE_NNZ elements);
                                1 = plain (one warp per set in input order, static grid);
                                2 = persistent warps over the sets in input order */
     DM_OPT_WARPS_PER_BLOCK = 4, /* 1..8 warps (sets) per thread block, 0 = automatic */
     DM_OPT_LSH_PHI0 = 5,        /* initial phi of dm_lsh's loop, as value/1024 (default 4096 = 4.0) */
-    DM_OPT_LARGE_NNZ = 6        /* batched form: element count from which a set gets a whole block
+    DM_OPT_LARGE_NNZ = 6,       /* batched form: element count from which a set gets a whole block
                                    (default 2048; 0 = never; dm_lsh never does) */
+    DM_OPT_GRAPH = 7,           /* 1: launch each call's kernel sequence as a CUDA graph, cached per
+                                   context; a call identical to a cached one (same pointers, sizes,
+                                   seed and settings) replays it with one launch, a new call of the
+                                   same shape patches the least recently used executable in place.
+                                   Capture runs on a context-owned stream, so the caller's stream
+                                   may itself be under capture.  0 (default): plain launches. */
+    DM_OPT_TUNED = 8            /* 1 (default): calls use the settings dm_autotune stored for their
+                                   (kind, k, K, b), in place of the options above; 0: ignore them;
+                                   2: forget them */
 };
 int dm_set_option(dm_ctx *ctx, int option, int64_t value);
+
+/* The settings dm_autotune chose and what they measured. */
+typedef struct dm_tuning {
+    int32_t form;             /* DM_OPT_FORM value (0 batched or 2 persistent) */
+    int32_t warps_per_block;  /* warps per block actually used */
+    int32_t phi0_1024;        /* initial phi, as value/1024 */
+    int32_t large_nnz;        /* DM_OPT_LARGE_NNZ value */
+    int64_t sets_timed;       /* rows of the batch the trials ran on */
+    float ms_default;         /* median time of the trial batch with the context's options */
+    float ms_tuned;           /* median time with the chosen settings */
+} dm_tuning;
+
+/* Launch-setting search (the paper has no counterpart; results never depend on the choice).
+ * Runs the call that dm_sketch / dm_sketch_bbit (lsh = 0, K_or_b = b, 0 for keys only) or dm_lsh
+ * (lsh = 1, k = L, K_or_b = K) would make on the first min(n_sets, max_sets) rows (max_sets <= 0:
+ * 65536) of the given device batch, timing each candidate with CUDA events on `stream` (median of
+ * three runs after a warm-up): initial phi, then warps per block, then the large-set threshold,
+ * then the form, each kept when it is faster.  Outputs of the trials go to temporary device
+ * memory (counted against the budget); the caller's batch is only read.  The choice is stored in
+ * the context for later calls with the same (kind, k, K, b) (see DM_OPT_TUNED) and, when result is
+ * not NULL, written there.  Synchronous.  Returns DM_EINVAL for n_sets == 0 or bad arguments and
+ * the first kernel-recorded error of the trial runs (a bad weight) like dm_sync_status. */
+int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+                int64_t n_sets, int32_t lsh, int32_t k, int32_t K_or_b, uint64_t seed, int64_t max_sets,
+                dm_tuning *result, void *stream);
 
 /* t = ceil(k ln k) + k as the library computes it (Theorem 1's proof); 0 for k < 1. */
 int64_t dm_t_of_k(int32_t k);
@@ -152,6 +188,94 @@ int64_t dm_t_of_k(int32_t k);
 /* The Poisson(1) inversion thresholds the library uses: T[n] = ceil(2^32 P(Poi(1) <= n)),
  * n = 0..11, written to host array out[12]. */
 void dm_poisson_thresholds(uint32_t *out);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving loop (the paper has no counterpart: it sketches one set per call on a CPU).
+ * Requests of one weighted set each, with their own k and seed, are admitted against a memory
+ * budget and batched continuously onto several lanes (a lane = a CUDA stream with its own
+ * device and page-locked host buffer): whenever a lane is free it takes the oldest pending
+ * requests, groups them by (k, seed), copies them to the device in one transfer, sketches each
+ * group in one launch sequence and copies the keys back in one transfer.  Each request receives
+ * exactly the keys dm_sketch gives for its row alone.  All pointers here are HOST pointers.
+ * Thread safety: submit / poll / wait / stats may be called from any number of host threads.
+ * --------------------------------------------------------------------------------------- */
+typedef struct dm_server dm_server;
+
+typedef struct dm_server_config {
+    int32_t device;            /* CUDA device */
+    int32_t lanes;             /* batches in flight at once (streams), 1..64; 0 = 4 */
+    size_t mem_budget_bytes;   /* admission budget: device bytes of admitted, unfinished requests
+                                  (32 + 8 nnz + 8 k each); 0 = 8 GiB.  The lanes' buffers are also
+                                  kept within it */
+    size_t lane_bytes;         /* device (and page-locked host) buffer of each lane = the largest
+                                  batch; 0 = min(budget / lanes, 64 MiB) */
+    int32_t max_batch;         /* requests per batch; 0 = 4096 */
+    int32_t max_wait_us;       /* batching window: a free lane waits until the oldest pending
+                                  request is this old (or the batch is full); 0 = no wait */
+    int32_t per_request;       /* 1 = plain per-request form (one request per batch, plain launch):
+                                  the comparison the batching is measured against */
+    int32_t large_nnz;         /* a group with a set of at least this many elements runs the batched
+                                  form (a block per such set); other groups run persistent warps;
+                                  0 = 2048 */
+} dm_server_config;
+
+typedef struct dm_server_stats {
+    int64_t submitted;         /* admitted requests */
+    int64_t completed;         /* finished requests (including failed ones) */
+    int64_t failed;            /* finished with a non-zero status */
+    int64_t rejected;          /* DM_EAGAIN answers */
+    int64_t batches;
+    int64_t admitted_bytes;    /* currently admitted */
+    double mean_batch;         /* requests per batch */
+    double p50_us, p99_us, max_us;   /* latency from arrival to result ready, over the most recent
+                                        4,194,304 completions */
+    int64_t groups;            /* (k, seed) groups run: one launch sequence each */
+    int64_t kernel_launches;   /* kernels launched for them (since the server started) */
+} dm_server_stats;
+
+/* Start a server: creates the lanes (contexts, streams, buffers) and one worker thread per lane.
+ * DM_EINVAL for a bad configuration, DM_ENOMEM if the buffers cannot be allocated. */
+int dm_server_create(dm_server **out, const dm_server_config *cfg);
+
+/* Finish every admitted request, stop the workers and release everything. */
+int dm_server_destroy(dm_server *srv);
+
+/* Submit one set (indices uint32[nnz], weights float32[nnz], host memory; both are copied before
+ * the call returns) for k minhashes with `seed`.  The keys are written to out (host uint64[k],
+ * which must stay valid until the request is reported done; NULL = computed but not delivered).
+ * On DM_OK *ticket identifies the request for dm_server_poll / dm_server_wait, one of which must
+ * eventually report it done (that releases it).  DM_EAGAIN: the budget is full now (nothing was
+ * admitted; retry).  DM_EINVAL: bad k or a negative, NaN or infinite weight.  DM_ENOMEM: the
+ * request alone is larger than a lane. */
+int dm_server_submit(dm_server *srv, const uint32_t *indices, const float *weights, int64_t nnz, int32_t k,
+                     uint64_t seed, uint64_t *out, int64_t *ticket);
+
+/* Without blocking: *status = -1 while the request is pending, else its final status (DM_OK, or
+ * the error its batch or its row met), in which case the ticket is released.  Returns DM_EINVAL for
+ * an unknown or released ticket. */
+int dm_server_poll(dm_server *srv, int64_t ticket, int32_t *status);
+
+/* Block until the request is done (timeout_us < 0: no limit) and release the ticket; *status as
+ * for dm_server_poll.  Returns DM_ETIMEOUT if the limit passed first (the ticket stays valid). */
+int dm_server_wait(dm_server *srv, int64_t ticket, int64_t timeout_us, int32_t *status);
+
+/* Play a request trace in real time from the calling thread: request i (row i of the CSR
+ * indptr/indices/weights, k[i], seed[i]) is submitted arrival_ns[i] nanoseconds after the start
+ * (non-decreasing); one refused for lack of budget is resubmitted as capacity frees.  Returns when
+ * all are done.  out (NULL = not delivered) receives the keys of request i at offset
+ * k[0] + ... + k[i-1]; latency_ns[i] (may be NULL) the time from the scheduled arrival to result
+ * ready; status[i] (may be NULL) the request's status (requests failing the host checks get
+ * DM_EINVAL and latency 0 without being submitted). */
+int dm_server_replay(dm_server *srv, int64_t n, const int64_t *indptr, const uint32_t *indices,
+                     const float *weights, const int32_t *k, const uint64_t *seed, const int64_t *arrival_ns,
+                     uint64_t *out, int64_t *latency_ns, int32_t *status);
+
+int dm_server_get_stats(dm_server *srv, dm_server_stats *out);
+int dm_server_reset_stats(dm_server *srv);
+
+/* Host-side fault injection: the next `batches` batches fail before any GPU work is queued, as a
+ * failed launch would; their requests finish with DM_ECUDA and the server carries on. */
+int dm_server_fail_batches(dm_server *srv, int32_t batches);
 
 #ifdef __cplusplus
 }

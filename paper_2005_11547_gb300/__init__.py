@@ -21,10 +21,12 @@ from .build import LIB, build
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
            "dm_sketch_host", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
            "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
-           "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "FORM_BATCHED", "FORM_PLAIN",
-           "FORM_PERSISTENT"]
+           "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "FORM_BATCHED",
+           "FORM_PLAIN", "FORM_PERSISTENT", "dm_autotune", "Tuning", "Server", "EAGAIN"]
 
 OPT_PHI0, OPT_COUNTERS, OPT_FORM, OPT_WARPS_PER_BLOCK, OPT_LSH_PHI0, OPT_LARGE_NNZ = 1, 2, 3, 4, 5, 6
+OPT_GRAPH, OPT_TUNED = 7, 8
+EAGAIN, ETIMEOUT = 7, 4
 FORM_BATCHED, FORM_PLAIN, FORM_PERSISTENT = 0, 1, 2
 _lock = threading.Lock()
 _lib = None
@@ -61,6 +63,16 @@ def load(path: str | None = None):
             "dm_t_of_k": ([i32], i64),
             "dm_poisson_thresholds": ([P], None),
             "dm_sketch_noalloc": ([P, P, P, i64, i32, u64, P, P], ctypes.c_int),
+            "dm_autotune": ([P, P, P, P, i64, i32, i32, i32, u64, i64, P, P], ctypes.c_int),
+            "dm_server_create": ([ctypes.POINTER(P), P], ctypes.c_int),
+            "dm_server_destroy": ([P], ctypes.c_int),
+            "dm_server_submit": ([P, P, P, i64, i32, u64, P, P], ctypes.c_int),
+            "dm_server_poll": ([P, i64, P], ctypes.c_int),
+            "dm_server_wait": ([P, i64, i64, P], ctypes.c_int),
+            "dm_server_replay": ([P, i64, P, P, P, P, P, P, P, P, P], ctypes.c_int),
+            "dm_server_get_stats": ([P, P], ctypes.c_int),
+            "dm_server_reset_stats": ([P], ctypes.c_int),
+            "dm_server_fail_batches": ([P, i32], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -213,6 +225,29 @@ def dm_sketch_noalloc(indptr, indices, weights, k: int, seed: int, out, stream=N
 NOALLOC_MAX_SETS = 262144
 
 
+class Tuning(ctypes.Structure):
+    """dm_tuning: the settings dm_autotune chose."""
+    _fields_ = [("form", ctypes.c_int32), ("warps_per_block", ctypes.c_int32), ("phi0_1024", ctypes.c_int32),
+                ("large_nnz", ctypes.c_int32), ("sets_timed", ctypes.c_int64), ("ms_default", ctypes.c_float),
+                ("ms_tuned", ctypes.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def dm_autotune(ctx: Context, indptr, indices, weights, k: int, seed: int, b: int = 0, lsh_K: int = 0,
+                max_sets: int = 0, stream=None) -> dict:
+    """Time launch settings on a prefix of a device batch and store the fastest in the context
+    for later calls of the same kind.  Sketches: k, b (0 = keys only); LSH: k = L and lsh_K = K."""
+    n, ip, ix, w = _csr_ptrs(indptr, indices, weights)
+    res = Tuning()
+    lsh = 1 if lsh_K > 0 else 0
+    _check(load().dm_autotune(ctx.handle, ip, ix, w, n, lsh, int(k), int(lsh_K if lsh else b),
+                              int(seed) & (2**64 - 1), int(max_sets), ctypes.cast(ctypes.byref(res), ctypes.c_void_p),
+                              _stream(stream)), "dm_autotune")
+    return res.as_dict()
+
+
 def dm_sync_status(ctx: Context, stream=None, raise_on_error: bool = True) -> int:
     rc = load().dm_sync_status(ctx.handle, _stream(stream))
     if rc and raise_on_error:
@@ -236,3 +271,118 @@ def dm_poisson_thresholds():
     arr = (ctypes.c_uint32 * 12)()
     load().dm_poisson_thresholds(ctypes.cast(arr, ctypes.c_void_p))
     return [int(v) for v in arr]
+
+
+class ServerConfig(ctypes.Structure):
+    """dm_server_config."""
+    _fields_ = [("device", ctypes.c_int32), ("lanes", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_size_t),
+                ("lane_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("max_wait_us", ctypes.c_int32),
+                ("per_request", ctypes.c_int32), ("large_nnz", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    """dm_server_stats."""
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("batches", ctypes.c_int64), ("admitted_bytes", ctypes.c_int64),
+                ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("groups", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+
+
+def _host_ptr(a, dtype, what):
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.dtype(dtype) or not a.flags.c_contiguous:
+        raise TypeError(f"{what} must be a contiguous numpy {dtype} array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Server:
+    """Owns a dm_server*: continuous batching of single-set requests (host arrays)."""
+
+    def __init__(self, device: int = 0, lanes: int = 0, mem_budget_bytes: int = 0, lane_bytes: int = 0,
+                 max_batch: int = 0, max_wait_us: int = 0, per_request: bool = False, large_nnz: int = 0):
+        cfg = ServerConfig(device, lanes, mem_budget_bytes, lane_bytes, max_batch, max_wait_us,
+                           1 if per_request else 0, large_nnz)
+        h = ctypes.c_void_p()
+        _check(load().dm_server_create(ctypes.byref(h), ctypes.cast(ctypes.byref(cfg), ctypes.c_void_p)),
+               "dm_server_create")
+        self.handle = h
+        self._keep = {}          # ticket -> output array kept alive until the request is released
+
+    def close(self):
+        if self.handle:
+            load().dm_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, indices, weights, k: int, seed: int, out=None):
+        """Returns (status, ticket, out): status 0 or EAGAIN (ticket None then); raises on other
+        errors.  out: numpy uint64[k] receiving the keys (allocated when None)."""
+        import numpy as np
+        if out is None:
+            out = np.empty(k, dtype=np.uint64)
+        t = ctypes.c_int64()
+        nnz = len(indices)
+        rc = load().dm_server_submit(self.handle, _host_ptr(indices, np.uint32, "indices"),
+                                     _host_ptr(weights, np.float32, "weights"), nnz, int(k),
+                                     int(seed) & (2**64 - 1), _host_ptr(out, np.uint64, "out"), ctypes.byref(t))
+        if rc == EAGAIN:
+            return rc, None, out
+        _check(rc, "dm_server_submit")
+        self._keep[t.value] = out
+        return 0, t.value, out
+
+    def poll(self, ticket: int):
+        """None while pending, else the request's status (and the ticket is released)."""
+        st = ctypes.c_int32()
+        _check(load().dm_server_poll(self.handle, int(ticket), ctypes.byref(st)), "dm_server_poll")
+        if st.value == -1:
+            return None
+        self._keep.pop(ticket, None)
+        return st.value
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """The request's status; None if the timeout passed first."""
+        st = ctypes.c_int32()
+        rc = load().dm_server_wait(self.handle, int(ticket), int(timeout_us), ctypes.byref(st))
+        if rc == ETIMEOUT:
+            return None
+        _check(rc, "dm_server_wait")
+        self._keep.pop(ticket, None)
+        return st.value
+
+    def replay(self, indptr, indices, weights, ks, seeds, arrival_ns, deliver: bool = True):
+        """Plays a trace in real time; returns (keys or None, latency_ns, status)."""
+        import numpy as np
+        n = len(indptr) - 1
+        ks = np.ascontiguousarray(ks, dtype=np.int32)
+        seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        arrival_ns = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        out = np.empty(int(ks.astype(np.int64).sum()), dtype=np.uint64) if deliver else None
+        lat = np.empty(n, dtype=np.int64)
+        st = np.empty(n, dtype=np.int32)
+        _check(load().dm_server_replay(self.handle, n, _host_ptr(indptr, np.int64, "indptr"),
+                                       _host_ptr(indices, np.uint32, "indices"), _host_ptr(weights, np.float32, "weights"),
+                                       _host_ptr(ks, np.int32, "k"), _host_ptr(seeds, np.uint64, "seed"),
+                                       _host_ptr(arrival_ns, np.int64, "arrival_ns"),
+                                       _host_ptr(out, np.uint64, "out") if deliver else None,
+                                       _host_ptr(lat, np.int64, "latency"), _host_ptr(st, np.int32, "status")),
+               "dm_server_replay")
+        return out, lat, st
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().dm_server_get_stats(self.handle, ctypes.cast(ctypes.byref(s), ctypes.c_void_p)),
+               "dm_server_get_stats")
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def reset_stats(self):
+        _check(load().dm_server_reset_stats(self.handle), "dm_server_reset_stats")
+
+    def fail_batches(self, n: int):
+        _check(load().dm_server_fail_batches(self.handle, int(n)), "dm_server_fail_batches")

@@ -9,11 +9,47 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "dm_device.cuh"
 #include "dm_internal.h"
 
 using dm::SketchParams;
+
+namespace {
+
+// Launch settings of one call.  None of them changes an output bit (the results are independent
+// of phi0, the form and the launch shape); they only move work around.
+struct Choice {
+    int form;           // 0 batched, 1 plain, 2 persistent in input order
+    int wpb;            // warps (sets) per block, 0 = automatic
+    float phi0;         // initial phi of Theorem 1's loop
+    int large_nnz;      // batched form: element count from which a set gets a whole block
+};
+
+struct TunedEntry {
+    bool lsh;
+    int k, K, b;
+    Choice c;
+};
+
+// Everything a call's launch sequence depends on.  Built zero-filled (padding included) so two
+// plans compare equal with memcmp exactly when the launches would be identical.
+struct Plan {
+    SketchParams p;
+    int lsh, bbit, count, form, grid_fast, grid_general, grid_large;
+};
+
+struct GraphEntry {
+    Plan plan;
+    cudaGraphExec_t exec;
+    uint64_t used;
+};
+
+constexpr size_t kMaxGraphs = 16;
+
+}  // namespace
 
 struct dm_ctx {
     int device = 0;
@@ -35,6 +71,16 @@ struct dm_ctx {
     // general-kernel work queue for calls on device buffers: int32[queue_cap] + a counter
     void *d_queue = nullptr;
     int64_t queue_cap = 0;
+    // launch settings that dm_autotune chose, per (kind, k, K, b)
+    std::vector<TunedEntry> tuned;
+    bool use_tuned = true;
+    // CUDA-graph replay of repeated identical calls
+    bool use_graph = false;
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_tick = 0;
+    cudaStream_t capture_stream = nullptr;
+    // resident blocks per SM, per kernel and launch shape
+    std::vector<std::pair<uint64_t, int>> occupancy;
 };
 
 namespace {
@@ -133,11 +179,33 @@ int ensure_queue(dm_ctx *ctx, int64_t n_sets) {
     return DM_OK;
 }
 
-// One batched call: sketches (lsh = false: k minhashes, optional b-bit words) or (L, K) LSH
-// (lsh = true: k = L).  queue: scratch for the general kernel's work queue (null = context's).
-int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
-             int64_t n_sets, bool lsh, int32_t k, int32_t K, int32_t b, uint64_t seed, uint64_t *out_words,
-             uint64_t *out_keys, uint32_t *out_lsh, cudaStream_t st, void *queue = nullptr) {
+// Blocks of a kernel resident per SM, cached per context (the query sets a kernel attribute
+// and costs a few microseconds).  which: 0 fast, 1 general, 2 large.
+int occupancy(dm_ctx *ctx, int which, bool lsh, bool bbit, int wpb, size_t smem) {
+    const uint64_t key = ((uint64_t)which) | ((uint64_t)lsh << 2) | ((uint64_t)bbit << 3) |
+                         ((uint64_t)wpb << 4) | ((uint64_t)smem << 12);
+    for (auto &e : ctx->occupancy)
+        if (e.first == key) return e.second;
+    int nb = which == 2 ? dm::large_blocks_per_sm(bbit, wpb, smem) : dm::blocks_per_sm(lsh, which, bbit, wpb, smem);
+    ctx->occupancy.emplace_back(key, nb);
+    return nb;
+}
+
+Choice choose(const dm_ctx *ctx, bool lsh, int k, int K, int b) {
+    Choice c{ctx->form, ctx->warps_per_block, lsh ? ctx->phi0_lsh : ctx->phi0, ctx->large_nnz};
+    if (ctx->use_tuned)
+        for (const auto &e : ctx->tuned)
+            if (e.lsh == lsh && e.k == k && e.K == K && e.b == b) return e.c;
+    return c;
+}
+
+// Checks a call and fills its plan: sketches (lsh = false: k minhashes, optional b-bit words)
+// or (L, K) LSH (lsh = true: k = L).  queue: scratch for the call's work queue (null = the
+// context's).  Returns DM_OK with pl.p.n_sets == 0 when there is nothing to launch.
+int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+              int64_t n_sets, bool lsh, int32_t k, int32_t K, int32_t b, uint64_t seed, uint64_t *out_words,
+              uint64_t *out_keys, uint32_t *out_lsh, void *queue, const Choice &ch, Plan &pl) {
+    std::memset(&pl, 0, sizeof(pl));
     if (!ctx) return DM_EINVAL;
     int rc = check_csr(indptr, indices, weights, n_sets);
     if (rc) return rc;
@@ -156,7 +224,7 @@ int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const 
     if (bbit && !out_words) return DM_EINVAL;
     if (n_sets == 0) return DM_OK;
     if (n_sets > 0x7FFFFFFF) return DM_EINVAL;
-    const int wpb = ctx->warps_per_block > 0 ? ctx->warps_per_block : auto_warps(lsh, k, K);
+    const int wpb = ch.wpb > 0 ? ch.wpb : auto_warps(lsh, k, K);
     const size_t smem_fast = dm::warp_bytes(lsh, k, K, 0) * wpb, smem = dm::warp_bytes(lsh, k, K, 1) * wpb;
     if (smem > 227 * 1024 || smem_fast > 227 * 1024) return DM_EINVAL;     // L and K too large for LSH
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -165,8 +233,7 @@ int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const 
         if ((rc = ensure_queue(ctx, n_sets)) != DM_OK) return rc;
         queue = ctx->d_queue;
     }
-    SketchParams p;
-    std::memset(&p, 0, sizeof(p));
+    SketchParams &p = pl.p;
     p.indptr = indptr;
     p.indices = indices;
     p.weights = weights;
@@ -175,7 +242,7 @@ int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const 
     p.K = lsh ? K : 0;
     p.t = (uint32_t)t;
     p.sigma = dm::mix64(seed ^ dm::kSeedSalt);
-    p.phi0 = lsh ? ctx->phi0_lsh : ctx->phi0;
+    p.phi0 = ch.phi0;
     p.b = bbit ? b : 0;
     p.words = bbit ? (int32_t)(((int64_t)k * b + 63) / 64) : 0;
     p.out_keys = out_keys;
@@ -188,30 +255,154 @@ int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const 
     p.warp_bytes_fast = (int32_t)dm::warp_bytes(lsh, k, K, 0);
     p.sink_bytes = (int32_t)dm::sink_bytes(lsh, k, K);
     dm::carve_call_scratch(queue, n_sets, p);
-    const bool count = ctx->counters != nullptr;
+    pl.lsh = lsh;
+    pl.bbit = bbit;
+    pl.count = ctx->counters != nullptr;
+    pl.form = ch.form;
     const int64_t blocks = (n_sets + wpb - 1) / wpb;
-    if (ctx->form == 1) {
+    if (ch.form == 1) {
         // plain form: one warp per set in input order, a block per wpb sets
         p.sched = 1;
-        return cuda_fail(dm::launch_sets(p, lsh, bbit, count, (int)blocks, (int)blocks, st));
+        pl.grid_fast = pl.grid_general = (int)blocks;
+        return DM_OK;
     }
     // persistent grids: as many blocks as can be resident, never more than there are sets
-    const int64_t cap0 = (int64_t)ctx->sm_count * dm::blocks_per_sm(lsh, 0, bbit, wpb, smem_fast);
-    const int64_t cap1 = (int64_t)ctx->sm_count * dm::blocks_per_sm(lsh, 1, bbit, wpb, smem);
-    const int grid = (int)(blocks < cap0 ? blocks : cap0);
-    const int grid_general = (int)(blocks < cap1 ? blocks : cap1);
-    if (ctx->form == 2) return cuda_fail(dm::launch_sets(p, lsh, bbit, count, grid, grid_general, st));
+    const int64_t cap0 = (int64_t)ctx->sm_count * occupancy(ctx, 0, lsh, bbit, wpb, smem_fast);
+    const int64_t cap1 = (int64_t)ctx->sm_count * occupancy(ctx, 1, lsh, bbit, wpb, smem);
+    pl.grid_fast = (int)(blocks < cap0 ? blocks : cap0);
+    pl.grid_general = (int)(blocks < cap1 ? blocks : cap1);
+    if (ch.form == 2) return DM_OK;
     // batched form (default): large sets get a block of 8 warps
     p.large_warps = 8;
-    p.large_nnz = lsh ? 0 : ctx->large_nnz;
-    int grid_large = 0;
+    p.large_nnz = lsh ? 0 : ch.large_nnz;
     if (p.large_nnz > 0) {
         const size_t lb = dm::large_block_bytes(k, p.large_warps);
-        if (lb <= 227 * 1024) grid_large = ctx->sm_count * dm::large_blocks_per_sm(bbit, p.large_warps, lb);
+        if (lb <= 227 * 1024) pl.grid_large = ctx->sm_count * occupancy(ctx, 2, false, bbit, p.large_warps, lb);
         else p.large_nnz = 0;
     }
-    return cuda_fail(dm::launch_batched(p, lsh, bbit, count, grid, grid_general, grid_large, st));
+    return DM_OK;
 }
+
+cudaError_t launch_plan(const Plan &pl, cudaStream_t st) {
+    if (pl.form == 0)
+        return dm::launch_batched(pl.p, pl.lsh, pl.bbit, pl.count, pl.grid_fast, pl.grid_general, pl.grid_large, st);
+    return dm::launch_sets(pl.p, pl.lsh, pl.bbit, pl.count, pl.grid_fast, pl.grid_general, st);
+}
+
+void drop_graphs(dm_ctx *ctx) {
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
+
+// Launches a plan, directly or (graph replay on) from a cached graph executable.  A plan seen
+// before is replayed as is; a new plan is captured on the context's capture stream and either
+// patched into the least recently used executable (when its launch sequence has the same
+// shape) or instantiated, the cache holding at most kMaxGraphs.
+int run_plan(dm_ctx *ctx, const Plan &pl, cudaStream_t st) {
+    if (!ctx->use_graph) return cuda_fail(launch_plan(pl, st));
+    for (auto &g : ctx->graphs)
+        if (std::memcmp(&g.plan, &pl, sizeof(Plan)) == 0) {
+            g.used = ++ctx->graph_tick;
+            return cuda_fail(cudaGraphLaunch(g.exec, st));
+        }
+    cudaError_t e;
+    if (!ctx->capture_stream &&
+        (e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_fail(e);
+    cudaError_t el = launch_plan(pl, ctx->capture_stream);
+    e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+    if (el != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(el != cudaSuccess ? el : e);
+    }
+    // same shape: same kernels in the same order (form, kind, templates, large kernel on/off)
+    auto same_shape = [&](const Plan &a) {
+        return a.form == pl.form && a.lsh == pl.lsh && a.bbit == pl.bbit && a.count == pl.count &&
+               (a.grid_large > 0 && a.p.large_nnz > 0) == (pl.grid_large > 0 && pl.p.large_nnz > 0);
+    };
+    GraphEntry *slot = nullptr;
+    for (auto &g : ctx->graphs)
+        if (same_shape(g.plan) && (!slot || g.used < slot->used)) slot = &g;
+    bool ready = false;
+    if (slot) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(slot->exec, graph, &info) == cudaSuccess) ready = true;
+        else cudaGetLastError();      // clear the update's error; instantiate below instead
+    }
+    if (!ready) {
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return cuda_fail(e);
+        }
+        if (ctx->graphs.size() >= kMaxGraphs) {
+            slot = &ctx->graphs[0];
+            for (auto &g : ctx->graphs)
+                if (g.used < slot->used) slot = &g;
+            cudaGraphExecDestroy(slot->exec);
+        } else {
+            ctx->graphs.push_back(GraphEntry{});
+            slot = &ctx->graphs.back();
+        }
+        slot->exec = exec;
+    }
+    cudaGraphDestroy(graph);
+    std::memcpy(&slot->plan, &pl, sizeof(Plan));
+    slot->used = ++ctx->graph_tick;
+    return cuda_fail(cudaGraphLaunch(slot->exec, st));
+}
+
+int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+             int64_t n_sets, bool lsh, int32_t k, int32_t K, int32_t b, uint64_t seed, uint64_t *out_words,
+             uint64_t *out_keys, uint32_t *out_lsh, cudaStream_t st, void *queue = nullptr,
+             const Choice *force = nullptr) {
+    if (!ctx) return DM_EINVAL;
+    const Choice ch = force ? *force : choose(ctx, lsh, k, K, b);
+    Plan pl;
+    int rc = plan_call(ctx, indptr, indices, weights, n_sets, lsh, k, K, b, seed, out_words, out_keys, out_lsh,
+                       queue, ch, pl);
+    if (rc || pl.p.n_sets == 0) return rc;
+    return run_plan(ctx, pl, st);
+}
+
+}  // namespace
+
+// Helpers of the serving loop (declared in dm_internal.h).
+namespace dm {
+
+int serve_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+                 int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *queue, int form, cudaStream_t st) {
+    if (!ctx) return DM_EINVAL;
+    Choice c = choose(ctx, false, k, 0, 0);
+    c.form = form;
+    return run_sets(ctx, indptr, indices, weights, n_sets, false, k, 0, 0, seed, nullptr, out, nullptr, st, queue,
+                    &c);
+}
+
+cudaError_t status_to_host(dm_ctx *ctx, cudaStream_t st) {
+    return cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+}
+
+int status_take(dm_ctx *ctx, cudaStream_t st) {
+    const int s = *ctx->h_status;
+    if (s) {
+        *ctx->h_status = 0;
+        cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return DM_ECUDA;
+    }
+    return s;
+}
+
+int context_large_nnz(const dm_ctx *ctx) { return ctx->large_nnz; }
+
+}  // namespace dm
+
+namespace {
 
 int run_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
                int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_words,
@@ -261,6 +452,8 @@ int dm_destroy(dm_ctx *ctx) {
     for (int i = 0; i < 2; ++i)
         if (ctx->copy_stream[i]) cudaStreamDestroy(ctx->copy_stream[i]);
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+    drop_graphs(ctx);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     delete ctx;
     return DM_OK;
 }
@@ -365,6 +558,125 @@ int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
     return DM_OK;
 }
 
+int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+                int64_t n_sets, int32_t lsh, int32_t k, int32_t K_or_b, uint64_t seed, int64_t max_sets,
+                dm_tuning *result, void *stream) {
+    if (!ctx || (lsh != 0 && lsh != 1)) return DM_EINVAL;
+    int rc = check_csr(indptr, indices, weights, n_sets);
+    if (rc) return rc;
+    const bool is_lsh = lsh == 1;
+    const int K = is_lsh ? K_or_b : 0, b = is_lsh ? 0 : K_or_b;
+    if (n_sets == 0) return DM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int64_t n = n_sets < (max_sets > 0 ? max_sets : 65536) ? n_sets : (max_sets > 0 ? max_sets : 65536);
+
+    // the prefix's largest row decides whether the large-set threshold is worth trying
+    std::vector<int64_t> ip((size_t)n + 1);
+    if ((e = cudaMemcpyAsync(ip.data(), indptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e);
+    int64_t max_nnz = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        if (ip[s + 1] < ip[s]) return DM_EINVAL;
+        max_nnz = ip[s + 1] - ip[s] > max_nnz ? ip[s + 1] - ip[s] : max_nnz;
+    }
+
+    // outputs of the trial runs go to scratch (the caller's buffers are not touched)
+    const int64_t words = b > 0 ? ((int64_t)k * b + 63) / 64 : 0;
+    const size_t out_bytes = is_lsh ? (size_t)n * k * 4 : (b > 0 ? (size_t)n * words * 8 : (size_t)n * k * 8);
+    if (is_lsh ? (k < 1 || k > 1024 || K < 1 || K > 32)
+               : (k < 1 || k > 8192 || !(b == 0 || b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32)))
+        return DM_EINVAL;
+    if ((rc = ensure_queue(ctx, n)) != DM_OK) return rc;
+    if (ctx->budget && out_bytes + queue_bytes(ctx->queue_cap) + ctx->d_stage_bytes > ctx->budget) return DM_ENOMEM;
+    void *d_out = nullptr;
+    if ((e = cudaMalloc(&d_out, out_bytes)) != cudaSuccess) return cuda_fail(e);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    for (auto &x : ev)
+        if ((e = cudaEventCreate(&x)) != cudaSuccess) break;
+
+    // median of three timed runs after one warm-up; +inf if the choice is rejected
+    auto time_choice = [&](const Choice &c, float &ms) -> int {
+        float v[3];
+        for (int r = 0; r < 4; ++r) {
+            cudaError_t er = cudaEventRecord(ev[0], st);
+            if (er != cudaSuccess) return cuda_fail(er);
+            int q = run_sets(ctx, indptr, indices, weights, n, is_lsh, k, K, b, seed,
+                             (!is_lsh && b > 0) ? (uint64_t *)d_out : nullptr,
+                             (!is_lsh && b == 0) ? (uint64_t *)d_out : nullptr,
+                             is_lsh ? (uint32_t *)d_out : nullptr, st, nullptr, &c);
+            if (q == DM_EINVAL) {
+                ms = 3.0e38f;
+                return DM_OK;
+            }
+            if (q) return q;
+            if ((er = cudaEventRecord(ev[1], st)) != cudaSuccess || (er = cudaEventSynchronize(ev[1])) != cudaSuccess)
+                return cuda_fail(er);
+            if (r > 0 && (er = cudaEventElapsedTime(&v[r - 1], ev[0], ev[1])) != cudaSuccess) return cuda_fail(er);
+        }
+        float lo = v[0] < v[1] ? v[0] : v[1], hi = v[0] < v[1] ? v[1] : v[0];
+        ms = v[2] < lo ? lo : (v[2] > hi ? hi : v[2]);
+        return DM_OK;
+    };
+
+    const bool use_graph = ctx->use_graph;
+    ctx->use_graph = false;                          // trials of one-off plans
+    Choice best{ctx->form == 1 ? 0 : ctx->form, ctx->warps_per_block, is_lsh ? ctx->phi0_lsh : ctx->phi0,
+                ctx->large_nnz};
+    float best_ms = 0.f, default_ms = 0.f;
+    rc = e == cudaSuccess ? time_choice(best, best_ms) : cuda_fail(e);
+    default_ms = best_ms;
+    // coordinate search: phi0, then warps per block, then the large-set threshold, then the form
+    auto try_set = [&](auto apply, const auto &values) {
+        for (auto v : values) {
+            if (rc) return;
+            Choice c = best;
+            apply(c, v);
+            float ms = 0.f;
+            rc = time_choice(c, ms);
+            if (!rc && ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    };
+    if (!rc) {
+        const std::vector<float> phis = is_lsh ? std::vector<float>{2.f, 3.f, 4.f, 6.f, 8.f}
+                                               : std::vector<float>{1.f, 1.25f, 1.5f, 2.f};
+        try_set([](Choice &c, float v) { c.phi0 = v; }, phis);
+        try_set([](Choice &c, int v) { c.wpb = v; }, std::vector<int>{2, 4, 8});
+        if (!is_lsh && max_nnz >= 1024)
+            try_set([](Choice &c, int v) { c.large_nnz = v; }, std::vector<int>{0, 1024, 2048, 4096, 8192});
+        try_set([](Choice &c, int v) { c.form = v; }, std::vector<int>{0, 2});
+    }
+    ctx->use_graph = use_graph;
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    cudaFree(d_out);
+    if (rc) return rc;
+    // trial runs of rows with bad weights recorded an error: report it like a call would
+    if ((rc = dm_sync_status(ctx, stream)) != DM_OK) return rc;
+    bool found = false;
+    for (auto &t : ctx->tuned)
+        if (t.lsh == is_lsh && t.k == k && t.K == K && t.b == b) {
+            t.c = best;
+            found = true;
+        }
+    if (!found) ctx->tuned.push_back(TunedEntry{is_lsh, k, K, b, best});
+    if (result) {
+        result->form = best.form;
+        result->warps_per_block = best.wpb > 0 ? best.wpb : auto_warps(is_lsh, k, K);
+        result->phi0_1024 = (int32_t)(best.phi0 * 1024.0f + 0.5f);
+        result->large_nnz = best.large_nnz;
+        result->sets_timed = n;
+        result->ms_default = default_ms;
+        result->ms_tuned = best_ms;
+    }
+    return DM_OK;
+}
+
 int dm_sync_status(dm_ctx *ctx, void *stream) {
     if (!ctx) return DM_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -390,6 +702,7 @@ const char *dm_strerror(int status) {
         case DM_ETIMEOUT: return "bounded device wait gave up";
         case DM_ERANGE: return "input outside the supported numeric range";
         case DM_EOVERFLOW: return "rank-limit doubling reached its limit";
+        case DM_EAGAIN: return "admission budget full; retry later";
         default: return "unknown status";
     }
 }
@@ -419,6 +732,19 @@ int dm_set_option(dm_ctx *ctx, int option, int64_t value) {
         case DM_OPT_WARPS_PER_BLOCK:
             if (value < 0 || value > 8) return DM_EINVAL;   // kernels are built for <= 256 threads
             ctx->warps_per_block = (int)value;
+            return DM_OK;
+        case DM_OPT_GRAPH:
+            if (value < 0 || value > 1) return DM_EINVAL;
+            ctx->use_graph = value != 0;
+            if (!ctx->use_graph) {
+                cudaSetDevice(ctx->device);
+                drop_graphs(ctx);
+            }
+            return DM_OK;
+        case DM_OPT_TUNED:
+            if (value < 0 || value > 2) return DM_EINVAL;
+            if (value == 2) ctx->tuned.clear();              // forget every dm_autotune choice
+            else ctx->use_tuned = value != 0;
             return DM_OK;
         default:
             return DM_EINVAL;

@@ -57,7 +57,8 @@ cudaError_t upload_poisson_table(const uint32_t *T);
 cudaError_t launch_sets(const SketchParams &p, bool lsh, bool bbit, bool count, int grid_fast, int grid_general,
                         cudaStream_t st);
 
-// Batched form: classification (fast / general / large, largest first), then the persistent
+// Batched form: classification (fast / general / large, costliest first by a Lemma 2 work
+// estimate), then the persistent
 // fast kernel, the persistent general kernel (general sets and those the fast kernel defers)
 // and, for sketches, the block-per-set kernel over large sets.  grid_large = 0: no large class.
 cudaError_t launch_batched(const SketchParams &p, bool lsh, bool bbit, bool count, int grid_fast,
@@ -70,5 +71,15 @@ int large_blocks_per_sm(bool bbit, int warps, size_t smem);
 // Scratch of one call: queue, order, classes and the small header (counters, histogram).
 size_t call_scratch_bytes(int64_t n_sets);
 void carve_call_scratch(void *base, int64_t n_sets, SketchParams &p);
+
+// Serving loop helpers (dm_api.cu).  serve_sketch: one dm_sketch call with the call's scratch at
+// `queue` (call_scratch_bytes(n_sets) bytes) and the given launch form.  status_to_host queues a
+// copy of the context's status word to its pinned host copy; status_take, once the stream has
+// been synchronized, returns that word and clears it on the device when it was set.
+int serve_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+                 int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *queue, int form, cudaStream_t st);
+cudaError_t status_to_host(dm_ctx *ctx, cudaStream_t st);
+int status_take(dm_ctx *ctx, cudaStream_t st);
+int context_large_nnz(const dm_ctx *ctx);
 
 }  // namespace dm

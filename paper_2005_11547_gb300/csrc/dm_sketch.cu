@@ -752,25 +752,42 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) set_kernel(const Sketc
 
 // ==========================================================================================
 // Batched form.  classify: per set, class (0 fast: first limit below 1; 1 general; 2 large:
-// >= large_nnz elements, sketches only) and a size bin that sorts larger sets first
-// (bin = 31 - floor(log2(nnz + 1))); scan: bin offsets per class; scatter: fast sets to
-// order[0..nF), general sets to queue[0..nG) (the general kernel's list; the fast kernel
-// appends the sets it defers after them), large sets to order[nF..nF+nL).
+// >= large_nnz elements, sketches only) and a size bin that sorts costlier sets first:
+// bin = 31 - floor(log2(E)) with E the Lemma 2 estimate of the areas inspected at the first
+// limit theta = phi0 / |x|_1,
+//     E = phi0 t + sum_i (log2(1 + t x_i) + 1) + nnz log2(1 + theta)
+// (the linear term, then per element the weight regions and the rank regions).  scan: bin
+// offsets per class; scatter: fast sets to order[0..nF), general sets to queue[0..nG) (the
+// general kernel's list; the fast kernel appends the sets it defers after them), large sets to
+// order[nF..nF+nL).  The estimate only orders work; it never changes a result.
 // ==========================================================================================
 __global__ void __launch_bounds__(256) classify_kernel(const SketchParams p) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const float t = (float)p.t;
     for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < p.n_sets; s += nw) {
         const int64_t beg = p.indptr[s], end = p.indptr[s + 1], nnz = end - beg;
-        float l1 = 0.f;
-        for (int64_t i = beg + lane; i < end; i += 32) l1 += p.weights[i];
+        float l1 = 0.f, wlog = 0.f;
+        for (int64_t i = beg + lane; i < end; i += 32) {
+            const float x = p.weights[i];
+            l1 += x;
+            if (x > 0.f) wlog += __log2f(1.0f + t * x) + 1.0f;
+        }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(kFull, l1, o);
+        for (int o = 16; o; o >>= 1) {
+            l1 += __shfl_xor_sync(kFull, l1, o);
+            wlog += __shfl_xor_sync(kFull, wlog, o);
+        }
         if (lane == 0) {
             int c;
             if (p.large_nnz > 0 && nnz >= p.large_nnz) c = 2;
             else c = (!(l1 > 0.f) || __fdiv_rn(p.phi0, l1) < 1.0f) ? 0 : 1;   // zero/invalid rows: fast
-            const int bin = 31 - (63 - __clzll((long long)(nnz + 1)));
+            float est = 1.0f;
+            if (l1 > 0.f && l1 < 3.0e38f && wlog < 3.0e38f)
+                est += p.phi0 * t + wlog + (float)nnz * __log2f(1.0f + p.phi0 / l1);
+            // floor(log2(est)) from the exponent field (est >= 1, finite or +inf)
+            int lg = (int)((__float_as_uint(est) >> 23) & 0xFFu) - 127;
+            const int bin = 31 - (lg > 31 ? 31 : lg);
             p.cls[s] = (uint8_t)(c * kBins + (bin < 0 ? 0 : bin));
             atomicAdd(&p.hist[c * kBins + (bin < 0 ? 0 : bin)], 1u);
         }
