@@ -132,14 +132,6 @@ __device__ __forceinline__ uint64_t cols(int nu, int rho, int nutop, uint64_t F)
     return rho == 0 ? 1ull : (F >> (64 - rho)) + 1;          // floor(f 2^rho) + 1
 }
 
-// Binary32 bit pattern, rounded toward zero, of rank = P 2^-S (P < 2^63, S <= 62).
-__device__ __forceinline__ uint32_t rank_code(uint64_t P, int S) {
-    if (P == 0) return 0;
-    int L = bitlen64(P);
-    uint64_t mant = (L >= 24) ? (P >> (L - 24)) : (P << (24 - L));
-    return ((uint32_t)(L + 125 - S) << 23) + (uint32_t)mant;   // biased exp = L + 126 - S
-}
-
 __device__ __forceinline__ uint32_t fastrange32(uint32_t h, uint32_t n) {
     return (uint32_t)(((uint64_t)h * n) >> 32);
 }

@@ -83,12 +83,13 @@ struct SketchSink {
         for (uint32_t j = lane; j < k; j += 32) slots[j] = ~0ull;
         __syncwarp();
     }
-    __device__ __forceinline__ void put(uint64_t qh, uint32_t code) {
+    __device__ __forceinline__ bool put(uint64_t qh, uint32_t code) {
         const uint32_t slot = fastrange32((uint32_t)(qh >> 32), k);
         atomicMin(reinterpret_cast<unsigned long long *>(&slots[slot]),
                   (unsigned long long)(((uint64_t)code << 32) | (uint32_t)qh));
+        return false;
     }
-    __device__ __forceinline__ void after_batch(int) {}
+    __device__ __forceinline__ void after_batch(int, bool) {}
     __device__ bool filled(int lane) {
         bool empty = false;
         for (uint32_t j = lane; j < k; j += 32) empty |= (slots[j] == ~0ull);
@@ -160,10 +161,11 @@ struct LshSink {
         if (lane == 0) *ovf_n = 0;
         __syncwarp();
     }
-    __device__ __forceinline__ void put(uint64_t qh, uint32_t code) {
+    // Returns true when the bucket is now full (or overflowed): after_batch must compact.
+    __device__ __forceinline__ bool put(uint64_t qh, uint32_t code) {
         const uint32_t b = fastrange32((uint32_t)(qh >> 32), L);
         const uint64_t key = ((uint64_t)code << 32) | (uint32_t)qh;
-        if (key >= tau[b]) return;
+        if (key >= tau[b]) return false;
         const uint32_t pos = atomicAdd(&cnt[b], 1u);
         if (pos < B) {
             buf[(size_t)b * B + pos] = key;
@@ -172,6 +174,7 @@ struct LshSink {
             ovf_k[o] = key;
             ovf_b[o] = (uint16_t)b;
         }
+        return pos + 1 >= B;
     }
     // Sort a bucket's candidates, merge its overflow entries and keep the K smallest.
     __device__ void compact(uint32_t b, uint32_t no) {
@@ -195,11 +198,10 @@ struct LshSink {
         cnt[b] = n;
         if (n == K) tau[b] = v[K - 1];
     }
-    __device__ void after_batch(int lane) {
-        const uint32_t no = *ovf_n;
-        bool need = no > 0;
-        for (uint32_t b = lane; b < L && !need; b += 32) need = cnt[b] >= B;
+    // Called by the whole warp after at most 64 puts; need: this lane's puts asked for it.
+    __device__ void after_batch(int lane, bool need) {
         if (!__any_sync(kFull, need)) return;
+        const uint32_t no = *ovf_n;
         for (uint32_t b = lane; b < L; b += 32) {
             bool hit = cnt[b] >= B;
             for (uint32_t o = 0; o < no && !hit; ++o) hit = ovf_b[o] == b;
@@ -233,102 +235,97 @@ struct LshSink {
 };
 
 // ==========================================================================================
-// Fast path: passes with a rank limit below 1.  Every region (nu, 0) is one column of rows
+// Fast path: passes with a rank limit theta <= 1.  Every region (nu, 0) is one column of rows
 // [rlo(nu), rhi(nu)) with rlo = floor(g_prev 2^nu) (0 on the first pass) and rhi =
-// ceil(g 2^nu), so an element's areas form a 1-D sequence.  For tiles whose elements all have
-// nu_top <= 31, floor(G / 2^(64 - nu)) = hi32(G) >> (32 - nu), the element's area count is
+// ceil(g 2^nu), so an element's areas form a 1-D sequence.  For elements with nu_top <= 31,
+// floor(G / 2^(64 - nu)) = hi32(G) >> (32 - nu), and the element's area count is
 // 1 + nu_top + sum_{nu=1..nu_top} (floor(gm1 / 2^(64-nu)) - floor(gfl_prev / 2^(64-nu))) with
-// sum_{nu=1..n} floor(G / 2^(64-nu)) = 2H - popc(H), H = floor(G / 2^(64-n)), and the area
-// counter e + gamma (nu 2^58 + r + 1) = e + gamma + gamma r + ((21 nu mod 64) << 58)
-// (gamma mod 64 = 21).  Other tiles send the set to the general kernel.
+// sum_{nu=1..n} floor(G / 2^(64-nu)) = 2H - popc(H), H = floor(G / 2^(64-n)).  The area counter
+// e + gamma (nu 2^58 + r + 1) is e + kt[nu] + gamma (r - rlo[nu]) with the per-pass table
+// kt[nu] = gamma (1 + rlo[nu]) + ((21 nu mod 64) << 58) (gamma mod 64 = 21).  Tiles with an
+// element beyond nu_top = 31 send the set to the general kernel.
 //
-// In each iteration every lane hashes one area and the darts of all 32 areas are written to
-// the queue at once (positions from a ballot prefix sum of X < 16), so the warp spends one
-// iteration per area slot.  A record is 16 bytes: the dart counter c = a + gamma (j + 1) and
-// pvs = r << 24 | vmax | S << 57 (r < 2^31), rank = (r 2^24 + u) 2^-S.
+// The areas of a segment (up to kSegTiles tiles of 32 elements) are split into 32 contiguous
+// equal shares, one per lane.  The warp then runs steps: a lane with no dart left fetches its
+// next area (area hash, Poisson count), and every lane with a dart left evaluates one dart
+// (dart hash, weight and rank tests; a kept dart is hashed to its bucket).  A step thus costs
+// one area and one dart evaluation whichever lanes need them, with no queue in between.
+//
+// Rank test in integers: a dart of row r has rank (r 2^24 + u) 2^-S, S = nu + 24, and its code
+// (binary32, rounded toward zero) is below bits(theta) iff r 2^24 + u < ceil(theta 2^S) =
+// pthr[nu] (theta is a binary32 value, so rounding toward zero cannot cross it).  Per area this
+// becomes u < uthr = pthr[nu] - r 2^24 (clamped to [0, 2^25]); likewise the previous pass's
+// limit gives u >= ulo for the sinks that must not see a dart twice.
 // ==========================================================================================
+constexpr int kSegTiles = 4, kSeg = 32 * kSegTiles;
+
 struct FastMem {
-    uint64_t *fq_c, *fq_p, *te;
-    uint32_t *tv, *toff, *rlo, *rhi;
-    int *tnu;
+    uint64_t *te, *kt, *pthr, *plo;     // te[kSeg]; kt, pthr, plo [kRowTab]
+    uint32_t *tv, *toff, *rlo, *rhi;    // tv, toff [kSeg]; rlo, rhi [kRowTab]
+    signed char *tnu;                   // [kSeg]
 };
 
-constexpr size_t kFastPathBytes = 2 * kQueue * 8 + 32 * 8 + 3 * 32 * 4 + 2 * kRowTab * 4;
+constexpr size_t kFastPathBytes = (size_t)kSeg * 8 + 3 * kRowTab * 8 + 2 * (size_t)kSeg * 4 + 2 * kRowTab * 4 +
+                                  (size_t)kSeg;
 
 __device__ __forceinline__ FastMem carve_fast(unsigned char *base) {
     FastMem m;
-    m.fq_c = reinterpret_cast<uint64_t *>(base);
-    m.fq_p = m.fq_c + kQueue;
-    m.te = m.fq_p + kQueue;
-    m.tv = reinterpret_cast<uint32_t *>(m.te + 32);
-    m.toff = m.tv + 32;
-    m.tnu = reinterpret_cast<int *>(m.toff + 32);
-    m.rlo = reinterpret_cast<uint32_t *>(m.tnu + 32);
+    m.te = reinterpret_cast<uint64_t *>(base);
+    m.kt = m.te + kSeg;
+    m.pthr = m.kt + kRowTab;
+    m.plo = m.pthr + kRowTab;
+    m.tv = reinterpret_cast<uint32_t *>(m.plo + kRowTab);
+    m.toff = m.tv + kSeg;
+    m.rlo = m.toff + kSeg;
     m.rhi = m.rlo + kRowTab;
+    m.tnu = reinterpret_cast<signed char *>(m.rhi + kRowTab);
     return m;
 }
 
-// Evaluate one queued dart: weight test, rank code, rank cut; returns the kept dart's code and
-// bucket/fingerprint hash.
-template <bool LOWER>
-__device__ __forceinline__ bool fast_eval(const FastMem &m, uint32_t pos, const PassCut &pc, uint32_t &code,
-                                          uint64_t &qh) {
-    const uint32_t i = pos & (kQueue - 1);
-    const uint64_t pvs = m.fq_p[i];
-    const uint64_t d = mix64(m.fq_c[i]);
-    const uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
-    const uint64_t P = (pvs & kRMask) | u;
-    // binary32 code of rank = P 2^-S rounded toward zero: exact u64 -> f32 conversion in
-    // round-toward-zero mode, then the exponent lowered by S
-    code = P ? __float_as_uint(__ull2float_rz(P)) - ((uint32_t)(pvs >> 57) << 23) : 0u;
-    if (v > ((uint32_t)pvs & kUMask) || code >= pc.cthr) return false;
-    if (LOWER && code < pc.cthr_lo) return false;
-    qh = mix64(d ^ kSlotSalt);
-    return true;
+// ceil(value(bits) 2^S) for a positive finite binary32 below 2 and 24 <= S <= 63 (< 2^40 here).
+__device__ __forceinline__ uint64_t ceil_scaled(uint32_t bits, int S) {
+    if (bits == 0) return 0;
+    const uint32_t ex = bits >> 23, fr = bits & 0x7FFFFFu;
+    const uint64_t m = ex ? (uint64_t)(fr | 0x800000u) : (uint64_t)fr;
+    const int sh = (ex ? (int)ex - 150 : -149) + S;
+    if (sh >= 0) return m << sh;
+    if (sh <= -24) return 1;                      // 0 < m 2^sh < 1
+    return (m + (1ull << -sh) - 1) >> -sh;
 }
 
-template <class Sink, bool COUNT>
-__device__ __forceinline__ void fast_drain(int n, Queue &q, const FastMem &m, Sink &sink, int lane,
-                                           const PassCut &pc, unsigned long long &kept) {
-    uint32_t c0 = 0, c1 = 0;
-    uint64_t q0 = 0, q1 = 0;
-    const bool e0 = lane < n && fast_eval<Sink::kLowerCut>(m, q.head + lane, pc, c0, q0);
-    const bool e1 = lane + 32 < n && fast_eval<Sink::kLowerCut>(m, q.head + 32 + lane, pc, c1, q1);
-    if (e0) sink.put(q0, c0);
-    if (e1) sink.put(q1, c1);
-    if (COUNT) kept += (unsigned long long)e0 + (unsigned long long)e1;
-    q.head += (uint32_t)n;
-    __syncwarp();
-    sink.after_batch(lane);
+__device__ __forceinline__ uint32_t clamp_u(uint64_t pt, uint64_t rb) {
+    return pt <= rb ? 0u : (uint32_t)min(pt - rb, (uint64_t)(1u << 25));
 }
 
 struct WalkF {
     int el, nu, nutop;
-    uint32_t r, rhi, vtop;
-    uint64_t e, ctr, pvr;     // pvr = vmax | S << 57 of the current region
+    uint32_t r, rhi, vtop, vmax;
+    uint64_t e, ctr, pthr, plo;
 
-    __device__ void region(const FastMem &m) {
+    __device__ __forceinline__ void region(const FastMem &m) {
         r = m.rlo[nu];
         rhi = m.rhi[nu];
-        pvr = (uint64_t)(nu == nutop ? vtop : kUMask) | ((uint64_t)(nu + 24) << 57);
-        ctr = e + kGolden + kGolden * (uint64_t)r + ((uint64_t)((21u * (uint32_t)nu) & 63u) << 58);
+        ctr = e + m.kt[nu];
+        pthr = m.pthr[nu];
+        plo = m.plo[nu];
+        vmax = nu == nutop ? vtop : kUMask;
     }
-    __device__ void load(const FastMem &m) {
+    __device__ __forceinline__ void load(const FastMem &m) {
         e = m.te[el];
         vtop = m.tv[el];
         nutop = m.tnu[el];
     }
-    __device__ void locate(uint32_t idx, const FastMem &m) {
+    // position the walk on area idx of the segment (idx < its total)
+    __device__ void locate(uint32_t idx, int n_el, const FastMem &m) {
         el = 0;                                   // last element whose offset is <= idx
-#pragma unroll
-        for (int step = 16; step; step >>= 1) {
-            int c = el + step;
-            if (c < 32 && m.toff[c] <= idx) el = c;
+        for (int step = kSeg / 2; step; step >>= 1) {
+            const int c = el + step;
+            if (c < n_el && m.toff[c] <= idx) el = c;
         }
         load(m);
         uint32_t li = idx - m.toff[el];
         for (nu = 0;; ++nu) {
-            uint32_t rows = m.rhi[nu] - m.rlo[nu];
+            const uint32_t rows = m.rhi[nu] - m.rlo[nu];
             if (li < rows) break;
             li -= rows;
         }
@@ -336,18 +333,18 @@ struct WalkF {
         r += li;
         ctr += kGolden * (uint64_t)li;
     }
-    __device__ uint64_t pvs() const { return pvr | ((uint64_t)r << 24); }
-    __device__ void advance(const FastMem &m) {
+    __device__ __forceinline__ void advance(int n_el, const FastMem &m) {
         ++r;
         ctr += kGolden;
-        if (r != rhi) return;
-        if (++nu > nutop) {
-            nu = 0;
-            do { ++el; } while (el < 32 && m.tnu[el] < 0);
-            if (el >= 32) return;
-            load(m);
+        while (r == rhi) {
+            if (++nu > nutop) {
+                nu = 0;
+                do { ++el; } while (el < n_el && m.tnu[el] < 0);
+                if (el >= n_el) return;
+                load(m);
+            }
+            region(m);
         }
-        region(m);
     }
 };
 
@@ -356,83 +353,97 @@ struct WalkF {
 template <class Sink, bool COUNT>
 __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, int64_t end, const PassCut &pc,
                          const FastMem &m, Sink &sink, int lane, unsigned long long *cnt) {
-    const unsigned lt = (1u << lane) - 1u;
+    constexpr bool LOWER = Sink::kLowerCut;
+    __syncwarp();
     for (int nu = lane; nu < kRowTab; nu += 32) {
-        int n = nu > kMaxRegion ? kMaxRegion : nu;
-        m.rlo[nu] = n ? (uint32_t)min(pc.gfl_lo >> (64 - n), (uint64_t)0xFFFFFFFFu) : 0u;
+        const int n = nu > kMaxRegion ? kMaxRegion : nu;
+        const uint32_t lo = n ? (uint32_t)min(pc.gfl_lo >> (64 - n), (uint64_t)0xFFFFFFFFu) : 0u;
+        m.rlo[nu] = lo;
         m.rhi[nu] = n ? (uint32_t)min((pc.gm1 >> (64 - n)) + 1, (uint64_t)0xFFFFFFFFu) : 1u;
+        m.kt[nu] = kGolden * (1ull + lo) + ((uint64_t)((21u * (uint32_t)nu) & 63u) << 58);
+        m.pthr[nu] = ceil_scaled(pc.cthr, n + 24);
+        m.plo[nu] = ceil_scaled(pc.cthr_lo, n + 24);
     }
     const uint32_t g_hi = (uint32_t)(pc.gm1 >> 32), glo_hi = (uint32_t)(pc.gfl_lo >> 32);
-    Queue q = {0, 0};
-    for (int64_t tile = first; tile < end; tile += stride) {
-        const int64_t pos = tile + lane;
-        int nutop = -1;
-        uint64_t F = 0, e = 0;
-        if (pos < end) {
-            nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F);
-            if (nutop >= 0) e = mix64(p.sigma + kGolden * ((uint64_t)p.indices[pos] + 1));
-        }
-        if (__any_sync(kFull, nutop == -2)) return DM_ERANGE;
-        if (!__all_sync(kFull, nutop <= 31)) return kDefer;
-        uint64_t n_el = 0;
-        if (nutop >= 0) {
-            n_el = 1 + (uint64_t)nutop;
-            if (nutop > 0) {
-                uint32_t H = g_hi >> (32 - nutop), Hl = glo_hi >> (32 - nutop);
-                n_el += (2 * (uint64_t)H - __popc(H)) - (2 * (uint64_t)Hl - __popc(Hl));
-            }
-        }
-        uint64_t incl = warp_incl_scan(n_el, lane);
-        const uint64_t total = __shfl_sync(kFull, incl, 31);
-        if (total >= (1ull << 31)) return kDefer;
-        m.te[lane] = e;
-        m.tv[lane] = (uint32_t)(F >> 40);
-        m.tnu[lane] = n_el ? nutop : -1;
-        m.toff[lane] = (uint32_t)(incl - n_el);
+    for (int64_t tile = first; tile < end;) {
+        // segment tables: geometry, element hash and area offsets of up to kSegTiles tiles
         __syncwarp();
-        if (total == 0) continue;
-        const uint32_t share = (uint32_t)((total + 31) >> 5);
-        const uint32_t lo = share * (uint32_t)lane;
-        const uint32_t mine = lo < (uint32_t)total ? min(share, (uint32_t)total - lo) : 0u;
-        WalkF s;
-        if (mine) s.locate(lo, m);
-        for (uint32_t it = 0; it < share; ++it) {
-            int X = 0;
-            uint64_t a = 0, pv = 0;
-            if (it < mine) {
-                a = mix64(s.ctr);
-                X = poisson1((uint32_t)(a >> 32), c_pois);
-                pv = s.pvs();
-                if (COUNT) { cnt[0]++; cnt[1] += X; }
-                if (it + 1 < mine) s.advance(m);
+        uint64_t base = 0;
+        int nt = 0;
+        for (; nt < kSegTiles && tile < end; ++nt, tile += stride) {
+            const int64_t pos = tile + lane;
+            int nutop = -1;
+            uint64_t F = 0, e = 0;
+            if (pos < end) {
+                nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F);
+                if (nutop >= 0) e = mix64(p.sigma + kGolden * ((uint64_t)p.indices[pos] + 1));
             }
-            // prefix sum of X (< 16) over the lanes from four ballots
-            const unsigned b0 = __ballot_sync(kFull, X & 1), b1 = __ballot_sync(kFull, X & 2);
-            const unsigned b2 = __ballot_sync(kFull, X & 4), b3 = __ballot_sync(kFull, X & 8);
-            const uint32_t T = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2) + 8 * __popc(b3);
-            if (T == 0) continue;
-            const uint32_t ex = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt) + 8 * __popc(b3 & lt);
-            // write the darts in queue-sized pieces (one piece unless T is far above its mean)
-            for (uint32_t done = 0; done < T;) {
-                const uint32_t room = kQueue - (q.tail - q.head);
-                const uint32_t lim = min(T - done, room);
-                uint32_t jlo = done > ex ? done - ex : 0u;
-                uint32_t jhi = done + lim > ex ? done + lim - ex : 0u;
-                if (jhi > (uint32_t)X) jhi = (uint32_t)X;
-                uint64_t c = a + kGolden * (uint64_t)(jlo + 1);
-                for (uint32_t j = jlo; j < jhi; ++j, c += kGolden) {
-                    const uint32_t i = (q.tail + ex + j - done) & (kQueue - 1);
-                    m.fq_c[i] = c;
-                    m.fq_p[i] = pv;
+            if (__any_sync(kFull, nutop == -2)) return DM_ERANGE;
+            if (!__all_sync(kFull, nutop <= 31)) return kDefer;
+            uint64_t n_el = 0;
+            if (nutop >= 0) {
+                n_el = 1 + (uint64_t)nutop;
+                if (nutop > 0) {
+                    const uint32_t H = g_hi >> (32 - nutop), Hl = glo_hi >> (32 - nutop);
+                    n_el += (2 * (uint64_t)H - __popc(H)) - (2 * (uint64_t)Hl - __popc(Hl));
                 }
-                q.tail += lim;
-                done += lim;
-                __syncwarp();
-                while (q.tail - q.head >= 64) fast_drain<Sink, COUNT>(64, q, m, sink, lane, pc, cnt[2]);
             }
+            const uint64_t incl = warp_incl_scan(n_el, lane);
+            const int slot = nt * 32 + lane;
+            m.te[slot] = e;
+            m.tv[slot] = (uint32_t)(F >> 40);
+            m.tnu[slot] = (signed char)(n_el ? nutop : -1);
+            m.toff[slot] = (uint32_t)min(base + incl - n_el, (uint64_t)0xFFFFFFFFu);
+            base += __shfl_sync(kFull, incl, 31);
+        }
+        if (base >= (1ull << 31)) return kDefer;
+        __syncwarp();
+        if (base == 0) continue;
+        const int n_el = nt * 32;
+        const uint32_t total = (uint32_t)base;
+        const uint32_t share = (total + 31) >> 5;
+        const uint32_t lo = share * (uint32_t)lane;
+        uint32_t left = lo < total ? min(share, total - lo) : 0u;
+        WalkF s;
+        if (left) s.locate(lo, n_el, m);
+        bool fresh = true;              // the walk sits on the next area to fetch
+        uint32_t nx = 0, uthr = 0, ulo = 0;
+        uint64_t c = 0;
+        bool need = false;
+        while (__any_sync(kFull, left | nx)) {
+            if (nx == 0 && left) {
+                if (!fresh) s.advance(n_el, m);
+                fresh = false;
+                --left;
+                c = mix64(s.ctr);
+                nx = (uint32_t)poisson1((uint32_t)(c >> 32), c_pois);
+                const uint64_t rb = (uint64_t)s.r << 24;
+                uthr = clamp_u(s.pthr, rb);
+                if (LOWER) ulo = clamp_u(s.plo, rb);
+                if (COUNT) { cnt[0]++; cnt[1] += nx; }
+            }
+            if (nx) {
+                --nx;
+                c += kGolden;
+                const uint64_t d = mix64(c);
+                const uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
+                bool keep = u < uthr && v <= s.vmax;
+                if (LOWER) keep = keep && u >= ulo;
+                if (keep) {
+                    const uint64_t P = ((uint64_t)s.r << 24) | u;
+                    // binary32 code of rank = P 2^-S rounded toward zero: exact u64 -> f32
+                    // conversion in round-toward-zero mode, then the exponent lowered by S
+                    const uint32_t code =
+                        P ? __float_as_uint(__ull2float_rz(P)) - ((uint32_t)(s.nu + 24) << 23) : 0u;
+                    need = sink.put(mix64(d ^ kSlotSalt), code);
+                    if (COUNT) cnt[2]++;
+                }
+            }
+            __syncwarp();
+            sink.after_batch(lane, need);
+            need = false;
         }
     }
-    if (q.tail != q.head) fast_drain<Sink, COUNT>((int)(q.tail - q.head), q, m, sink, lane, pc, cnt[2]);
     return 0;
 }
 
@@ -487,12 +498,13 @@ __device__ __forceinline__ void gen_drain(int n, Queue &q, const GenMem &m, Sink
     uint64_t q0 = 0, q1 = 0;
     const bool e0 = lane < n && gen_eval<Sink::kLowerCut>(m, q.head + lane, pc, c0, q0);
     const bool e1 = lane + 32 < n && gen_eval<Sink::kLowerCut>(m, q.head + 32 + lane, pc, c1, q1);
-    if (e0) sink.put(q0, c0);
-    if (e1) sink.put(q1, c1);
+    bool need = false;
+    if (e0) need = sink.put(q0, c0);
+    if (e1) need |= sink.put(q1, c1);
     if (COUNT) kept += (unsigned long long)e0 + (unsigned long long)e1;
     q.head += (uint32_t)n;
     __syncwarp();
-    sink.after_batch(lane);
+    sink.after_batch(lane, need);
 }
 
 __device__ __forceinline__ int tile_element(const GenMem &m, uint64_t idx) {
