@@ -36,7 +36,6 @@ constexpr int kMaxPasses = 21;     // phi0 * 2^20 at most (Theorem 1's loop limi
 constexpr int kDefer = -1;         // a pass the fast kernel leaves to the general kernel
 constexpr int kRowTab = 40;        // fast path: rows of nu = 0..38 (+1 pad)
 constexpr int kOverflow = 64;      // LSH: appends past a full bucket within one batch
-constexpr uint64_t kRMask = ((1ull << 55) - 1) & ~(uint64_t)kUMask;
 // batched form: hist[0..96) bin counts, [96..192) bin cursors, [192..195) class totals
 constexpr int kClasses = 3, kBins = 32, kCursors = kClasses * kBins, kTotals = 2 * kClasses * kBins;
 constexpr size_t kHeaderBytes = 1024;   // queue count, 3 work counters, histogram, totals
@@ -74,6 +73,7 @@ struct SketchSink {
     uint64_t *slots;
     uint32_t k;
     static constexpr bool kLowerCut = false;      // min is idempotent: band overlap is harmless
+    static constexpr bool kRing = false;          // kept darts go straight to their bucket
 
     __device__ void bind(unsigned char *base, const SketchParams &p) {
         slots = reinterpret_cast<uint64_t *>(base);
@@ -141,6 +141,7 @@ struct LshSink {
     uint16_t *ovf_b;
     uint32_t L, K, B;
     static constexpr bool kLowerCut = true;
+    static constexpr bool kRing = true;           // kept darts are buffered and put 32 at a time
 
     __device__ void bind(unsigned char *base, const SketchParams &p) {
         L = (uint32_t)p.k;
@@ -259,14 +260,20 @@ struct LshSink {
 // ==========================================================================================
 constexpr int kSegTiles = 4, kSeg = 32 * kSegTiles;
 
+constexpr int kKept = 64;            // kept-dart ring (LSH): drained 32 at a time
+
 struct FastMem {
     uint64_t *te, *kt, *pthr, *plo;     // te[kSeg]; kt, pthr, plo [kRowTab]
     uint32_t *tv, *toff, *rlo, *rhi;    // tv, toff [kSeg]; rlo, rhi [kRowTab]
     signed char *tnu;                   // [kSeg]
+    uint64_t *kd;                       // ring: kept darts' hashes [kKept] (sinks with kRing)
+    uint32_t *kc;                       // ring: their rank codes [kKept]
 };
 
 constexpr size_t kFastPathBytes = (size_t)kSeg * 8 + 3 * kRowTab * 8 + 2 * (size_t)kSeg * 4 + 2 * kRowTab * 4 +
                                   (size_t)kSeg;
+constexpr size_t kFastRingBytes = (size_t)kKept * 12;
+static_assert(kFastPathBytes % 16 == 0, "the ring after the fast-path tables must stay aligned");
 
 __device__ __forceinline__ FastMem carve_fast(unsigned char *base) {
     FastMem m;
@@ -279,6 +286,8 @@ __device__ __forceinline__ FastMem carve_fast(unsigned char *base) {
     m.rlo = m.toff + kSeg;
     m.rhi = m.rlo + kRowTab;
     m.tnu = reinterpret_cast<signed char *>(m.rhi + kRowTab);
+    m.kd = reinterpret_cast<uint64_t *>(base + kFastPathBytes);
+    m.kc = reinterpret_cast<uint32_t *>(m.kd + kKept);
     return m;
 }
 
@@ -348,6 +357,18 @@ struct WalkF {
     }
 };
 
+// Hash n <= 32 kept darts of the ring from position h to their buckets (the whole warp).
+template <class Sink>
+__device__ __forceinline__ void fast_put(const FastMem &m, Sink &sink, uint32_t h, uint32_t n, int lane) {
+    bool need = false;
+    if ((uint32_t)lane < n) {
+        const uint32_t i = (h + (uint32_t)lane) & (kKept - 1);
+        need = sink.put(mix64(m.kd[i] ^ kSlotSalt), m.kc[i]);
+    }
+    __syncwarp();
+    sink.after_batch(lane, need);
+}
+
 // One rank-region-0 pass over tiles first, first + stride, ... of the row [.., end).  Returns 0,
 // an error code, or kDefer.
 template <class Sink, bool COUNT>
@@ -365,6 +386,8 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         m.plo[nu] = ceil_scaled(pc.cthr_lo, n + 24);
     }
     const uint32_t g_hi = (uint32_t)(pc.gm1 >> 32), glo_hi = (uint32_t)(pc.gfl_lo >> 32);
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t kq = 0, kh = 0;            // kept-dart ring: tail and head
     for (int64_t tile = first; tile < end;) {
         // segment tables: geometry, element hash and area offsets of up to kSegTiles tiles
         __syncwarp();
@@ -409,7 +432,6 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         bool fresh = true;              // the walk sits on the next area to fetch
         uint32_t nx = 0, uthr = 0, ulo = 0;
         uint64_t c = 0;
-        bool need = false;
         while (__any_sync(kFull, left | nx)) {
             if (nx == 0 && left) {
                 if (!fresh) s.advance(n_el, m);
@@ -422,27 +444,53 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
                 if (LOWER) ulo = clamp_u(s.plo, rb);
                 if (COUNT) { cnt[0]++; cnt[1] += nx; }
             }
+            bool keep = false;
+            uint64_t d = 0;
+            uint32_t u = 0;
             if (nx) {
                 --nx;
                 c += kGolden;
-                const uint64_t d = mix64(c);
-                const uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
-                bool keep = u < uthr && v <= s.vmax;
+                d = mix64(c);
+                u = (uint32_t)(d >> 40);
+                const uint32_t v = (uint32_t)(d >> 16) & kUMask;
+                keep = u < uthr && v <= s.vmax;
                 if (LOWER) keep = keep && u >= ulo;
+            }
+            if (!Sink::kRing) {
+                // bucket minimum at once (a shared-memory atomic is cheap)
+                if (keep) {
+                    const uint64_t P = ((uint64_t)s.r << 24) | u;
+                    const uint32_t code =
+                        P ? __float_as_uint(__ull2float_rz(P)) - ((uint32_t)(s.nu + 24) << 23) : 0u;
+                    sink.put(mix64(d ^ kSlotSalt), code);
+                    if (COUNT) cnt[2]++;
+                }
+                continue;
+            }
+            // kept darts go to the ring; 32 of them at a time are hashed to their buckets
+            const unsigned km = __ballot_sync(kFull, keep);
+            if (km) {
                 if (keep) {
                     const uint64_t P = ((uint64_t)s.r << 24) | u;
                     // binary32 code of rank = P 2^-S rounded toward zero: exact u64 -> f32
                     // conversion in round-toward-zero mode, then the exponent lowered by S
-                    const uint32_t code =
-                        P ? __float_as_uint(__ull2float_rz(P)) - ((uint32_t)(s.nu + 24) << 23) : 0u;
-                    need = sink.put(mix64(d ^ kSlotSalt), code);
+                    const uint32_t i = (kq + __popc(km & lt)) & (kKept - 1);
+                    m.kd[i] = d;
+                    m.kc[i] = P ? __float_as_uint(__ull2float_rz(P)) - ((uint32_t)(s.nu + 24) << 23) : 0u;
                     if (COUNT) cnt[2]++;
                 }
+                kq += __popc(km);
+                if (kq - kh >= 32) {
+                    __syncwarp();
+                    fast_put<Sink>(m, sink, kh, 32, lane);
+                    kh += 32;
+                }
             }
-            __syncwarp();
-            sink.after_batch(lane, need);
-            need = false;
         }
+    }
+    if (kq != kh) {
+        __syncwarp();
+        fast_put<Sink>(m, sink, kh, kq - kh, lane);
     }
     return 0;
 }
@@ -1032,7 +1080,7 @@ cudaError_t launch_batched(const SketchParams &p0, bool lsh, bool bbit, bool cou
 
 size_t warp_bytes(bool lsh, int k, int K, int mode) {
     const size_t sink = lsh ? lsh_sink_bytes(k, K) : sketch_sink_bytes(k);
-    return sink + (mode == 0 ? kFastPathBytes : kGenPathBytes);
+    return sink + (mode == 0 ? kFastPathBytes + (lsh ? kFastRingBytes : 0) : kGenPathBytes);
 }
 
 size_t sink_bytes(bool lsh, int k, int K) { return lsh ? lsh_sink_bytes(k, K) : sketch_sink_bytes(k); }
