@@ -31,7 +31,6 @@ namespace dm {
 __constant__ uint32_t c_pois[12];
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kQueue = 128;        // dart records per warp
 constexpr int kMaxPasses = 21;     // phi0 * 2^20 at most (Theorem 1's loop limit)
 constexpr int kDefer = -1;         // a pass the fast kernel leaves to the general kernel
 constexpr int kRowTab = 40;        // fast path: rows of nu = 0..38 (+1 pad)
@@ -48,10 +47,6 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
     }
     return v;
 }
-
-struct Queue {
-    uint32_t tail, head;
-};
 
 // ==========================================================================================
 // Sinks
@@ -497,62 +492,25 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
 
 // ==========================================================================================
 // General path: every region (nu, rho), columns w and rows r, in 64-bit arithmetic, with the
-// same one-iteration-per-area batched emission as the fast path.  A record holds the dart
-// counter, pv = pb | vmax (the rank base pb is a multiple of 2^24) and meta = sh | S << 6:
-// rank = (pb + (u << sh)) 2^-S.
+// same step loop as the fast path (a lane with no dart left fetches its next area; every lane
+// with a dart left evaluates one).  A dart of the current area has rank (pb + (u << sh)) 2^-S
+// with the area's rank base pb (a multiple of 2^24), sh = 38 - nu and S = 62 - rho, and hits x
+// iff v <= vmax.
 // ==========================================================================================
 struct GenMem {
-    uint64_t *dq_c, *dq_p, *te, *tF, *toff;
+    uint64_t *te, *tF, *toff;
     int *tnu;
-    uint16_t *dq_m;
 };
 
-constexpr size_t kGenPathBytes = 2 * kQueue * 8 + 3 * 32 * 8 + 32 * 4 + kQueue * 2;
+constexpr size_t kGenPathBytes = 3 * 32 * 8 + 32 * 4;
 
 __device__ __forceinline__ GenMem carve_gen(unsigned char *base) {
     GenMem m;
-    m.dq_c = reinterpret_cast<uint64_t *>(base);
-    m.dq_p = m.dq_c + kQueue;
-    m.te = m.dq_p + kQueue;
+    m.te = reinterpret_cast<uint64_t *>(base);
     m.tF = m.te + 32;
     m.toff = m.tF + 32;
     m.tnu = reinterpret_cast<int *>(m.toff + 32);
-    m.dq_m = reinterpret_cast<uint16_t *>(m.tnu + 32);
     return m;
-}
-
-__device__ __forceinline__ uint32_t pack_meta(int sh, int S) { return (uint32_t)sh | ((uint32_t)S << 6); }
-
-template <bool LOWER>
-__device__ __forceinline__ bool gen_eval(const GenMem &m, uint32_t pos, const PassCut &pc, uint32_t &code,
-                                         uint64_t &qh) {
-    const uint32_t i = pos & (kQueue - 1);
-    const uint64_t pv = m.dq_p[i];
-    const uint32_t meta = m.dq_m[i];
-    const uint64_t d = mix64(m.dq_c[i]);
-    const uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
-    const uint64_t P = (pv & ~(uint64_t)kUMask) + ((uint64_t)u << (meta & 63));
-    code = P ? __float_as_uint(__ull2float_rz(P)) - ((meta >> 6) << 23) : 0u;
-    if (v > ((uint32_t)pv & kUMask) || code >= pc.cthr) return false;
-    if (LOWER && code < pc.cthr_lo) return false;
-    qh = mix64(d ^ kSlotSalt);
-    return true;
-}
-
-template <class Sink, bool COUNT>
-__device__ __forceinline__ void gen_drain(int n, Queue &q, const GenMem &m, Sink &sink, int lane,
-                                          const PassCut &pc, unsigned long long &kept) {
-    uint32_t c0 = 0, c1 = 0;
-    uint64_t q0 = 0, q1 = 0;
-    const bool e0 = lane < n && gen_eval<Sink::kLowerCut>(m, q.head + lane, pc, c0, q0);
-    const bool e1 = lane + 32 < n && gen_eval<Sink::kLowerCut>(m, q.head + 32 + lane, pc, c1, q1);
-    bool need = false;
-    if (e0) need = sink.put(q0, c0);
-    if (e1) need |= sink.put(q1, c1);
-    if (COUNT) kept += (unsigned long long)e0 + (unsigned long long)e1;
-    q.head += (uint32_t)n;
-    __syncwarp();
-    sink.after_batch(lane, need);
 }
 
 __device__ __forceinline__ int tile_element(const GenMem &m, uint64_t idx) {
@@ -565,17 +523,42 @@ __device__ __forceinline__ int tile_element(const GenMem &m, uint64_t idx) {
     return el;
 }
 
+// sum_{nu=1..m} floor(G / 2^(64 - nu)) = 2H - popc(H) with H = floor(G / 2^(64 - m)); 0 for m = 0.
+__device__ __forceinline__ uint64_t floor_sum(uint64_t G, int m) {
+    if (m <= 0) return 0;
+    const uint64_t H = G >> (64 - m);
+    return 2 * H - (uint64_t)__popcll(H);
+}
+
+// Rows of rank region rho summed over weight regions nu = 0 .. n-1 (every one of them below the
+// element's last region, so all its columns count): sum of rows_hi - rows_lo in closed form.
+__device__ __forceinline__ uint64_t rows_upto(const PassCut &pc, int rho, int n) {
+    if (n <= 0) return 0;
+    uint64_t hi = rho == pc.rho_top ? (uint64_t)n + floor_sum(pc.gm1, n - 1) : (1ull << n) - 1;
+    uint64_t lo = rho == pc.rho_lo ? floor_sum(pc.gfl_lo, n - 1) : 0;
+    return hi - lo;
+}
+
 struct WalkG {
     int el, nu, rho, nutop;
     uint64_t w, r, ncols, rlo, rhi;
     uint64_t e, F, WT, rbase, packhi, ctr;
 
-    __device__ static uint64_t count(int nutop, uint64_t F, const PassCut &pc) {
+    // areas of weight regions nu < n (n <= nutop): 2^rho columns each
+    __device__ static uint64_t count_below(int n, const PassCut &pc) {
         uint64_t total = 0;
-        for (int n = 0; n <= nutop; ++n)
-            for (int h = pc.rho_lo; h <= pc.rho_top; ++h)
-                total += cols(n, h, nutop, F) * (rows_hi(pc, n, h) - rows_lo(pc, n, h));
+        for (int h = pc.rho_lo; h <= pc.rho_top; ++h) total += rows_upto(pc, h, n) << h;
         return total;
+    }
+    // areas of the last weight region nu = nutop
+    __device__ static uint64_t count_top(int nutop, uint64_t F, const PassCut &pc) {
+        uint64_t total = 0;
+        for (int h = pc.rho_lo; h <= pc.rho_top; ++h)
+            total += cols(nutop, h, nutop, F) * (rows_hi(pc, nutop, h) - rows_lo(pc, nutop, h));
+        return total;
+    }
+    __device__ static uint64_t count(int nutop, uint64_t F, const PassCut &pc) {
+        return count_below(nutop, pc) + count_top(nutop, F, pc);
     }
     __device__ void region(const PassCut &pc) {
         ncols = cols(nu, rho, nutop, F);
@@ -595,27 +578,31 @@ struct WalkG {
         el = tile_element(m, idx);
         load(m);
         uint64_t li = idx - m.toff[el];
-        for (nu = 0; nu <= nutop; ++nu) {
-            bool found = false;
-            for (rho = pc.rho_lo; rho <= pc.rho_top; ++rho) {
-                region(pc);
-                uint64_t nrows = rhi - rlo, c = ncols * nrows;
-                if (li < c) {
-                    w = li / nrows;
-                    r = rlo + (li - w * nrows);
-                    found = true;
-                    break;
-                }
-                li -= c;
+        // weight region: the largest n <= nutop with count_below(n) <= li (binary search;
+        // count_below is non-decreasing in n)
+        int lo = 0, hi = nutop;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (count_below(mid, pc) <= li) lo = mid;
+            else hi = mid - 1;
+        }
+        nu = lo;
+        li -= count_below(nu, pc);
+        for (rho = pc.rho_lo; rho <= pc.rho_top; ++rho) {
+            region(pc);
+            const uint64_t nrows = rhi - rlo, c = ncols * nrows;
+            if (li < c) {
+                w = li / nrows;
+                r = rlo + (li - w * nrows);
+                break;
             }
-            if (found) break;
+            li -= c;
         }
         set_ctr();
     }
     __device__ uint64_t pv() const {
         return rbase + (r << (62 - nu)) + min(WT - (w << 24), (uint64_t)kUMask);
     }
-    __device__ uint32_t meta() const { return pack_meta(38 - nu, 62 - rho); }
     __device__ void advance(const GenMem &m, const PassCut &pc) {
         ++r;
         ctr += kGolden;
@@ -644,8 +631,7 @@ struct WalkG {
 template <class Sink, bool COUNT>
 __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, int64_t end, const PassCut &pc,
                         const GenMem &m, Sink &sink, int lane, unsigned long long *cnt) {
-    const unsigned lt = (1u << lane) - 1u;
-    Queue q = {0, 0};
+    constexpr bool LOWER = Sink::kLowerCut;
     for (int64_t tile = first; tile < end; tile += stride) {
         const int64_t pos = tile + lane;
         int nutop = -1;
@@ -657,6 +643,7 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
         if (__any_sync(kFull, nutop == -2)) return DM_ERANGE;
         const uint64_t n_el = nutop >= 0 ? WalkG::count(nutop, F, pc) : 0;
         const uint64_t incl = warp_incl_scan(n_el, lane);
+        __syncwarp();
         m.te[lane] = e;
         m.tF[lane] = F;
         m.tnu[lane] = n_el ? nutop : -1;
@@ -666,49 +653,47 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
         if (total == 0) continue;
         const uint64_t share = (total + 31) >> 5;
         const uint64_t lo = share * lane;
-        const uint64_t mine = lo < total ? min(share, total - lo) : 0;   // areas of this lane
+        uint64_t left = lo < total ? min(share, total - lo) : 0;   // areas of this lane
         WalkG s;
-        if (mine) s.locate(lo, m, pc);
-        // one iteration per area slot: every lane hashes one area, then the darts of all 32
-        // areas are written at once (positions from a ballot prefix sum of X < 16)
-        for (uint64_t it = 0; it < share; ++it) {
-            int X = 0;
-            uint64_t a = 0, pv = 0;
-            uint32_t meta = 0;
-            if (it < mine) {
-                a = mix64(s.ctr);
-                X = poisson1((uint32_t)(a >> 32), c_pois);
-                pv = s.pv();
-                meta = s.meta();
-                if (COUNT) { cnt[0]++; cnt[1] += X; }
-                if (it + 1 < mine) s.advance(m, pc);
+        if (left) s.locate(lo, m, pc);
+        bool fresh = true;              // the walk sits on the next area to fetch
+        uint32_t nx = 0, vmax = 0, sh = 0, S = 0;
+        uint64_t c = 0, pb = 0;
+        while (__any_sync(kFull, left != 0 || nx != 0)) {
+            bool need = false;
+            if (nx == 0 && left) {
+                if (!fresh) s.advance(m, pc);
+                fresh = false;
+                --left;
+                c = mix64(s.ctr);
+                nx = (uint32_t)poisson1((uint32_t)(c >> 32), c_pois);
+                const uint64_t pv = s.pv();
+                pb = pv & ~(uint64_t)kUMask;
+                vmax = (uint32_t)pv & kUMask;
+                sh = 38 - (uint32_t)s.nu;
+                S = 62 - (uint32_t)s.rho;
+                if (COUNT) { cnt[0]++; cnt[1] += nx; }
             }
-            const unsigned b0 = __ballot_sync(kFull, X & 1), b1 = __ballot_sync(kFull, X & 2);
-            const unsigned b2 = __ballot_sync(kFull, X & 4), b3 = __ballot_sync(kFull, X & 8);
-            const uint32_t T = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2) + 8 * __popc(b3);
-            if (T == 0) continue;
-            const uint32_t ex = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt) + 8 * __popc(b3 & lt);
-            for (uint32_t done = 0; done < T;) {
-                const uint32_t room = kQueue - (q.tail - q.head);
-                const uint32_t lim = min(T - done, room);
-                uint32_t jlo = done > ex ? done - ex : 0u;
-                uint32_t jhi = done + lim > ex ? done + lim - ex : 0u;
-                if (jhi > (uint32_t)X) jhi = (uint32_t)X;
-                uint64_t c = a + kGolden * (uint64_t)(jlo + 1);
-                for (uint32_t j = jlo; j < jhi; ++j, c += kGolden) {
-                    const uint32_t i = (q.tail + ex + j - done) & (kQueue - 1);
-                    m.dq_c[i] = c;
-                    m.dq_p[i] = pv;
-                    m.dq_m[i] = (uint16_t)meta;
+            if (nx) {
+                --nx;
+                c += kGolden;
+                const uint64_t d = mix64(c);
+                const uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
+                const uint64_t P = pb + ((uint64_t)u << sh);
+                // binary32 code of rank = P 2^-S rounded toward zero (exact u64 -> f32
+                // conversion in round-toward-zero mode, then the exponent lowered by S)
+                const uint32_t code = P ? __float_as_uint(__ull2float_rz(P)) - (S << 23) : 0u;
+                bool keep = v <= vmax && code < pc.cthr;
+                if (LOWER) keep = keep && code >= pc.cthr_lo;
+                if (keep) {
+                    need = sink.put(mix64(d ^ kSlotSalt), code);
+                    if (COUNT) cnt[2]++;
                 }
-                q.tail += lim;
-                done += lim;
-                __syncwarp();
-                while (q.tail - q.head >= 64) gen_drain<Sink, COUNT>(64, q, m, sink, lane, pc, cnt[2]);
             }
+            __syncwarp();
+            sink.after_batch(lane, need);
         }
     }
-    if (q.tail != q.head) gen_drain<Sink, COUNT>((int)(q.tail - q.head), q, m, sink, lane, pc, cnt[2]);
     return 0;
 }
 
@@ -718,7 +703,7 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
 // with the general walk.  Warps are persistent and claim work items from a global counter.
 // ==========================================================================================
 template <class Sink, bool BBIT, bool COUNT, int MODE>
-__global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) set_kernel(const SketchParams p) {
+__global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) set_kernel(const SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
