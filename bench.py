@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--form", choices=["batched", "plain", "persistent"], default="batched",
                     help="launch form (the plain form is the one-warp-per-set reference)")
     ap.add_argument("--large-nnz", type=int, default=None, help="batched form: element count of a large set")
+    ap.add_argument("--autotune", choices=["auto", "on", "off"], default="auto",
+                    help="dm_autotune on a prefix before timing (auto: W2 only)")
+    ap.add_argument("--no-graph", action="store_true", help="plain launches instead of CUDA-graph replay")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain per-set form measured beside")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -272,14 +276,36 @@ def gpu_arm(args):
         else:
             dmx.dm_lsh(c, ip, ix, w, 64, 8, SEED, out=keys, stream=stream)
 
+    # launch settings: the autotuner on a prefix of the batch (results never depend on them)
+    tuning = None
+    if args.autotune == "on" or (args.autotune == "auto" and wl == "W2"):
+        if args.form != "batched":
+            raise SystemExit("--autotune needs the batched form")
+        if wl == "W1":
+            tuning = dmx.dm_autotune(ctx, ip, ix, w, K_SLOTS, SEED, b=B_BITS, stream=stream)
+        elif wl == "W2":
+            tuning = dmx.dm_autotune(ctx, ip, ix, w, 1024, SEED, max_sets=50_000, stream=stream)
+        else:
+            tuning = dmx.dm_autotune(ctx, ip, ix, w, 64, SEED, lsh_K=8, stream=stream)
+    if not args.no_graph:
+        dmx.dm_set_option(ctx, dmx.OPT_GRAPH, 1)
+
     def step():
         launch(ctx)
 
-    # work units of one launch (untimed counting launch; counters never change output bits)
+    # work units of one launch (untimed counting launch with the same settings; counters never
+    # change output bits)
     cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
     cctx = dmx.dm_create(local)
     dmx.dm_set_option(cctx, dmx.OPT_COUNTERS, cnt.data_ptr())
     dmx.dm_set_option(cctx, dmx.OPT_FORM, form_id)
+    if args.large_nnz is not None:
+        dmx.dm_set_option(cctx, dmx.OPT_LARGE_NNZ, args.large_nnz)
+    if tuning:
+        dmx.dm_set_option(cctx, dmx.OPT_FORM, tuning["form"])
+        dmx.dm_set_option(cctx, dmx.OPT_WARPS_PER_BLOCK, tuning["warps_per_block"])
+        dmx.dm_set_option(cctx, dmx.OPT_LARGE_NNZ, tuning["large_nnz"])
+        dmx.dm_set_option(cctx, dmx.OPT_LSH_PHI0 if wl == "W3" else dmx.OPT_PHI0, tuning["phi0_1024"])
     launch(cctx)
     dmx.dm_sync_status(cctx)
     areas, darts, kept, passes = [int(v) for v in cnt.cpu().tolist()]
@@ -308,6 +334,26 @@ def gpu_arm(args):
     t_max = max_over_ranks(dist, total_ms / 1e3, True)
     all_sets = sum_over_ranks(dist, float(n * args.steps), True)
     value = all_sets / t_max
+
+    # the plain per-set form (one warp per set in input order, static grid) on the same batch
+    plain = None
+    if not args.no_plain and args.form == "batched":
+        pctx = dmx.dm_create(local)
+        dmx.dm_set_option(pctx, dmx.OPT_FORM, dmx.FORM_PLAIN)
+        launch(pctx)
+        pe = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        barrier(dist, True)
+        pe[0].record(stream)
+        for _ in range(3):
+            launch(pctx)
+        pe[1].record(stream)
+        barrier(dist, True)
+        dmx.dm_sync_status(pctx)
+        pctx.close()
+        p_ms = pe[0].elapsed_time(pe[1]) / 3
+        p_max = max_over_ranks(dist, p_ms / 1e3, True)
+        plain = {"ms_per_step": p_max * 1e3, "value": all_sets / args.steps / p_max, "unit": "sets/s",
+                 "batched_over_plain": value / (all_sets / args.steps / p_max)}
 
     # end to end through the host-buffer C-ABI entry (copies inside the timed region)
     e2e = None
@@ -372,10 +418,13 @@ def gpu_arm(args):
             "minhashes_per_s": value * kk,
             "config": {"workload": desc if args.sets is None else f"{wl} prefix of {n} sets",
                        "n_sets": n, "k": kk, "b": B_BITS if wl == "W1" else None, "seed": SEED,
-                       "form": args.form,
+                       "form": args.form + ("" if args.no_graph else " + CUDA graph")
+                               + (" + autotuned" if tuning else ""),
                        "l2": "inputs 2 GB and outputs 2 GB per step, > 129 MB L2: no flush needed"},
             "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": (2 if args.form != "batched" else (5 if wl == "W3" else 6)) * args.steps,
+            "plain_form": plain, "tuning": tuning,
+            "gpu_launches": (2 if (tuning["form"] if tuning else form_id) != dmx.FORM_BATCHED
+                             else (5 if wl == "W3" else 6)) * args.steps,
             "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)
