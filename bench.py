@@ -55,8 +55,8 @@ def parse():
     ap.add_argument("--form", choices=["batched", "plain", "persistent"], default="batched",
                     help="launch form (the plain form is the one-warp-per-set reference)")
     ap.add_argument("--large-nnz", type=int, default=None, help="batched form: element count of a large set")
-    ap.add_argument("--autotune", choices=["auto", "on", "off"], default="auto",
-                    help="dm_autotune on a prefix before timing (auto: W2 only)")
+    ap.add_argument("--autotune", choices=["on", "off"], default="on",
+                    help="dm_autotune on a prefix of the batch before the warm-up (launch settings only)")
     ap.add_argument("--no-graph", action="store_true", help="plain launches instead of CUDA-graph replay")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-set form measured beside")
     ap.add_argument("--no-e2e", action="store_true")
@@ -278,9 +278,7 @@ def gpu_arm(args):
 
     # launch settings: the autotuner on a prefix of the batch (results never depend on them)
     tuning = None
-    if args.autotune == "on" or (args.autotune == "auto" and wl == "W2"):
-        if args.form != "batched":
-            raise SystemExit("--autotune needs the batched form")
+    if args.autotune == "on" and args.form == "batched":
         if wl == "W1":
             tuning = dmx.dm_autotune(ctx, ip, ix, w, K_SLOTS, SEED, b=B_BITS, stream=stream)
         elif wl == "W2":

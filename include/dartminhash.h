@@ -132,7 +132,7 @@ const char *dm_strerror(int status);
 
 /* Tuning and instrumentation options (dm_set_option).  None of them changes any output bit. */
 enum dm_option {
-    DM_OPT_PHI0 = 1,        /* initial phi of Theorem 1's loop, as value/1024 (default 1024 = 1.0) */
+    DM_OPT_PHI0 = 1,        /* initial phi of Theorem 1's loop, as value/1024 (default 1280 = 1.25) */
     DM_OPT_COUNTERS = 2,    /* device pointer to uint64[4] accumulating areas inspected, darts
                                generated, darts kept and passes (0 = off) */
     DM_OPT_FORM = 3,        /* launch form: 0 = batched (default: sets classified by first rank
@@ -142,7 +142,7 @@ enum dm_option {
                                1 = plain (one warp per set in input order, static grid);
                                2 = persistent warps over the sets in input order */
     DM_OPT_WARPS_PER_BLOCK = 4, /* 1..8 warps (sets) per thread block, 0 = automatic */
-    DM_OPT_LSH_PHI0 = 5,        /* initial phi of dm_lsh's loop, as value/1024 (default 4096 = 4.0) */
+    DM_OPT_LSH_PHI0 = 5,        /* initial phi of dm_lsh's loop, as value/1024 (default 3072 = 3.0) */
     DM_OPT_LARGE_NNZ = 6,       /* batched form: element count from which a set gets a whole block
                                    (default 2048; 0 = never; dm_lsh never does) */
     DM_OPT_GRAPH = 7,           /* 1: launch each call's kernel sequence as a CUDA graph, cached per

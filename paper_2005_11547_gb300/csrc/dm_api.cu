@@ -57,8 +57,9 @@ struct dm_ctx {
     int sm_count = 0;
     int *d_status = nullptr;
     int *h_status = nullptr;       // pinned
-    float phi0 = 1.0f;             // initial phi of the sketch loop (Theorem 1)
-    float phi0_lsh = 4.0f;         // initial phi of the LSH loop (every bucket needs K darts)
+    float phi0 = 1.25f;            // initial phi of the sketch loop (Theorem 1); 1.25 spares most
+                                   // retries at 25% more first-pass darts (measured faster on W1/W2)
+    float phi0_lsh = 3.0f;         // initial phi of the LSH loop (every bucket needs K darts)
     unsigned long long *counters = nullptr;
     int form = 0;                  // 0 batched, 1 plain, 2 persistent in input order
     int warps_per_block = 0;       // 0 = automatic

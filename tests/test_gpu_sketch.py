@@ -228,6 +228,7 @@ def test_counters_and_streams(dmx, torch_mod, ctx, oracle_mod):
     cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
     c2 = dmx.dm_create(0)
     dmx.dm_set_option(c2, dmx.OPT_COUNTERS, cnt.data_ptr())
+    dmx.dm_set_option(c2, dmx.OPT_PHI0, 1024)             # phi0 = 1, as the oracle below
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         ip, ix, w = to_dev(torch, b)
