@@ -143,8 +143,10 @@ enum dm_option {
                                2 = persistent warps over the sets in input order */
     DM_OPT_WARPS_PER_BLOCK = 4, /* 1..8 warps (sets) per thread block, 0 = automatic */
     DM_OPT_LSH_PHI0 = 5,        /* initial phi of dm_lsh's loop, as value/1024 (default 3072 = 3.0) */
-    DM_OPT_LARGE_NNZ = 6,       /* batched form: element count from which a set gets a whole block
-                                   (default 2048; 0 = never; dm_lsh never does) */
+    DM_OPT_LARGE_NNZ = 6,       /* batched form: element count from which a set gets a whole block of
+                                   8 warps (default 2048; 0 = never; dm_lsh never does).  A set of
+                                   fewer than 512 elements on a block has each tile's areas split
+                                   among the 8 warps; a larger one has its tiles dealt to them */
     DM_OPT_GRAPH = 7,           /* 1: launch each call's kernel sequence as a CUDA graph, cached per
                                    context; a call identical to a cached one (same pointers, sizes,
                                    seed and settings) replays it with one launch, a new call of the

@@ -376,10 +376,12 @@ int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const 
 namespace dm {
 
 int serve_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
-                 int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *queue, int form, cudaStream_t st) {
+                 int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *queue, int form, int large_nnz,
+                 cudaStream_t st) {
     if (!ctx) return DM_EINVAL;
     Choice c = choose(ctx, false, k, 0, 0);
     c.form = form;
+    if (large_nnz >= 0) c.large_nnz = large_nnz;
     return run_sets(ctx, indptr, indices, weights, n_sets, false, k, 0, 0, seed, nullptr, out, nullptr, st, queue,
                     &c);
 }
@@ -648,8 +650,8 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
                                                : std::vector<float>{1.f, 1.25f, 1.5f, 2.f};
         try_set([](Choice &c, float v) { c.phi0 = v; }, phis);
         try_set([](Choice &c, int v) { c.wpb = v; }, std::vector<int>{2, 4, 8});
-        if (!is_lsh && max_nnz >= 1024)
-            try_set([](Choice &c, int v) { c.large_nnz = v; }, std::vector<int>{0, 1024, 2048, 4096, 8192});
+        if (!is_lsh && max_nnz >= 256)
+            try_set([](Choice &c, int v) { c.large_nnz = v; }, std::vector<int>{0, 256, 512, 1024, 2048, 4096, 8192});
         try_set([](Choice &c, int v) { c.form = v; }, std::vector<int>{0, 2});
     }
     ctx->use_graph = use_graph;

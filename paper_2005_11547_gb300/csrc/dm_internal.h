@@ -73,11 +73,13 @@ size_t call_scratch_bytes(int64_t n_sets);
 void carve_call_scratch(void *base, int64_t n_sets, SketchParams &p);
 
 // Serving loop helpers (dm_api.cu).  serve_sketch: one dm_sketch call with the call's scratch at
-// `queue` (call_scratch_bytes(n_sets) bytes) and the given launch form.  status_to_host queues a
+// `queue` (call_scratch_bytes(n_sets) bytes), the given launch form and large-set threshold
+// (-1: the context's).  status_to_host queues a
 // copy of the context's status word to its pinned host copy; status_take, once the stream has
 // been synchronized, returns that word and clears it on the device when it was set.
 int serve_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
-                 int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *queue, int form, cudaStream_t st);
+                 int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *queue, int form, int large_nnz,
+                 cudaStream_t st);
 cudaError_t status_to_host(dm_ctx *ctx, cudaStream_t st);
 int status_take(dm_ctx *ctx, cudaStream_t st);
 int context_large_nnz(const dm_ctx *ctx);

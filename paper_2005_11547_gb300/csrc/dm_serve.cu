@@ -24,9 +24,13 @@ using dm::serve::Request;
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+constexpr int kGroupStreams = 4;  // groups of one batch run concurrently on these
+
 struct Lane {
     dm_ctx *ctx = nullptr;
     cudaStream_t st = nullptr;
+    cudaStream_t gst[kGroupStreams] = {};
+    cudaEvent_t ev_in = nullptr, ev_done[kGroupStreams] = {};
     unsigned char *d = nullptr;    // device buffer
     unsigned char *h = nullptr;    // page-locked host buffer, same size
 };
@@ -41,6 +45,7 @@ class CudaExecutor : public dm::serve::Executor {
     size_t lane_bytes = 0;
     bool per_request = false;
     int large_nnz = 2048;
+    int block_sets = 0;            // a group this small gives every set a block of 8 warps
     std::vector<Lane> lanes;
     std::atomic<int64_t> kernel_launches{0};
 
@@ -50,12 +55,20 @@ class CudaExecutor : public dm::serve::Executor {
         lanes.resize((size_t)n_lanes);
         cudaError_t e = cudaSetDevice(dev);
         if (e != cudaSuccess) return DM_ECUDA;
+        int sms = 0;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return DM_ECUDA;
+        block_sets = 2 * sms;                       // two resident 8-warp blocks per SM
         for (auto &L : lanes) {
             int rc = dm_create(&L.ctx, dev, 0);
             if (rc) return rc;
             if ((e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&L.ev_in, cudaEventDisableTiming)) != cudaSuccess ||
                 (e = cudaMalloc(&L.d, bytes)) != cudaSuccess || (e = cudaMallocHost(&L.h, bytes)) != cudaSuccess)
                 return e == cudaErrorMemoryAllocation ? DM_ENOMEM : DM_ECUDA;
+            for (int i = 0; i < kGroupStreams; ++i)
+                if ((e = cudaStreamCreateWithFlags(&L.gst[i], cudaStreamNonBlocking)) != cudaSuccess ||
+                    (e = cudaEventCreateWithFlags(&L.ev_done[i], cudaEventDisableTiming)) != cudaSuccess)
+                    return DM_ECUDA;
         }
         return DM_OK;
     }
@@ -66,6 +79,12 @@ class CudaExecutor : public dm::serve::Executor {
             if (L.st) cudaStreamSynchronize(L.st);
             if (L.d) cudaFree(L.d);
             if (L.h) cudaFreeHost(L.h);
+            for (int i = 0; i < kGroupStreams; ++i) {
+                if (L.gst[i]) cudaStreamSynchronize(L.gst[i]);
+                if (L.gst[i]) cudaStreamDestroy(L.gst[i]);
+                if (L.ev_done[i]) cudaEventDestroy(L.ev_done[i]);
+            }
+            if (L.ev_in) cudaEventDestroy(L.ev_in);
             if (L.st) cudaStreamDestroy(L.st);
             if (L.ctx) dm_destroy(L.ctx);
         }
@@ -116,22 +135,38 @@ class CudaExecutor : public dm::serve::Executor {
             }
         }
         if ((e = cudaMemcpyAsync(L.d, L.h, in_end, cudaMemcpyHostToDevice, L.st)) != cudaSuccess) return DM_ECUDA;
+        // the groups run concurrently, each on a stream of its own after the input copy
+        const bool fork = !per_request && groups.size() > 1;
+        if (fork && (e = cudaEventRecord(L.ev_in, L.st)) != cudaSuccess) return DM_ECUDA;
         for (size_t g = 0; g < groups.size(); ++g) {
+            const size_t n = groups[g].reqs.size();
             int64_t max_nnz = 0;
             for (const Request *r : groups[g].reqs) max_nnz = r->nnz > max_nnz ? r->nnz : max_nnz;
-            // plain per-request form; else persistent warps, or the batched form when a set is
-            // large enough for a block of its own
-            const int form = per_request ? 1 : (large_nnz > 0 && max_nnz >= large_nnz ? 0 : 2);
+            // plain per-request form; a small group gives each set a block of 8 warps (batched
+            // form with every non-empty set in the large class); otherwise persistent warps, or
+            // the batched form when a set is large enough for a block of its own
+            int form = 2, large = -1;
+            if (per_request) form = 1;
+            else if ((int64_t)n <= block_sets) { form = 0; large = 1; }
+            else if (large_nnz > 0 && max_nnz >= large_nnz) form = 0;
+            cudaStream_t gs = fork ? L.gst[g % kGroupStreams] : L.st;
+            if (fork && (e = cudaStreamWaitEvent(gs, L.ev_in, 0)) != cudaSuccess) return DM_ECUDA;
             int rc = dm::serve_sketch(L.ctx, (const int64_t *)(L.d + lay[g].ip), (const uint32_t *)(L.d + lay[g].idx),
-                                      (const float *)(L.d + lay[g].w), (int64_t)groups[g].reqs.size(), groups[g].k,
-                                      groups[g].seed, (uint64_t *)(L.d + lay[g].out), L.d + lay[g].scr, form, L.st);
+                                      (const float *)(L.d + lay[g].w), (int64_t)n, groups[g].k, groups[g].seed,
+                                      (uint64_t *)(L.d + lay[g].out), L.d + lay[g].scr, form, large, gs);
             if (rc) {
                 cudaStreamSynchronize(L.st);
+                for (int i = 0; i < kGroupStreams; ++i) cudaStreamSynchronize(L.gst[i]);
                 return rc;
             }
             // kernels of the form: fast + general, plus classify, scan, scatter, large (batched)
             kernel_launches += form == 0 ? 6 : 2;
         }
+        if (fork)
+            for (int i = 0; i < kGroupStreams && (size_t)i < groups.size(); ++i)
+                if ((e = cudaEventRecord(L.ev_done[i], L.gst[i])) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(L.st, L.ev_done[i], 0)) != cudaSuccess)
+                    return DM_ECUDA;
         if (out_end > in_end &&
             (e = cudaMemcpyAsync(L.h + in_end, L.d + in_end, out_end - in_end, cudaMemcpyDeviceToHost, L.st)) !=
                 cudaSuccess)

@@ -364,11 +364,13 @@ __device__ __forceinline__ void fast_put(const FastMem &m, Sink &sink, uint32_t 
     sink.after_batch(lane, need);
 }
 
-// One rank-region-0 pass over tiles first, first + stride, ... of the row [.., end).  Returns 0,
-// an error code, or kDefer.
+// One rank-region-0 pass over tiles first, first + stride, ... of the row [.., end).  The areas
+// of each segment are split among nparts warps (this one is number part), 32 lanes each.
+// Returns 0, an error code, or kDefer.
 template <class Sink, bool COUNT>
 __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, int64_t end, const PassCut &pc,
-                         const FastMem &m, Sink &sink, int lane, unsigned long long *cnt) {
+                         const FastMem &m, Sink &sink, int lane, unsigned long long *cnt, int part = 0,
+                         int nparts = 1) {
     constexpr bool LOWER = Sink::kLowerCut;
     __syncwarp();
     for (int nu = lane; nu < kRowTab; nu += 32) {
@@ -418,9 +420,9 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         __syncwarp();
         if (base == 0) continue;
         const int n_el = nt * 32;
-        const uint32_t total = (uint32_t)base;
-        const uint32_t share = (total + 31) >> 5;
-        const uint32_t lo = share * (uint32_t)lane;
+        const uint32_t total = (uint32_t)base, lanes = 32u * (uint32_t)nparts;
+        const uint32_t share = (total + lanes - 1) / lanes;
+        const uint32_t lo = share * (32u * (uint32_t)part + (uint32_t)lane);
         uint32_t left = lo < total ? min(share, total - lo) : 0u;
         WalkF s;
         if (left) s.locate(lo, n_el, m);
@@ -626,11 +628,12 @@ struct WalkG {
     }
 };
 
-// One pass with the general walk over tiles first, first + stride, ... of the row [.., end).
-// Returns 0 or an error code.
+// One pass with the general walk over tiles first, first + stride, ... of the row [.., end), each
+// tile's areas split among nparts warps (this one is number part).  Returns 0 or an error code.
 template <class Sink, bool COUNT>
 __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, int64_t end, const PassCut &pc,
-                        const GenMem &m, Sink &sink, int lane, unsigned long long *cnt) {
+                        const GenMem &m, Sink &sink, int lane, unsigned long long *cnt, int part = 0,
+                        int nparts = 1) {
     constexpr bool LOWER = Sink::kLowerCut;
     for (int64_t tile = first; tile < end; tile += stride) {
         const int64_t pos = tile + lane;
@@ -651,8 +654,9 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
         __syncwarp();
         const uint64_t total = __shfl_sync(kFull, incl, 31);
         if (total == 0) continue;
-        const uint64_t share = (total + 31) >> 5;
-        const uint64_t lo = share * lane;
+        const uint64_t lanes = 32ull * (uint64_t)nparts;
+        const uint64_t share = (total + lanes - 1) / lanes;
+        const uint64_t lo = share * (32ull * (uint64_t)part + (uint64_t)lane);
         uint64_t left = lo < total ? min(share, total - lo) : 0;   // areas of this lane
         WalkG s;
         if (left) s.locate(lo, m, pc);
@@ -864,10 +868,11 @@ __global__ void __launch_bounds__(256) scatter_kernel(const SketchParams p) {
 }
 
 // Large sets: a block per set.  The block's warps share the set's k bucket minima in shared
-// memory (atomicMin works across warps) and take the set's tiles round-robin, each with its
-// own dart queue; passes are separated by block barriers.  A pass runs the fast walk when the
-// limit is below 1 and every tile allows it, else the general walk over all tiles (a dart seen
-// twice does not change a minimum).
+// memory (atomicMin works across warps).  A set of at least two tiles per warp has its tiles
+// dealt round-robin to the warps; a smaller one (few elements, much work) has every tile's
+// areas split among all the warps.  Passes are separated by block barriers.  A pass runs the
+// fast walk when the limit is below 1 and every tile allows it, else the general walk over all
+// tiles (a dart seen twice does not change a minimum).
 size_t large_block_bytes(int k, int warps) {
     const size_t per = kFastPathBytes > kGenPathBytes ? kFastPathBytes : kGenPathBytes;
     return sketch_sink_bytes(k) + (size_t)warps * per + 64;
@@ -893,6 +898,7 @@ __global__ void __launch_bounds__(256, 2) large_kernel(const SketchParams p) {
         if (wi >= n_work) break;
         const int64_t set = p.order[base + wi];
         const int64_t beg = p.indptr[set], end = p.indptr[set + 1];
+        const bool split = end - beg < 64 * (int64_t)nwarps;
         float l1 = 0.f;
         int bad = 0;
         for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
@@ -923,9 +929,13 @@ __global__ void __launch_bounds__(256, 2) large_kernel(const SketchParams p) {
                 pc.gm1 = rc.gm1;
                 pc.cthr = th;
                 int e = kDefer;
-                if (pc.rho_top == 0) e = fast_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, fm, sink, lane, cnt);
+                if (pc.rho_top == 0)
+                    e = split ? fast_pass<SketchSink, COUNT>(p, beg, 32, end, pc, fm, sink, lane, cnt, wid, nwarps)
+                              : fast_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, fm, sink, lane, cnt);
                 const int any_defer = __syncthreads_or(e == kDefer);
-                if (any_defer) e = gen_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, gm, sink, lane, cnt);
+                if (any_defer)
+                    e = split ? gen_pass<SketchSink, COUNT>(p, beg, 32, end, pc, gm, sink, lane, cnt, wid, nwarps)
+                              : gen_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, gm, sink, lane, cnt);
                 ++passes;
                 if (__syncthreads_or(e == DM_ERANGE)) { err = DM_ERANGE; break; }
                 int empty = 0;

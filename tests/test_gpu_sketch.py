@@ -222,6 +222,27 @@ def test_forms_on_heavy_tailed_batch(dmx, torch_mod, oracle_mod, form):
     c2.close()
 
 
+@pytest.mark.parametrize("k", [1, 64, 1024])
+def test_block_per_set_split_and_stride(dmx, torch_mod, oracle_mod, k):
+    """Every non-empty set on a block of 8 warps (large-set threshold 1): sets below 512 elements
+    split each tile's areas among the warps, larger ones deal their tiles; norms over six
+    decades exercise both walks."""
+    rng = np.random.default_rng(70 + k)
+    rows = []
+    for s in range(160):
+        nnz = int(rng.choice([0, 1, 2, 5, 31, 33, 100, 511, 512, 700, 3000]))
+        idx = np.sort(rng.choice(1 << 24, nnz, replace=False)).astype(np.uint32)
+        z = rng.lognormal(size=nnz)
+        rows.append((idx, (z / max(z.sum(), 1e-30) * 10 ** rng.uniform(-3, 3)).astype(np.float32)))
+    b = workloads.csr_of(rows)
+    c2 = dmx.dm_create(0)
+    dmx.dm_set_option(c2, dmx.OPT_LARGE_NNZ, 1)
+    got, rc = gpu_sketch(dmx, torch_mod, c2, b, k, 23)
+    c2.close()
+    assert rc == 0
+    assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 23, threads=THREADS), f"k={k}")
+
+
 def test_counters_and_streams(dmx, torch_mod, ctx, oracle_mod):
     torch = torch_mod
     b = workloads.workload0(300)
