@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--form", choices=["batched", "plain", "persistent"], default="batched",
                     help="launch form (the plain form is the one-warp-per-set reference)")
     ap.add_argument("--large-nnz", type=int, default=None, help="batched form: element count of a large set")
+    ap.add_argument("--phi0", type=float, default=None, help="initial phi (launch setting; with --autotune off)")
+    ap.add_argument("--wpb", type=int, default=None, help="warps per block (launch setting; with --autotune off)")
     ap.add_argument("--autotune", choices=["on", "off"], default="on",
                     help="dm_autotune on a prefix of the batch before the warm-up (launch settings only)")
     ap.add_argument("--no-graph", action="store_true", help="plain launches instead of CUDA-graph replay")
@@ -262,10 +264,17 @@ def gpu_arm(args):
         keys = torch.empty((n, kk), dtype=torch.int64, device="cuda")
         outw = torch.empty((n, words), dtype=torch.int64, device="cuda") if wl == "W1" else None
     form_id = {"batched": dmx.FORM_BATCHED, "plain": dmx.FORM_PLAIN, "persistent": dmx.FORM_PERSISTENT}[args.form]
+    def manual_settings(c):
+        dmx.dm_set_option(c, dmx.OPT_FORM, form_id)
+        if args.large_nnz is not None:
+            dmx.dm_set_option(c, dmx.OPT_LARGE_NNZ, args.large_nnz)
+        if args.phi0 is not None:
+            dmx.dm_set_option(c, dmx.OPT_LSH_PHI0 if wl == "W3" else dmx.OPT_PHI0, int(round(args.phi0 * 1024)))
+        if args.wpb is not None:
+            dmx.dm_set_option(c, dmx.OPT_WARPS_PER_BLOCK, args.wpb)
+
     ctx = dmx.dm_create(local)
-    dmx.dm_set_option(ctx, dmx.OPT_FORM, form_id)
-    if args.large_nnz is not None:
-        dmx.dm_set_option(ctx, dmx.OPT_LARGE_NNZ, args.large_nnz)
+    manual_settings(ctx)
     stream = torch.cuda.current_stream()
 
     def launch(c):
@@ -296,13 +305,12 @@ def gpu_arm(args):
     cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
     cctx = dmx.dm_create(local)
     dmx.dm_set_option(cctx, dmx.OPT_COUNTERS, cnt.data_ptr())
-    dmx.dm_set_option(cctx, dmx.OPT_FORM, form_id)
-    if args.large_nnz is not None:
-        dmx.dm_set_option(cctx, dmx.OPT_LARGE_NNZ, args.large_nnz)
+    manual_settings(cctx)
     if tuning:
         dmx.dm_set_option(cctx, dmx.OPT_FORM, tuning["form"])
         dmx.dm_set_option(cctx, dmx.OPT_WARPS_PER_BLOCK, tuning["warps_per_block"])
         dmx.dm_set_option(cctx, dmx.OPT_LARGE_NNZ, tuning["large_nnz"])
+        dmx.dm_set_option(cctx, dmx.OPT_LARGE_WORK, tuning["large_work"])
         dmx.dm_set_option(cctx, dmx.OPT_LSH_PHI0 if wl == "W3" else dmx.OPT_PHI0, tuning["phi0_1024"])
     launch(cctx)
     dmx.dm_sync_status(cctx)

@@ -153,9 +153,13 @@ enum dm_option {
                                    same shape patches the least recently used executable in place.
                                    Capture runs on a context-owned stream, so the caller's stream
                                    may itself be under capture.  0 (default): plain launches. */
-    DM_OPT_TUNED = 8            /* 1 (default): calls use the settings dm_autotune stored for their
+    DM_OPT_TUNED = 8,           /* 1 (default): calls use the settings dm_autotune stored for their
                                    (kind, k, K, b), in place of the options above; 0: ignore them;
                                    2: forget them */
+    DM_OPT_LARGE_WORK = 9       /* batched form: a set whose Lemma 2 estimate of the areas it
+                                   inspects (phi0 t + sum_i (log2(1 + t x_i) + 1) +
+                                   nnz log2(1 + phi0/|x|_1)) reaches this value also gets a block of
+                                   8 warps (default 0 = never; dm_lsh never does) */
 };
 int dm_set_option(dm_ctx *ctx, int option, int64_t value);
 
@@ -165,6 +169,7 @@ typedef struct dm_tuning {
     int32_t warps_per_block;  /* warps per block actually used */
     int32_t phi0_1024;        /* initial phi, as value/1024 */
     int32_t large_nnz;        /* DM_OPT_LARGE_NNZ value */
+    int32_t large_work;       /* DM_OPT_LARGE_WORK value */
     int64_t sets_timed;       /* rows of the batch the trials ran on */
     float ms_default;         /* median time of the trial batch with the context's options */
     float ms_tuned;           /* median time with the chosen settings */

@@ -21,11 +21,11 @@ from .build import LIB, build
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
            "dm_sketch_host", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
            "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
-           "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "FORM_BATCHED",
+           "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "OPT_LARGE_WORK", "FORM_BATCHED",
            "FORM_PLAIN", "FORM_PERSISTENT", "dm_autotune", "Tuning", "Server", "EAGAIN"]
 
 OPT_PHI0, OPT_COUNTERS, OPT_FORM, OPT_WARPS_PER_BLOCK, OPT_LSH_PHI0, OPT_LARGE_NNZ = 1, 2, 3, 4, 5, 6
-OPT_GRAPH, OPT_TUNED = 7, 8
+OPT_GRAPH, OPT_TUNED, OPT_LARGE_WORK = 7, 8, 9
 EAGAIN, ETIMEOUT = 7, 4
 FORM_BATCHED, FORM_PLAIN, FORM_PERSISTENT = 0, 1, 2
 _lock = threading.Lock()
@@ -228,8 +228,8 @@ NOALLOC_MAX_SETS = 262144
 class Tuning(ctypes.Structure):
     """dm_tuning: the settings dm_autotune chose."""
     _fields_ = [("form", ctypes.c_int32), ("warps_per_block", ctypes.c_int32), ("phi0_1024", ctypes.c_int32),
-                ("large_nnz", ctypes.c_int32), ("sets_timed", ctypes.c_int64), ("ms_default", ctypes.c_float),
-                ("ms_tuned", ctypes.c_float)]
+                ("large_nnz", ctypes.c_int32), ("large_work", ctypes.c_int32), ("sets_timed", ctypes.c_int64),
+                ("ms_default", ctypes.c_float), ("ms_tuned", ctypes.c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

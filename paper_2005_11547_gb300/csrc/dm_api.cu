@@ -26,6 +26,7 @@ struct Choice {
     int wpb;            // warps (sets) per block, 0 = automatic
     float phi0;         // initial phi of Theorem 1's loop
     int large_nnz;      // batched form: element count from which a set gets a whole block
+    float large_work;   // batched form: Lemma 2 work estimate from which a set gets one (0: off)
 };
 
 struct TunedEntry {
@@ -64,6 +65,7 @@ struct dm_ctx {
     int form = 0;                  // 0 batched, 1 plain, 2 persistent in input order
     int warps_per_block = 0;       // 0 = automatic
     int large_nnz = 2048;          // batched form: sets with this many elements get a block
+    float large_work = 0.f;        // batched form: sets with this work estimate get a block
     // staging for the host-buffer entry points
     void *d_stage = nullptr;
     size_t d_stage_bytes = 0;
@@ -193,7 +195,7 @@ int occupancy(dm_ctx *ctx, int which, bool lsh, bool bbit, int wpb, size_t smem)
 }
 
 Choice choose(const dm_ctx *ctx, bool lsh, int k, int K, int b) {
-    Choice c{ctx->form, ctx->warps_per_block, lsh ? ctx->phi0_lsh : ctx->phi0, ctx->large_nnz};
+    Choice c{ctx->form, ctx->warps_per_block, lsh ? ctx->phi0_lsh : ctx->phi0, ctx->large_nnz, ctx->large_work};
     if (ctx->use_tuned)
         for (const auto &e : ctx->tuned)
             if (e.lsh == lsh && e.k == k && e.K == K && e.b == b) return e.c;
@@ -276,7 +278,8 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
     // batched form (default): large sets get a block of 8 warps
     p.large_warps = 8;
     p.large_nnz = lsh ? 0 : ch.large_nnz;
-    if (p.large_nnz > 0) {
+    p.large_work = lsh ? 0.f : ch.large_work;
+    if (p.large_nnz > 0 || p.large_work > 0.f) {
         const size_t lb = dm::large_block_bytes(k, p.large_warps);
         if (lb <= 227 * 1024) pl.grid_large = ctx->sm_count * occupancy(ctx, 2, false, bbit, p.large_warps, lb);
         else p.large_nnz = 0;
@@ -322,7 +325,8 @@ int run_plan(dm_ctx *ctx, const Plan &pl, cudaStream_t st) {
     // same shape: same kernels in the same order (form, kind, templates, large kernel on/off)
     auto same_shape = [&](const Plan &a) {
         return a.form == pl.form && a.lsh == pl.lsh && a.bbit == pl.bbit && a.count == pl.count &&
-               (a.grid_large > 0 && a.p.large_nnz > 0) == (pl.grid_large > 0 && pl.p.large_nnz > 0);
+               (a.grid_large > 0 && (a.p.large_nnz > 0 || a.p.large_work > 0.f)) ==
+                   (pl.grid_large > 0 && (pl.p.large_nnz > 0 || pl.p.large_work > 0.f));
     };
     GraphEntry *slot = nullptr;
     for (auto &g : ctx->graphs)
@@ -627,7 +631,7 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
     const bool use_graph = ctx->use_graph;
     ctx->use_graph = false;                          // trials of one-off plans
     Choice best{ctx->form == 1 ? 0 : ctx->form, ctx->warps_per_block, is_lsh ? ctx->phi0_lsh : ctx->phi0,
-                ctx->large_nnz};
+                ctx->large_nnz, ctx->large_work};
     float best_ms = 0.f, default_ms = 0.f;
     rc = e == cudaSuccess ? time_choice(best, best_ms) : cuda_fail(e);
     default_ms = best_ms;
@@ -652,6 +656,9 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
         try_set([](Choice &c, int v) { c.wpb = v; }, std::vector<int>{2, 4, 8});
         if (!is_lsh && max_nnz >= 256)
             try_set([](Choice &c, int v) { c.large_nnz = v; }, std::vector<int>{0, 256, 512, 1024, 2048, 4096, 8192});
+        if (!is_lsh)
+            try_set([](Choice &c, float v) { c.large_work = v; },
+                    std::vector<float>{0.f, 16384.f, 32768.f, 65536.f, 131072.f});
         try_set([](Choice &c, int v) { c.form = v; }, std::vector<int>{0, 2});
     }
     ctx->use_graph = use_graph;
@@ -673,6 +680,7 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
         result->warps_per_block = best.wpb > 0 ? best.wpb : auto_warps(is_lsh, k, K);
         result->phi0_1024 = (int32_t)(best.phi0 * 1024.0f + 0.5f);
         result->large_nnz = best.large_nnz;
+        result->large_work = (int32_t)best.large_work;
         result->sets_timed = n;
         result->ms_default = default_ms;
         result->ms_tuned = best_ms;
@@ -727,6 +735,10 @@ int dm_set_option(dm_ctx *ctx, int option, int64_t value) {
         case DM_OPT_LARGE_NNZ:
             if (value < 0 || value > 0x7FFFFFFF) return DM_EINVAL;
             ctx->large_nnz = (int)value;
+            return DM_OK;
+        case DM_OPT_LARGE_WORK:
+            if (value < 0 || value > (1ll << 40)) return DM_EINVAL;
+            ctx->large_work = (float)value;
             return DM_OK;
         case DM_OPT_LSH_PHI0:
             if (value < 1 || value > 1024 * 1024) return DM_EINVAL;

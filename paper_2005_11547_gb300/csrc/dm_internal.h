@@ -39,6 +39,7 @@ struct SketchParams {
     uint8_t *cls;               // per set: class * 32 + descending size bin
     unsigned int *hist;         // 3 x 32 bin counts, then 3 x 32 bin cursors, then class totals
     int32_t large_nnz;          // sets with at least this many elements go to the block kernel
+    float large_work;           // so do sets whose Lemma 2 work estimate reaches this (0: off)
     int32_t large_warps;        // warps per block of the large-set kernel
 };
 

@@ -801,7 +801,8 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) set_kernel(const Sketc
 
 // ==========================================================================================
 // Batched form.  classify: per set, class (0 fast: first limit below 1; 1 general; 2 large:
-// >= large_nnz elements, sketches only) and a size bin that sorts costlier sets first:
+// >= large_nnz elements or a work estimate >= large_work, sketches only) and a size bin that
+// sorts costlier sets first:
 // bin = 31 - floor(log2(E)) with E the Lemma 2 estimate of the areas inspected at the first
 // limit theta = phi0 / |x|_1,
 //     E = phi0 t + sum_i (log2(1 + t x_i) + 1) + nnz log2(1 + theta)
@@ -828,12 +829,13 @@ __global__ void __launch_bounds__(256) classify_kernel(const SketchParams p) {
             wlog += __shfl_xor_sync(kFull, wlog, o);
         }
         if (lane == 0) {
-            int c;
-            if (p.large_nnz > 0 && nnz >= p.large_nnz) c = 2;
-            else c = (!(l1 > 0.f) || __fdiv_rn(p.phi0, l1) < 1.0f) ? 0 : 1;   // zero/invalid rows: fast
             float est = 1.0f;
             if (l1 > 0.f && l1 < 3.0e38f && wlog < 3.0e38f)
                 est += p.phi0 * t + wlog + (float)nnz * __log2f(1.0f + p.phi0 / l1);
+            int c;
+            if (p.large_nnz > 0 && nnz >= p.large_nnz) c = 2;
+            else if (p.large_work > 0.f && nnz > 0 && est >= p.large_work) c = 2;
+            else c = (!(l1 > 0.f) || __fdiv_rn(p.phi0, l1) < 1.0f) ? 0 : 1;   // zero/invalid rows: fast
             // floor(log2(est)) from the exponent field (est >= 1, finite or +inf)
             int lg = (int)((__float_as_uint(est) >> 23) & 0xFFu) - 127;
             const int bin = 31 - (lg > 31 ? 31 : lg);
@@ -1049,7 +1051,10 @@ cudaError_t launch_batched(const SketchParams &p0, bool lsh, bool bbit, bool cou
                            int grid_general, int grid_large, cudaStream_t st) {
     SketchParams p = p0;
     p.sched = 2;
-    if (lsh || grid_large <= 0) p.large_nnz = 0;
+    if (lsh || grid_large <= 0) {
+        p.large_nnz = 0;
+        p.large_work = 0.f;
+    }
     cudaError_t e = cudaMemsetAsync(p.queue_count, 0, kHeaderBytes, st);
     if (e != cudaSuccess) return e;
     const int cgrid = (int)((p.n_sets + 7) / 8 < 4096 ? (p.n_sets + 7) / 8 : 4096);
@@ -1059,7 +1064,7 @@ cudaError_t launch_batched(const SketchParams &p0, bool lsh, bool bbit, bool cou
     scatter_kernel<<<sgrid, 256, 0, st>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the largest sets first: their blocks become resident before the fast kernel's
-    if (!lsh && grid_large > 0) {
+    if (!lsh && grid_large > 0 && (p.large_nnz > 0 || p.large_work > 0.f)) {
         if ((e = count ? (bbit ? launch_large<true, true>(p, grid_large, st) : launch_large<false, true>(p, grid_large, st))
                        : (bbit ? launch_large<true, false>(p, grid_large, st) : launch_large<false, false>(p, grid_large, st)))
             != cudaSuccess)

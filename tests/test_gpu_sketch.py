@@ -243,6 +243,20 @@ def test_block_per_set_split_and_stride(dmx, torch_mod, oracle_mod, k):
     assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 23, threads=THREADS), f"k={k}")
 
 
+def test_large_class_by_work_estimate(dmx, torch_mod, oracle_mod):
+    """Sets sent to the block kernel by their work estimate (DM_OPT_LARGE_WORK) rather than their
+    size: same bits as the oracle."""
+    b = workloads.workload2(600)
+    c2 = dmx.dm_create(0)
+    dmx.dm_set_option(c2, dmx.OPT_LARGE_NNZ, 0)
+    dmx.dm_set_option(c2, dmx.OPT_LARGE_WORK, 12000)
+    for k in (64, 1024):
+        got, rc = gpu_sketch(dmx, torch_mod, c2, b, k, 29)
+        assert rc == 0
+        assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 29, threads=THREADS), f"k={k}")
+    c2.close()
+
+
 def test_counters_and_streams(dmx, torch_mod, ctx, oracle_mod):
     torch = torch_mod
     b = workloads.workload0(300)
