@@ -291,7 +291,7 @@ def gpu_arm(args):
         if wl == "W1":
             tuning = dmx.dm_autotune(ctx, ip, ix, w, K_SLOTS, SEED, b=B_BITS, stream=stream)
         elif wl == "W2":
-            tuning = dmx.dm_autotune(ctx, ip, ix, w, 1024, SEED, max_sets=50_000, stream=stream)
+            tuning = dmx.dm_autotune(ctx, ip, ix, w, 1024, SEED, max_sets=n, stream=stream)
         else:
             tuning = dmx.dm_autotune(ctx, ip, ix, w, 64, SEED, lsh_K=8, stream=stream)
     if not args.no_graph:

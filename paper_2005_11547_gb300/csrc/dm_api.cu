@@ -84,6 +84,9 @@ struct dm_ctx {
     cudaStream_t capture_stream = nullptr;
     // resident blocks per SM, per kernel and launch shape
     std::vector<std::pair<uint64_t, int>> occupancy;
+    // side stream of the large-set kernel (created on first use)
+    dm::SideStream side = {nullptr, nullptr, nullptr};
+    bool side_ready = false;
 };
 
 namespace {
@@ -287,9 +290,28 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
     return DM_OK;
 }
 
-cudaError_t launch_plan(const Plan &pl, cudaStream_t st) {
-    if (pl.form == 0)
-        return dm::launch_batched(pl.p, pl.lsh, pl.bbit, pl.count, pl.grid_fast, pl.grid_general, pl.grid_large, st);
+cudaError_t ensure_side(dm_ctx *ctx) {
+    if (ctx->side_ready) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&ctx->side.st, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->side.join, cudaEventDisableTiming)) != cudaSuccess)
+        return e;
+    ctx->side_ready = true;
+    return cudaSuccess;
+}
+
+cudaError_t launch_plan(dm_ctx *ctx, const Plan &pl, cudaStream_t st) {
+    if (pl.form == 0) {
+        const dm::SideStream *side = nullptr;
+        if (pl.grid_large > 0 && !pl.lsh) {
+            cudaError_t e = ensure_side(ctx);
+            if (e != cudaSuccess) return e;
+            side = &ctx->side;
+        }
+        return dm::launch_batched(pl.p, pl.lsh, pl.bbit, pl.count, pl.grid_fast, pl.grid_general, pl.grid_large, st,
+                                  side);
+    }
     return dm::launch_sets(pl.p, pl.lsh, pl.bbit, pl.count, pl.grid_fast, pl.grid_general, st);
 }
 
@@ -303,7 +325,7 @@ void drop_graphs(dm_ctx *ctx) {
 // patched into the least recently used executable (when its launch sequence has the same
 // shape) or instantiated, the cache holding at most kMaxGraphs.
 int run_plan(dm_ctx *ctx, const Plan &pl, cudaStream_t st) {
-    if (!ctx->use_graph) return cuda_fail(launch_plan(pl, st));
+    if (!ctx->use_graph) return cuda_fail(launch_plan(ctx, pl, st));
     for (auto &g : ctx->graphs)
         if (std::memcmp(&g.plan, &pl, sizeof(Plan)) == 0) {
             g.used = ++ctx->graph_tick;
@@ -316,7 +338,7 @@ int run_plan(dm_ctx *ctx, const Plan &pl, cudaStream_t st) {
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return cuda_fail(e);
-    cudaError_t el = launch_plan(pl, ctx->capture_stream);
+    cudaError_t el = launch_plan(ctx, pl, ctx->capture_stream);
     e = cudaStreamEndCapture(ctx->capture_stream, &graph);
     if (el != cudaSuccess || e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -461,6 +483,11 @@ int dm_destroy(dm_ctx *ctx) {
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
     drop_graphs(ctx);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->side_ready) {
+        cudaStreamDestroy(ctx->side.st);
+        cudaEventDestroy(ctx->side.fork);
+        cudaEventDestroy(ctx->side.join);
+    }
     delete ctx;
     return DM_OK;
 }

@@ -62,8 +62,14 @@ cudaError_t launch_sets(const SketchParams &p, bool lsh, bool bbit, bool count, 
 // estimate), then the persistent
 // fast kernel, the persistent general kernel (general sets and those the fast kernel defers)
 // and, for sketches, the block-per-set kernel over large sets.  grid_large = 0: no large class.
+// A second stream for the large-set kernel, forked from and joined back to the call's stream
+// with the two events (so the sequence stays capturable as a graph).
+struct SideStream {
+    cudaStream_t st;
+    cudaEvent_t fork, join;
+};
 cudaError_t launch_batched(const SketchParams &p, bool lsh, bool bbit, bool count, int grid_fast,
-                           int grid_general, int grid_large, cudaStream_t st);
+                           int grid_general, int grid_large, cudaStream_t st, const SideStream *side = nullptr);
 
 // Shared memory of the large-set kernel's blocks.
 size_t large_block_bytes(int k, int warps);

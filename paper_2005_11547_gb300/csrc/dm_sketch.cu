@@ -1048,7 +1048,7 @@ cudaError_t launch_sets(const SketchParams &p, bool lsh, bool bbit, bool count, 
 }
 
 cudaError_t launch_batched(const SketchParams &p0, bool lsh, bool bbit, bool count, int grid_fast,
-                           int grid_general, int grid_large, cudaStream_t st) {
+                           int grid_general, int grid_large, cudaStream_t st, const SideStream *side) {
     SketchParams p = p0;
     p.sched = 2;
     if (lsh || grid_large <= 0) {
@@ -1063,10 +1063,20 @@ cudaError_t launch_batched(const SketchParams &p0, bool lsh, bool bbit, bool cou
     const int sgrid = (int)((p.n_sets + 255) / 256 < 4096 ? (p.n_sets + 255) / 256 : 4096);
     scatter_kernel<<<sgrid, 256, 0, st>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // the largest sets first: their blocks become resident before the fast kernel's
-    if (!lsh && grid_large > 0 && (p.large_nnz > 0 || p.large_work > 0.f)) {
-        if ((e = count ? (bbit ? launch_large<true, true>(p, grid_large, st) : launch_large<false, true>(p, grid_large, st))
-                       : (bbit ? launch_large<true, false>(p, grid_large, st) : launch_large<false, false>(p, grid_large, st)))
+    // the large sets are independent of the fast kernel's deferrals: with a side stream their
+    // kernel runs beside the fast and general kernels (each fills the SMs the other leaves),
+    // else first, so that their blocks become resident before the fast kernel's
+    const bool large = !lsh && grid_large > 0 && (p.large_nnz > 0 || p.large_work > 0.f);
+    cudaStream_t lst = st;
+    if (large && side) {
+        if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(side->st, side->fork, 0)) != cudaSuccess)
+            return e;
+        lst = side->st;
+    }
+    if (large) {
+        if ((e = count ? (bbit ? launch_large<true, true>(p, grid_large, lst) : launch_large<false, true>(p, grid_large, lst))
+                       : (bbit ? launch_large<true, false>(p, grid_large, lst) : launch_large<false, false>(p, grid_large, lst)))
             != cudaSuccess)
             return e;
     }
@@ -1075,7 +1085,13 @@ cudaError_t launch_batched(const SketchParams &p0, bool lsh, bool bbit, bool cou
         return launch_mode<LshSink, 1>(p, false, count, grid_general, st);
     }
     if ((e = launch_mode<SketchSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
-    return launch_mode<SketchSink, 1>(p, bbit, count, grid_general, st);
+    if ((e = launch_mode<SketchSink, 1>(p, bbit, count, grid_general, st)) != cudaSuccess) return e;
+    if (large && side) {
+        if ((e = cudaEventRecord(side->join, side->st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 size_t warp_bytes(bool lsh, int k, int K, int mode) {
