@@ -55,7 +55,7 @@ __host__ __device__ size_t sketch_sink_bytes(int k) { return ((size_t)k * 8 + 15
 
 size_t lsh_sink_bytes(int L, int K) {
     size_t B = 2 * (size_t)K;
-    size_t b = (size_t)L * 8 * (B + 1)           // candidate buffers and thresholds
+    size_t b = (size_t)L * 8 * (B + 2)           // candidate buffers (stride B + 1) and thresholds
              + (size_t)kOverflow * 8               // overflow keys
              + (size_t)L * 4                       // counts
              + 16                                  // overflow count
@@ -129,12 +129,14 @@ struct SketchSink {
 // up to B = 2K candidates and a threshold tau (its K-th smallest key after the last
 // compaction; keys >= tau can never enter the bottom K).  Appends past B go to an overflow
 // list; after each batch, buckets that filled up are compacted to their K smallest keys.
-// Band passes must not add a dart twice, so darts below the previous limit are cut.
+// Band passes must not add a dart twice, so darts below the previous limit are cut.  Bucket
+// arrays are B + 1 entries apart, so that lanes compacting neighbouring buckets at once hit
+// different shared-memory banks.
 struct LshSink {
     uint64_t *buf, *tau, *ovf_k;
     uint32_t *cnt, *ovf_n;
     uint16_t *ovf_b;
-    uint32_t L, K, B;
+    uint32_t L, K, B, S;                          // S = B + 1: stride between bucket arrays
     static constexpr bool kLowerCut = true;
     static constexpr bool kRing = true;           // kept darts are buffered and put 32 at a time
 
@@ -142,8 +144,9 @@ struct LshSink {
         L = (uint32_t)p.k;
         K = (uint32_t)p.K;
         B = 2 * K;
+        S = B + 1;
         buf = reinterpret_cast<uint64_t *>(base);
-        tau = buf + (size_t)L * B;
+        tau = buf + (size_t)L * S;
         ovf_k = tau + L;
         cnt = reinterpret_cast<uint32_t *>(ovf_k + kOverflow);
         ovf_n = cnt + L;
@@ -164,7 +167,7 @@ struct LshSink {
         if (key >= tau[b]) return false;
         const uint32_t pos = atomicAdd(&cnt[b], 1u);
         if (pos < B) {
-            buf[(size_t)b * B + pos] = key;
+            buf[(size_t)b * S + pos] = key;
         } else {
             const uint32_t o = atomicAdd(ovf_n, 1u);       // < kOverflow: a batch has <= 64 darts
             ovf_k[o] = key;
@@ -174,7 +177,7 @@ struct LshSink {
     }
     // Sort a bucket's candidates, merge its overflow entries and keep the K smallest.
     __device__ void compact(uint32_t b, uint32_t no) {
-        uint64_t *v = buf + (size_t)b * B;
+        uint64_t *v = buf + (size_t)b * S;
         uint32_t n = min(cnt[b], B);
         for (uint32_t i = 1; i < n; ++i) {               // insertion sort
             uint64_t x = v[i];
@@ -222,7 +225,7 @@ struct LshSink {
                 continue;
             }
             compact(b, 0);                               // sorted, exactly K
-            const uint64_t *v = buf + (size_t)b * B;
+            const uint64_t *v = buf + (size_t)b * S;
             uint64_t h = kLshInit;
             for (uint32_t m = 0; m < K; ++m) h = mix64(h ^ v[m]);
             o[b] = (uint32_t)(h >> 32);
