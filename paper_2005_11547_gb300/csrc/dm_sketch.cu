@@ -260,30 +260,36 @@ constexpr int kSegTiles = 4, kSeg = 32 * kSegTiles;
 
 constexpr int kKept = 64;            // kept-dart ring (LSH): drained 32 at a time
 
+// Per-pass record of weight region nu (32 bytes, read with two 16-byte loads): the area
+// counter offset kt, the integer rank thresholds of this and of the previous pass, and rows.
+struct RowRec {
+    uint64_t kt, pthr;
+    uint32_t rlo, rhi;
+    uint64_t plo;
+};
+// Per-element record of a segment (16 bytes, one load): element key, offset of its first area in
+// the segment, and vtop | nu_top << 24 (nu_top = -1: no areas).
+struct ElRec {
+    uint64_t e;
+    uint32_t off, vn;
+};
+
 struct FastMem {
-    uint64_t *te, *kt, *pthr, *plo;     // te[kSeg]; kt, pthr, plo [kRowTab]
-    uint32_t *tv, *toff, *rlo, *rhi;    // tv, toff [kSeg]; rlo, rhi [kRowTab]
-    signed char *tnu;                   // [kSeg]
+    RowRec *rt;                         // [kRowTab]
+    ElRec *el;                          // [kSeg]
     uint64_t *kd;                       // ring: kept darts' hashes [kKept] (sinks with kRing)
     uint32_t *kc;                       // ring: their rank codes [kKept]
 };
 
-constexpr size_t kFastPathBytes = (size_t)kSeg * 8 + 3 * kRowTab * 8 + 2 * (size_t)kSeg * 4 + 2 * kRowTab * 4 +
-                                  (size_t)kSeg;
+constexpr size_t kFastPathBytes = (size_t)kRowTab * sizeof(RowRec) + (size_t)kSeg * sizeof(ElRec);
 constexpr size_t kFastRingBytes = (size_t)kKept * 12;
+static_assert(sizeof(RowRec) == 32 && sizeof(ElRec) == 16, "record layout");
 static_assert(kFastPathBytes % 16 == 0, "the ring after the fast-path tables must stay aligned");
 
 __device__ __forceinline__ FastMem carve_fast(unsigned char *base) {
     FastMem m;
-    m.te = reinterpret_cast<uint64_t *>(base);
-    m.kt = m.te + kSeg;
-    m.pthr = m.kt + kRowTab;
-    m.plo = m.pthr + kRowTab;
-    m.tv = reinterpret_cast<uint32_t *>(m.plo + kRowTab);
-    m.toff = m.tv + kSeg;
-    m.rlo = m.toff + kSeg;
-    m.rhi = m.rlo + kRowTab;
-    m.tnu = reinterpret_cast<signed char *>(m.rhi + kRowTab);
+    m.rt = reinterpret_cast<RowRec *>(base);
+    m.el = reinterpret_cast<ElRec *>(m.rt + kRowTab);
     m.kd = reinterpret_cast<uint64_t *>(base + kFastPathBytes);
     m.kc = reinterpret_cast<uint32_t *>(m.kd + kKept);
     return m;
@@ -310,29 +316,32 @@ struct WalkF {
     uint64_t e, ctr, pthr, plo;
 
     __device__ __forceinline__ void region(const FastMem &m) {
-        r = m.rlo[nu];
-        rhi = m.rhi[nu];
-        ctr = e + m.kt[nu];
-        pthr = m.pthr[nu];
-        plo = m.plo[nu];
+        const uint4 a = *reinterpret_cast<const uint4 *>(&m.rt[nu]);          // kt, pthr
+        const uint4 b = *(reinterpret_cast<const uint4 *>(&m.rt[nu]) + 1);    // rlo, rhi, plo
+        r = b.x;
+        rhi = b.y;
+        ctr = e + (((uint64_t)a.y << 32) | a.x);
+        pthr = ((uint64_t)a.w << 32) | a.z;
+        plo = ((uint64_t)b.w << 32) | b.z;
         vmax = nu == nutop ? vtop : kUMask;
     }
     __device__ __forceinline__ void load(const FastMem &m) {
-        e = m.te[el];
-        vtop = m.tv[el];
-        nutop = m.tnu[el];
+        const uint4 q = *reinterpret_cast<const uint4 *>(&m.el[el]);
+        e = ((uint64_t)q.y << 32) | q.x;
+        vtop = q.w & kUMask;
+        nutop = (int)(signed char)(q.w >> 24);
     }
     // position the walk on area idx of the segment (idx < its total)
     __device__ void locate(uint32_t idx, int n_el, const FastMem &m) {
         el = 0;                                   // last element whose offset is <= idx
         for (int step = kSeg / 2; step; step >>= 1) {
             const int c = el + step;
-            if (c < n_el && m.toff[c] <= idx) el = c;
+            if (c < n_el && m.el[c].off <= idx) el = c;
         }
         load(m);
-        uint32_t li = idx - m.toff[el];
+        uint32_t li = idx - m.el[el].off;
         for (nu = 0;; ++nu) {
-            const uint32_t rows = m.rhi[nu] - m.rlo[nu];
+            const uint32_t rows = m.rt[nu].rhi - m.rt[nu].rlo;
             if (li < rows) break;
             li -= rows;
         }
@@ -346,7 +355,7 @@ struct WalkF {
         while (r == rhi) {
             if (++nu > nutop) {
                 nu = 0;
-                do { ++el; } while (el < n_el && m.tnu[el] < 0);
+                do { ++el; } while (el < n_el && (signed char)(m.el[el].vn >> 24) < 0);
                 if (el >= n_el) return;
                 load(m);
             }
@@ -378,12 +387,13 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
     __syncwarp();
     for (int nu = lane; nu < kRowTab; nu += 32) {
         const int n = nu > kMaxRegion ? kMaxRegion : nu;
+        RowRec &rr = m.rt[nu];
         const uint32_t lo = n ? (uint32_t)min(pc.gfl_lo >> (64 - n), (uint64_t)0xFFFFFFFFu) : 0u;
-        m.rlo[nu] = lo;
-        m.rhi[nu] = n ? (uint32_t)min((pc.gm1 >> (64 - n)) + 1, (uint64_t)0xFFFFFFFFu) : 1u;
-        m.kt[nu] = kGolden * (1ull + lo) + ((uint64_t)((21u * (uint32_t)nu) & 63u) << 58);
-        m.pthr[nu] = ceil_scaled(pc.cthr, n + 24);
-        m.plo[nu] = ceil_scaled(pc.cthr_lo, n + 24);
+        rr.rlo = lo;
+        rr.rhi = n ? (uint32_t)min((pc.gm1 >> (64 - n)) + 1, (uint64_t)0xFFFFFFFFu) : 1u;
+        rr.kt = kGolden * (1ull + lo) + ((uint64_t)((21u * (uint32_t)nu) & 63u) << 58);
+        rr.pthr = ceil_scaled(pc.cthr, n + 24);
+        rr.plo = ceil_scaled(pc.cthr_lo, n + 24);
     }
     const uint32_t g_hi = (uint32_t)(pc.gm1 >> 32), glo_hi = (uint32_t)(pc.gfl_lo >> 32);
     const unsigned lt = (1u << lane) - 1u;
@@ -412,11 +422,9 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
                 }
             }
             const uint64_t incl = warp_incl_scan(n_el, lane);
-            const int slot = nt * 32 + lane;
-            m.te[slot] = e;
-            m.tv[slot] = (uint32_t)(F >> 40);
-            m.tnu[slot] = (signed char)(n_el ? nutop : -1);
-            m.toff[slot] = (uint32_t)min(base + incl - n_el, (uint64_t)0xFFFFFFFFu);
+            const uint32_t off = (uint32_t)min(base + incl - n_el, (uint64_t)0xFFFFFFFFu);
+            const uint32_t vn = (uint32_t)(F >> 40) | ((uint32_t)(uint8_t)(signed char)(n_el ? nutop : -1) << 24);
+            *reinterpret_cast<uint4 *>(&m.el[nt * 32 + lane]) = make_uint4((uint32_t)e, (uint32_t)(e >> 32), off, vn);
             base += __shfl_sync(kFull, incl, 31);
         }
         if (base >= (1ull << 31)) return kDefer;
