@@ -53,8 +53,12 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
 // ==========================================================================================
 __host__ __device__ size_t sketch_sink_bytes(int k) { return ((size_t)k * 8 + 15) & ~(size_t)15; }
 
+// LSH buckets hold K + kLshSlack candidates between compactions: a small slack keeps a warp's
+// shared memory small (more resident warps), and compacting a few entries is cheap.
+constexpr uint32_t kLshSlack = 2;
+
 size_t lsh_sink_bytes(int L, int K) {
-    size_t B = 2 * (size_t)K;
+    size_t B = (size_t)K + kLshSlack;
     size_t b = (size_t)L * 8 * (B + 2)           // candidate buffers (stride B + 1) and thresholds
              + (size_t)kOverflow * 8               // overflow keys
              + (size_t)L * 4                       // counts
@@ -126,7 +130,7 @@ struct SketchSink {
 };
 
 // L buckets, each the K smallest keys of the darts hashed to it ((L, K) LSH).  A bucket keeps
-// up to B = 2K candidates and a threshold tau (its K-th smallest key after the last
+// up to B = K + kLshSlack candidates and a threshold tau (its K-th smallest key after the last
 // compaction; keys >= tau can never enter the bottom K).  Appends past B go to an overflow
 // list; after each batch, buckets that filled up are compacted to their K smallest keys.
 // Band passes must not add a dart twice, so darts below the previous limit are cut.  Bucket
@@ -143,7 +147,7 @@ struct LshSink {
     __device__ void bind(unsigned char *base, const SketchParams &p) {
         L = (uint32_t)p.k;
         K = (uint32_t)p.K;
-        B = 2 * K;
+        B = K + kLshSlack;
         S = B + 1;
         buf = reinterpret_cast<uint64_t *>(base);
         tau = buf + (size_t)L * S;
