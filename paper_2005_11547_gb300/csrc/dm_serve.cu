@@ -27,7 +27,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr int kGroupStreams = 4;  // groups of one batch run concurrently on these
 
 struct Lane {
-    dm_ctx *ctx = nullptr;
+    dm_ctx *ctx[kGroupStreams] = {};   // one per group stream: each has its own side streams
     cudaStream_t st = nullptr;
     cudaStream_t gst[kGroupStreams] = {};
     cudaEvent_t ev_in = nullptr, ev_done[kGroupStreams] = {};
@@ -59,8 +59,10 @@ class CudaExecutor : public dm::serve::Executor {
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return DM_ECUDA;
         block_sets = 2 * sms;                       // two resident 8-warp blocks per SM
         for (auto &L : lanes) {
-            int rc = dm_create(&L.ctx, dev, 0);
-            if (rc) return rc;
+            for (int i = 0; i < kGroupStreams; ++i) {
+                int rc = dm_create(&L.ctx[i], dev, 0);
+                if (rc) return rc;
+            }
             if ((e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking)) != cudaSuccess ||
                 (e = cudaEventCreateWithFlags(&L.ev_in, cudaEventDisableTiming)) != cudaSuccess ||
                 (e = cudaMalloc(&L.d, bytes)) != cudaSuccess || (e = cudaMallocHost(&L.h, bytes)) != cudaSuccess)
@@ -86,7 +88,8 @@ class CudaExecutor : public dm::serve::Executor {
             }
             if (L.ev_in) cudaEventDestroy(L.ev_in);
             if (L.st) cudaStreamDestroy(L.st);
-            if (L.ctx) dm_destroy(L.ctx);
+            for (int i = 0; i < kGroupStreams; ++i)
+                if (L.ctx[i]) dm_destroy(L.ctx[i]);
         }
     }
 
@@ -150,8 +153,9 @@ class CudaExecutor : public dm::serve::Executor {
             else if ((int64_t)n <= block_sets) { form = 0; large = 1; }
             else if (large_nnz > 0 && max_nnz >= large_nnz) form = 0;
             cudaStream_t gs = fork ? L.gst[g % kGroupStreams] : L.st;
+            dm_ctx *gctx = L.ctx[fork ? g % kGroupStreams : 0];
             if (fork && (e = cudaStreamWaitEvent(gs, L.ev_in, 0)) != cudaSuccess) return DM_ECUDA;
-            int rc = dm::serve_sketch(L.ctx, (const int64_t *)(L.d + lay[g].ip), (const uint32_t *)(L.d + lay[g].idx),
+            int rc = dm::serve_sketch(gctx, (const int64_t *)(L.d + lay[g].ip), (const uint32_t *)(L.d + lay[g].idx),
                                       (const float *)(L.d + lay[g].w), (int64_t)n, groups[g].k, groups[g].seed,
                                       (uint64_t *)(L.d + lay[g].out), L.d + lay[g].scr, form, large, gs);
             if (rc) {
@@ -171,10 +175,16 @@ class CudaExecutor : public dm::serve::Executor {
             (e = cudaMemcpyAsync(L.h + in_end, L.d + in_end, out_end - in_end, cudaMemcpyDeviceToHost, L.st)) !=
                 cudaSuccess)
             return DM_ECUDA;
-        if ((e = dm::status_to_host(L.ctx, L.st)) != cudaSuccess) return DM_ECUDA;
+        const int nctx = fork ? (int)(groups.size() < (size_t)kGroupStreams ? groups.size() : kGroupStreams) : 1;
+        for (int i = 0; i < nctx; ++i)
+            if ((e = dm::status_to_host(L.ctx[i], L.st)) != cudaSuccess) return DM_ECUDA;
         if ((e = cudaStreamSynchronize(L.st)) != cudaSuccess) return DM_ECUDA;
-        const int status = dm::status_take(L.ctx, L.st);
-        if (status == DM_ECUDA) return DM_ECUDA;
+        int status = 0;
+        for (int i = 0; i < nctx; ++i) {
+            const int s = dm::status_take(L.ctx[i], L.st);
+            if (s == DM_ECUDA) return DM_ECUDA;
+            if (!status) status = s;
+        }
         // deliver; a kernel-recorded error (a weight or norm out of range) marks its rows all-ones,
         // which a set with a positive weight never gets otherwise: those requests carry the error
         for (size_t g = 0; g < groups.size(); ++g) {
