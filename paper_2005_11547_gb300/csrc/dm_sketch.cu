@@ -264,10 +264,14 @@ constexpr int kSegTiles = 4, kSeg = 32 * kSegTiles;
 
 constexpr int kKept = 64;            // kept-dart ring (LSH): drained 32 at a time
 
-// Per-pass record of weight region nu (32 bytes, read with two 16-byte loads): the area
-// counter offset kt, the integer rank thresholds of this and of the previous pass, and rows.
-struct RowRec {
+// Per-pass records of weight region nu, two 16-byte halves in separate arrays (lanes reading
+// different regions then collide in a shared-memory bank only for regions 8 apart): the area
+// counter offset kt and the integer rank threshold of this pass; the rows and the threshold of
+// the previous pass.
+struct RowA {
     uint64_t kt, pthr;
+};
+struct RowB {
     uint32_t rlo, rhi;
     uint64_t plo;
 };
@@ -279,21 +283,23 @@ struct ElRec {
 };
 
 struct FastMem {
-    RowRec *rt;                         // [kRowTab]
+    RowA *ra;                           // [kRowTab]
+    RowB *rb;                           // [kRowTab]
     ElRec *el;                          // [kSeg]
     uint64_t *kd;                       // ring: kept darts' hashes [kKept] (sinks with kRing)
     uint32_t *kc;                       // ring: their rank codes [kKept]
 };
 
-constexpr size_t kFastPathBytes = (size_t)kRowTab * sizeof(RowRec) + (size_t)kSeg * sizeof(ElRec);
+constexpr size_t kFastPathBytes = (size_t)kRowTab * (sizeof(RowA) + sizeof(RowB)) + (size_t)kSeg * sizeof(ElRec);
 constexpr size_t kFastRingBytes = (size_t)kKept * 12;
-static_assert(sizeof(RowRec) == 32 && sizeof(ElRec) == 16, "record layout");
+static_assert(sizeof(RowA) == 16 && sizeof(RowB) == 16 && sizeof(ElRec) == 16, "record layout");
 static_assert(kFastPathBytes % 16 == 0, "the ring after the fast-path tables must stay aligned");
 
 __device__ __forceinline__ FastMem carve_fast(unsigned char *base) {
     FastMem m;
-    m.rt = reinterpret_cast<RowRec *>(base);
-    m.el = reinterpret_cast<ElRec *>(m.rt + kRowTab);
+    m.ra = reinterpret_cast<RowA *>(base);
+    m.rb = reinterpret_cast<RowB *>(m.ra + kRowTab);
+    m.el = reinterpret_cast<ElRec *>(m.rb + kRowTab);
     m.kd = reinterpret_cast<uint64_t *>(base + kFastPathBytes);
     m.kc = reinterpret_cast<uint32_t *>(m.kd + kKept);
     return m;
@@ -320,8 +326,8 @@ struct WalkF {
     uint64_t e, ctr, pthr, plo;
 
     __device__ __forceinline__ void region(const FastMem &m) {
-        const uint4 a = *reinterpret_cast<const uint4 *>(&m.rt[nu]);          // kt, pthr
-        const uint4 b = *(reinterpret_cast<const uint4 *>(&m.rt[nu]) + 1);    // rlo, rhi, plo
+        const uint4 a = *reinterpret_cast<const uint4 *>(&m.ra[nu]);          // kt, pthr
+        const uint4 b = *reinterpret_cast<const uint4 *>(&m.rb[nu]);          // rlo, rhi, plo
         r = b.x;
         rhi = b.y;
         ctr = e + (((uint64_t)a.y << 32) | a.x);
@@ -345,7 +351,7 @@ struct WalkF {
         load(m);
         uint32_t li = idx - m.el[el].off;
         for (nu = 0;; ++nu) {
-            const uint32_t rows = m.rt[nu].rhi - m.rt[nu].rlo;
+            const uint32_t rows = m.rb[nu].rhi - m.rb[nu].rlo;
             if (li < rows) break;
             li -= rows;
         }
@@ -391,13 +397,12 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
     __syncwarp();
     for (int nu = lane; nu < kRowTab; nu += 32) {
         const int n = nu > kMaxRegion ? kMaxRegion : nu;
-        RowRec &rr = m.rt[nu];
         const uint32_t lo = n ? (uint32_t)min(pc.gfl_lo >> (64 - n), (uint64_t)0xFFFFFFFFu) : 0u;
-        rr.rlo = lo;
-        rr.rhi = n ? (uint32_t)min((pc.gm1 >> (64 - n)) + 1, (uint64_t)0xFFFFFFFFu) : 1u;
-        rr.kt = kGolden * (1ull + lo) + ((uint64_t)((21u * (uint32_t)nu) & 63u) << 58);
-        rr.pthr = ceil_scaled(pc.cthr, n + 24);
-        rr.plo = ceil_scaled(pc.cthr_lo, n + 24);
+        m.rb[nu].rlo = lo;
+        m.rb[nu].rhi = n ? (uint32_t)min((pc.gm1 >> (64 - n)) + 1, (uint64_t)0xFFFFFFFFu) : 1u;
+        m.rb[nu].plo = ceil_scaled(pc.cthr_lo, n + 24);
+        m.ra[nu].kt = kGolden * (1ull + lo) + ((uint64_t)((21u * (uint32_t)nu) & 63u) << 58);
+        m.ra[nu].pthr = ceil_scaled(pc.cthr, n + 24);
     }
     const uint32_t g_hi = (uint32_t)(pc.gm1 >> 32), glo_hi = (uint32_t)(pc.gfl_lo >> 32);
     const unsigned lt = (1u << lane) - 1u;
