@@ -79,6 +79,8 @@ def _load():
         lib.dmo_sketch_bbit.restype = ctypes.c_int
         lib.dmo_lsh.argtypes = [P, P, P, i64, i32, i32, u64, P, dbl, P, P]
         lib.dmo_lsh.restype = ctypes.c_int
+        lib.dmo_bottomk.argtypes = [P, P, P, i64, i32, u64, P, dbl, P, P]
+        lib.dmo_bottomk.restype = ctypes.c_int
         lib.dmo_darthash.argtypes = [P, P, i64, i64, u64, P, flt, P, i64, P]
         lib.dmo_darthash.restype = ctypes.c_int64
         lib.dmo_dart_record_size.restype = ctypes.c_int64
@@ -239,6 +241,27 @@ def lsh(indptr, indices, weights, L: int, K: int, seed: int, *, phi0: float = 1.
         return lib.dmo_lsh(_ptr(ip), _ptr(indices), _ptr(weights), b - a, L, K, seed & (2**64 - 1),
                            _ptr(T), float(phi0), ctypes.c_void_p(out.ctypes.data + a * L * 4),
                            ctypes.c_void_p(wk.ctypes.data + a * 32))
+
+    _run_chunked(n, threads, fn)
+    return (out, wk) if work else out
+
+
+def bottomk(indptr, indices, weights, k: int, seed: int, *, phi0: float = 1.0, threads: int = 1,
+            work: bool = False):
+    """Bottom-k weighted sketch uint64[n, k] (Section 3): t = k, phi raised until DartHash returns
+    at least k darts, the k smallest keys in increasing order (all ones for an empty set)."""
+    lib = _load()
+    indptr, indices, weights = _csr(indptr, indices, weights)
+    n = len(indptr) - 1
+    out = np.empty((n, k), dtype=np.uint64)
+    wk = np.zeros((n, 4), dtype=np.int64)
+    T = _table()
+
+    def fn(a, b):
+        ip = indptr[a:b + 1]
+        return lib.dmo_bottomk(_ptr(ip), _ptr(indices), _ptr(weights), b - a, k, seed & (2**64 - 1), _ptr(T),
+                               float(phi0), ctypes.c_void_p(out.ctypes.data + a * k * 8),
+                               ctypes.c_void_p(wk.ctypes.data + a * 32))
 
     _run_chunked(n, threads, fn)
     return (out, wk) if work else out

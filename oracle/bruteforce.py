@@ -103,3 +103,20 @@ def sketch(indices, weights, k: int, t: int, seed: int, nu_box: int, rho_box: in
             if best[slot] is None or key < best[slot]:
                 best[slot] = key
     return best
+
+
+def bottomk(indices, weights, k: int, t: int, seed: int, nu_box: int, rho_box: int, T):
+    """Box-limited bottom-k sketch (Section 3, "Bottom-k minhash"): the k smallest keys of the
+    darts of rank below 2^(rho_box+1) - 1 that hit x, in increasing order, or None when the box
+    holds fewer than k of them (then the box cannot decide the k-th)."""
+    bound = Fraction(2 ** (rho_box + 1) - 1)
+    for x in weights:
+        assert Fraction(float(x)) * t < 2 ** (nu_box + 1) - 1, "box too small in weight"
+    keys = []
+    for i, x in zip(indices, weights):
+        if not x > 0:
+            continue
+        keys.extend(key for rank, key, q in box_darts(int(i), float(x), t, seed, nu_box, rho_box, T)
+                    if rank < bound)
+    keys.sort()
+    return keys[:k] if len(keys) >= k else None

@@ -394,6 +394,48 @@ int dmo_lsh(const int64_t *indptr, const uint32_t *indices, const float *weights
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Bottom-k weighted sketch (Section 3, "Bottom-k minhash"): t = k; phi is raised until   */
+/* DartHash returns at least k darts; the k smallest keys in increasing order.            */
+/* ------------------------------------------------------------------------------------ */
+int dmo_bottomk(const int64_t *indptr, const uint32_t *indices, const float *weights, int64_t n_sets,
+                int32_t k, uint64_t seed, const uint32_t *T, double phi0, uint64_t *out, int64_t *work) {
+    if (k < 1) return DMO_EINVAL;
+    uint64_t sigma = seed_key(seed);
+    int status = DMO_OK;
+    lsh_ctx c = { NULL, NULL, 0, 0, 1, 0 };
+    for (int64_t s = 0; s < n_sets; s++) {
+        int64_t bgn = indptr[s], end = indptr[s + 1];
+        const uint32_t *idx = indices + bgn; const float *wt = weights + bgn; int64_t nnz = end - bgn;
+        uint64_t *o = out + s * (int64_t)k;
+        for (int32_t j = 0; j < k; j++) o[j] = UINT64_MAX;
+        double l1;
+        int rc = check_row(wt, nnz, &l1);
+        dmo_work W = {0, 0, 0};
+        int64_t passes = 0;
+        if (!rc && l1 > 0.0) {
+            for (double phi = phi0; ; phi *= 2.0) {
+                if (phi > DMO_PHI_MAX) { rc = DMO_EOVERFLOW; break; }
+                float theta = (float)(phi / l1);
+                if (!(theta > 0.0f) || isinf(theta)) { rc = DMO_ERANGE; break; }
+                c.n = 0;
+                rc = darthash(idx, wt, nnz, (int64_t)k, sigma, T, theta, lsh_sink, &c, &W);
+                passes++;
+                if (c.oom) rc = DMO_ENOMEM;
+                if (rc) break;
+                if (c.n < k) continue;
+                qsort(c.key, (size_t)c.n, sizeof(uint64_t), cmp_u64);
+                for (int32_t j = 0; j < k; j++) o[j] = c.key[j];
+                break;
+            }
+        }
+        if (rc && !status) status = rc;
+        if (work) { work[4 * s] = W.areas; work[4 * s + 1] = W.darts; work[4 * s + 2] = W.kept; work[4 * s + 3] = passes; }
+    }
+    free(c.key); free(c.bucket);
+    return status;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Test access: the kept darts of one row at a fixed theta (Algorithm 1's output set D).  */
 /* ------------------------------------------------------------------------------------ */
 typedef struct { dmo_dart *buf; int64_t n, cap; } collect_ctx;
