@@ -94,6 +94,17 @@ int dm_sketch_bbit(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
 int dm_lsh(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
            int64_t n_sets, int32_t L, int32_t K, uint64_t seed, uint32_t *out, void *stream);
 
+/* Bottom-k weighted sketch (Section 3, "Bottom-k minhash and fast approximate near neighbor
+ * search": with t = k, raise phi until DartHash returns at least k darts and keep them sorted by
+ * rank).  out: uint64[n_sets * k]; row s holds the k smallest keys of set s's darts (the same
+ * 64-bit keys as dm_sketch: rank code << 32 | fingerprint, the fingerprint being the low 32 bits
+ * of the bucket hash) in increasing order.  A set with no positive weight gets all ones.  The
+ * union estimator |S_k(x v y) n S_k(x) n S_k(y)| / k of the weighted Jaccard similarity, with
+ * x v y the coordinatewise maximum, is Bin(k, J) / k.  1 <= k <= 1024 (the candidate buffer,
+ * 8 * 2^ceil(log2(max(2k, k + 32))) bytes per set, lives in shared memory). */
+int dm_bottomk(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+               int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream);
+
 /* dm_sketch / dm_sketch_bbit with HOST arrays: indptr, indices, weights, out_keys and
  * out_words are host pointers (page-locked memory gives full copy speed).  b = 0 computes keys
  * only (out_keys required, out_words ignored); b in {1, 2, 4, 8, 16, 32} also writes the b-bit
@@ -176,8 +187,8 @@ typedef struct dm_tuning {
 } dm_tuning;
 
 /* Launch-setting search (the paper has no counterpart; results never depend on the choice).
- * Runs the call that dm_sketch / dm_sketch_bbit (lsh = 0, K_or_b = b, 0 for keys only) or dm_lsh
- * (lsh = 1, k = L, K_or_b = K) would make on the first min(n_sets, max_sets) rows (max_sets <= 0:
+ * Runs the call that dm_sketch / dm_sketch_bbit (lsh = 0, K_or_b = b, 0 for keys only), dm_lsh
+ * (lsh = 1, k = L, K_or_b = K) or dm_bottomk (lsh = 2, K_or_b = 0) would make on the first min(n_sets, max_sets) rows (max_sets <= 0:
  * 65536) of the given device batch, timing each candidate with CUDA events on `stream` (median of
  * three runs after a warm-up): initial phi, then warps per block, then the large-set threshold,
  * then the form, each kept when it is faster.  Outputs of the trials go to temporary device

@@ -19,7 +19,7 @@ import threading
 from .build import LIB, build
 
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
-           "dm_sketch_host", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
+           "dm_sketch_host", "dm_bottomk", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
            "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
            "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "OPT_LARGE_WORK", "FORM_BATCHED",
            "FORM_PLAIN", "FORM_PERSISTENT", "dm_autotune", "Tuning", "Server", "EAGAIN"]
@@ -56,6 +56,7 @@ def load(path: str | None = None):
             "dm_sketch": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
             "dm_sketch_bbit": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_lsh": ([P, P, P, P, i64, i32, i32, u64, P, P], ctypes.c_int),
+            "dm_bottomk": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
             "dm_sketch_host": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_sync_status": ([P, P], ctypes.c_int),
             "dm_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -183,6 +184,20 @@ def dm_lsh(ctx: Context, indptr, indices, weights, L: int, K: int, seed: int, ou
     return out
 
 
+def dm_bottomk(ctx: Context, indptr, indices, weights, k: int, seed: int, out=None, stream=None):
+    """uint64[n_sets, k] bottom-k sketches: each row the k smallest keys in increasing order
+    (returned as an int64 tensor holding the same bits)."""
+    import torch
+    n, ip, ix, w = _csr_ptrs(indptr, indices, weights)
+    if out is None:
+        out = torch.empty((n, k), dtype=torch.int64, device=indptr.device)
+    elif out.numel() != n * k:
+        raise ValueError("out has the wrong size")
+    _check(load().dm_bottomk(ctx.handle, ip, ix, w, n, int(k), int(seed) & (2**64 - 1),
+                             _dev_ptr(out, "uint64", "out"), _stream(stream)), "dm_bottomk")
+    return out
+
+
 def dm_sketch_host(ctx: Context, indptr, indices, weights, k: int, seed: int, out_keys=None, b: int = 0,
                    out_words=None, stream=None):
     """dm_sketch (b = 0) or dm_sketch_bbit (b > 0) on host tensors (pinned memory for full copy
@@ -236,12 +251,13 @@ class Tuning(ctypes.Structure):
 
 
 def dm_autotune(ctx: Context, indptr, indices, weights, k: int, seed: int, b: int = 0, lsh_K: int = 0,
-                max_sets: int = 0, stream=None) -> dict:
+                max_sets: int = 0, stream=None, bottomk: bool = False) -> dict:
     """Time launch settings on a prefix of a device batch and store the fastest in the context
-    for later calls of the same kind.  Sketches: k, b (0 = keys only); LSH: k = L and lsh_K = K."""
+    for later calls of the same kind.  Sketches: k, b (0 = keys only); LSH: k = L and lsh_K = K;
+    bottom-k sketches: k and bottomk=True."""
     n, ip, ix, w = _csr_ptrs(indptr, indices, weights)
     res = Tuning()
-    lsh = 1 if lsh_K > 0 else 0
+    lsh = 2 if bottomk else (1 if lsh_K > 0 else 0)
     _check(load().dm_autotune(ctx.handle, ip, ix, w, n, lsh, int(k), int(lsh_K if lsh else b),
                               int(seed) & (2**64 - 1), int(max_sets), ctypes.cast(ctypes.byref(res), ctypes.c_void_p),
                               _stream(stream)), "dm_autotune")

@@ -30,7 +30,7 @@ struct Choice {
 };
 
 struct TunedEntry {
-    bool lsh;
+    int kind;
     int k, K, b;
     Choice c;
 };
@@ -39,7 +39,7 @@ struct TunedEntry {
 // plans compare equal with memcmp exactly when the launches would be identical.
 struct Plan {
     SketchParams p;
-    int lsh, bbit, count, form, grid_fast, grid_general, grid_large;
+    int kind, bbit, count, form, grid_fast, grid_general, grid_large;
 };
 
 struct GraphEntry {
@@ -154,8 +154,8 @@ int cuda_fail(cudaError_t e) {
 
 // Warps per block: as many as fit 96 KB of shared memory (so two or more blocks are resident),
 // at most 8.
-int auto_warps(bool lsh, int k, int K) {
-    size_t a = dm::warp_bytes(lsh, k, K, 0), b = dm::warp_bytes(lsh, k, K, 1);
+int auto_warps(int kind, int k, int K) {
+    size_t a = dm::warp_bytes(kind, k, K, 0), b = dm::warp_bytes(kind, k, K, 1);
     size_t per = a > b ? a : b;
     int w = (int)((96 * 1024) / per);
     if (w > 8) w = 8;
@@ -187,30 +187,33 @@ int ensure_queue(dm_ctx *ctx, int64_t n_sets) {
 
 // Blocks of a kernel resident per SM, cached per context (the query sets a kernel attribute
 // and costs a few microseconds).  which: 0 fast, 1 general, 2 large.
-int occupancy(dm_ctx *ctx, int which, bool lsh, bool bbit, int wpb, size_t smem) {
-    const uint64_t key = ((uint64_t)which) | ((uint64_t)lsh << 2) | ((uint64_t)bbit << 3) |
-                         ((uint64_t)wpb << 4) | ((uint64_t)smem << 12);
+int occupancy(dm_ctx *ctx, int which, int kind, bool bbit, int wpb, size_t smem) {
+    const uint64_t key = ((uint64_t)which) | ((uint64_t)kind << 2) | ((uint64_t)bbit << 4) |
+                         ((uint64_t)wpb << 5) | ((uint64_t)smem << 12);
     for (auto &e : ctx->occupancy)
         if (e.first == key) return e.second;
-    int nb = which == 2 ? dm::large_blocks_per_sm(bbit, wpb, smem) : dm::blocks_per_sm(lsh, which, bbit, wpb, smem);
+    int nb = which == 2 ? dm::large_blocks_per_sm(bbit, wpb, smem) : dm::blocks_per_sm(kind, which, bbit, wpb, smem);
     ctx->occupancy.emplace_back(key, nb);
     return nb;
 }
 
-Choice choose(const dm_ctx *ctx, bool lsh, int k, int K, int b) {
-    Choice c{ctx->form, ctx->warps_per_block, lsh ? ctx->phi0_lsh : ctx->phi0, ctx->large_nnz, ctx->large_work};
+Choice choose(const dm_ctx *ctx, int kind, int k, int K, int b) {
+    Choice c{ctx->form, ctx->warps_per_block, kind == dm::kLsh ? ctx->phi0_lsh : ctx->phi0, ctx->large_nnz,
+             ctx->large_work};
     if (ctx->use_tuned)
         for (const auto &e : ctx->tuned)
-            if (e.lsh == lsh && e.k == k && e.K == K && e.b == b) return e.c;
+            if (e.kind == kind && e.k == k && e.K == K && e.b == b) return e.c;
     return c;
 }
 
-// Checks a call and fills its plan: sketches (lsh = false: k minhashes, optional b-bit words)
-// or (L, K) LSH (lsh = true: k = L).  queue: scratch for the call's work queue (null = the
-// context's).  Returns DM_OK with pl.p.n_sets == 0 when there is nothing to launch.
+// Checks a call and fills its plan: sketches (kSketch: k minhashes, optional b-bit words), (L, K)
+// LSH (kLsh: k = L) or bottom-k sketches (kBottomK: the k smallest keys).  queue: scratch for the
+// call's work queue (null = the context's).  Returns DM_OK with pl.p.n_sets == 0 when there is
+// nothing to launch.
 int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
-              int64_t n_sets, bool lsh, int32_t k, int32_t K, int32_t b, uint64_t seed, uint64_t *out_words,
+              int64_t n_sets, int kind, int32_t k, int32_t K, int32_t b, uint64_t seed, uint64_t *out_words,
               uint64_t *out_keys, uint32_t *out_lsh, void *queue, const Choice &ch, Plan &pl) {
+    const bool lsh = kind == dm::kLsh;
     std::memset(&pl, 0, sizeof(pl));
     if (!ctx) return DM_EINVAL;
     int rc = check_csr(indptr, indices, weights, n_sets);
@@ -219,6 +222,9 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
     if (lsh) {
         if (k < 1 || k > 1024 || K < 1 || K > 32 || !out_lsh) return DM_EINVAL;
         t = (int64_t)k * K;
+    } else if (kind == dm::kBottomK) {
+        if (k < 1 || k > 1024 || !out_keys || b != 0) return DM_EINVAL;
+        t = k;                                      // Section 3: t = k for the bottom-k sketch
     } else {
         if (k < 1 || k > 8192) return DM_EINVAL;
         t = t_of_k(k);
@@ -230,8 +236,8 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
     if (bbit && !out_words) return DM_EINVAL;
     if (n_sets == 0) return DM_OK;
     if (n_sets > 0x7FFFFFFF) return DM_EINVAL;
-    const int wpb = ch.wpb > 0 ? ch.wpb : auto_warps(lsh, k, K);
-    const size_t smem_fast = dm::warp_bytes(lsh, k, K, 0) * wpb, smem = dm::warp_bytes(lsh, k, K, 1) * wpb;
+    const int wpb = ch.wpb > 0 ? ch.wpb : auto_warps(kind, k, K);
+    const size_t smem_fast = dm::warp_bytes(kind, k, K, 0) * wpb, smem = dm::warp_bytes(kind, k, K, 1) * wpb;
     if (smem > 227 * 1024 || smem_fast > 227 * 1024) return DM_EINVAL;     // L and K too large for LSH
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -257,11 +263,11 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
     p.status = ctx->d_status;
     p.counters = ctx->counters;
     p.warps_per_block = wpb;
-    p.warp_bytes = (int32_t)dm::warp_bytes(lsh, k, K, 1);
-    p.warp_bytes_fast = (int32_t)dm::warp_bytes(lsh, k, K, 0);
-    p.sink_bytes = (int32_t)dm::sink_bytes(lsh, k, K);
+    p.warp_bytes = (int32_t)dm::warp_bytes(kind, k, K, 1);
+    p.warp_bytes_fast = (int32_t)dm::warp_bytes(kind, k, K, 0);
+    p.sink_bytes = (int32_t)((dm::sink_bytes(kind, k, K) + 15) & ~(size_t)15);
     dm::carve_call_scratch(queue, n_sets, p);
-    pl.lsh = lsh;
+    pl.kind = kind;
     pl.bbit = bbit;
     pl.count = ctx->counters != nullptr;
     pl.form = ch.form;
@@ -273,15 +279,15 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
         return DM_OK;
     }
     // persistent grids: as many blocks as can be resident, never more than there are sets
-    const int64_t cap0 = (int64_t)ctx->sm_count * occupancy(ctx, 0, lsh, bbit, wpb, smem_fast);
-    const int64_t cap1 = (int64_t)ctx->sm_count * occupancy(ctx, 1, lsh, bbit, wpb, smem);
+    const int64_t cap0 = (int64_t)ctx->sm_count * occupancy(ctx, 0, kind, bbit, wpb, smem_fast);
+    const int64_t cap1 = (int64_t)ctx->sm_count * occupancy(ctx, 1, kind, bbit, wpb, smem);
     pl.grid_fast = (int)(blocks < cap0 ? blocks : cap0);
     pl.grid_general = (int)(blocks < cap1 ? blocks : cap1);
     if (ch.form == 2) return DM_OK;
     // batched form (default): large sets get a block of 8 warps
     p.large_warps = 8;
-    p.large_nnz = lsh ? 0 : ch.large_nnz;
-    p.large_work = lsh ? 0.f : ch.large_work;
+    p.large_nnz = kind != dm::kSketch ? 0 : ch.large_nnz;
+    p.large_work = kind != dm::kSketch ? 0.f : ch.large_work;
     if (p.large_nnz > 0 || p.large_work > 0.f) {
         const size_t lb = dm::large_block_bytes(k, p.large_warps);
         if (lb <= 227 * 1024) pl.grid_large = ctx->sm_count * occupancy(ctx, 2, false, bbit, p.large_warps, lb);
@@ -304,15 +310,15 @@ cudaError_t ensure_side(dm_ctx *ctx) {
 cudaError_t launch_plan(dm_ctx *ctx, const Plan &pl, cudaStream_t st) {
     if (pl.form == 0) {
         const dm::SideStream *side = nullptr;
-        if (pl.grid_large > 0 && !pl.lsh) {
+        if (pl.grid_large > 0 && pl.kind == dm::kSketch) {
             cudaError_t e = ensure_side(ctx);
             if (e != cudaSuccess) return e;
             side = &ctx->side;
         }
-        return dm::launch_batched(pl.p, pl.lsh, pl.bbit, pl.count, pl.grid_fast, pl.grid_general, pl.grid_large, st,
+        return dm::launch_batched(pl.p, pl.kind, pl.bbit, pl.count, pl.grid_fast, pl.grid_general, pl.grid_large, st,
                                   side);
     }
-    return dm::launch_sets(pl.p, pl.lsh, pl.bbit, pl.count, pl.grid_fast, pl.grid_general, st);
+    return dm::launch_sets(pl.p, pl.kind, pl.bbit, pl.count, pl.grid_fast, pl.grid_general, st);
 }
 
 void drop_graphs(dm_ctx *ctx) {
@@ -346,7 +352,7 @@ int run_plan(dm_ctx *ctx, const Plan &pl, cudaStream_t st) {
     }
     // same shape: same kernels in the same order (form, kind, templates, large kernel on/off)
     auto same_shape = [&](const Plan &a) {
-        return a.form == pl.form && a.lsh == pl.lsh && a.bbit == pl.bbit && a.count == pl.count &&
+        return a.form == pl.form && a.kind == pl.kind && a.bbit == pl.bbit && a.count == pl.count &&
                (a.grid_large > 0 && (a.p.large_nnz > 0 || a.p.large_work > 0.f)) ==
                    (pl.grid_large > 0 && (pl.p.large_nnz > 0 || pl.p.large_work > 0.f));
     };
@@ -384,13 +390,13 @@ int run_plan(dm_ctx *ctx, const Plan &pl, cudaStream_t st) {
 }
 
 int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
-             int64_t n_sets, bool lsh, int32_t k, int32_t K, int32_t b, uint64_t seed, uint64_t *out_words,
+             int64_t n_sets, int kind, int32_t k, int32_t K, int32_t b, uint64_t seed, uint64_t *out_words,
              uint64_t *out_keys, uint32_t *out_lsh, cudaStream_t st, void *queue = nullptr,
              const Choice *force = nullptr) {
     if (!ctx) return DM_EINVAL;
-    const Choice ch = force ? *force : choose(ctx, lsh, k, K, b);
+    const Choice ch = force ? *force : choose(ctx, kind, k, K, b);
     Plan pl;
-    int rc = plan_call(ctx, indptr, indices, weights, n_sets, lsh, k, K, b, seed, out_words, out_keys, out_lsh,
+    int rc = plan_call(ctx, indptr, indices, weights, n_sets, kind, k, K, b, seed, out_words, out_keys, out_lsh,
                        queue, ch, pl);
     if (rc || pl.p.n_sets == 0) return rc;
     return run_plan(ctx, pl, st);
@@ -405,10 +411,10 @@ int serve_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, co
                  int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *queue, int form, int large_nnz,
                  cudaStream_t st) {
     if (!ctx) return DM_EINVAL;
-    Choice c = choose(ctx, false, k, 0, 0);
+    Choice c = choose(ctx, dm::kSketch, k, 0, 0);
     c.form = form;
     if (large_nnz >= 0) c.large_nnz = large_nnz;
-    return run_sets(ctx, indptr, indices, weights, n_sets, false, k, 0, 0, seed, nullptr, out, nullptr, st, queue,
+    return run_sets(ctx, indptr, indices, weights, n_sets, dm::kSketch, k, 0, 0, seed, nullptr, out, nullptr, st, queue,
                     &c);
 }
 
@@ -436,7 +442,7 @@ namespace {
 int run_sketch(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
                int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_words,
                uint64_t *out_keys, cudaStream_t st, void *queue = nullptr) {
-    return run_sets(ctx, indptr, indices, weights, n_sets, false, k, 0, b, seed, out_words, out_keys, nullptr,
+    return run_sets(ctx, indptr, indices, weights, n_sets, dm::kSketch, k, 0, b, seed, out_words, out_keys, nullptr,
                     st, queue);
 }
 
@@ -507,7 +513,13 @@ int dm_sketch_bbit(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
 
 int dm_lsh(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
            int64_t n_sets, int32_t L, int32_t K, uint64_t seed, uint32_t *out, void *stream) {
-    return run_sets(ctx, indptr, indices, weights, n_sets, true, L, K, 0, seed, nullptr, nullptr, out,
+    return run_sets(ctx, indptr, indices, weights, n_sets, dm::kLsh, L, K, 0, seed, nullptr, nullptr, out,
+                    (cudaStream_t)stream);
+}
+
+int dm_bottomk(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+               int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream) {
+    return run_sets(ctx, indptr, indices, weights, n_sets, dm::kBottomK, k, 0, 0, seed, nullptr, out, nullptr,
                     (cudaStream_t)stream);
 }
 
@@ -595,11 +607,12 @@ int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
 int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
                 int64_t n_sets, int32_t lsh, int32_t k, int32_t K_or_b, uint64_t seed, int64_t max_sets,
                 dm_tuning *result, void *stream) {
-    if (!ctx || (lsh != 0 && lsh != 1)) return DM_EINVAL;
+    if (!ctx || lsh < 0 || lsh > 2) return DM_EINVAL;
+    const int kind = lsh;                        // 0 sketches, 1 (L, K) LSH, 2 bottom-k
     int rc = check_csr(indptr, indices, weights, n_sets);
     if (rc) return rc;
-    const bool is_lsh = lsh == 1;
-    const int K = is_lsh ? K_or_b : 0, b = is_lsh ? 0 : K_or_b;
+    const bool is_lsh = kind == dm::kLsh;
+    const int K = is_lsh ? K_or_b : 0, b = kind == dm::kSketch ? K_or_b : 0;
     if (n_sets == 0) return DM_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -621,7 +634,8 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
     const int64_t words = b > 0 ? ((int64_t)k * b + 63) / 64 : 0;
     const size_t out_bytes = is_lsh ? (size_t)n * k * 4 : (b > 0 ? (size_t)n * words * 8 : (size_t)n * k * 8);
     if (is_lsh ? (k < 1 || k > 1024 || K < 1 || K > 32)
-               : (k < 1 || k > 8192 || !(b == 0 || b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32)))
+               : kind == dm::kBottomK ? (k < 1 || k > 1024 || K_or_b != 0)
+                                      : (k < 1 || k > 8192 || !(b == 0 || b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32)))
         return DM_EINVAL;
     if ((rc = ensure_queue(ctx, n)) != DM_OK) return rc;
     if (ctx->budget && out_bytes + queue_bytes(ctx->queue_cap) + ctx->d_stage_bytes > ctx->budget) return DM_ENOMEM;
@@ -637,7 +651,7 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
         for (int r = 0; r < 4; ++r) {
             cudaError_t er = cudaEventRecord(ev[0], st);
             if (er != cudaSuccess) return cuda_fail(er);
-            int q = run_sets(ctx, indptr, indices, weights, n, is_lsh, k, K, b, seed,
+            int q = run_sets(ctx, indptr, indices, weights, n, kind, k, K, b, seed,
                              (!is_lsh && b > 0) ? (uint64_t *)d_out : nullptr,
                              (!is_lsh && b == 0) ? (uint64_t *)d_out : nullptr,
                              is_lsh ? (uint32_t *)d_out : nullptr, st, nullptr, &c);
@@ -681,9 +695,9 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
                                                : std::vector<float>{1.f, 1.25f, 1.5f, 2.f};
         try_set([](Choice &c, float v) { c.phi0 = v; }, phis);
         try_set([](Choice &c, int v) { c.wpb = v; }, std::vector<int>{2, 4, 8});
-        if (!is_lsh && max_nnz >= 256)
+        if (kind == dm::kSketch && max_nnz >= 256)
             try_set([](Choice &c, int v) { c.large_nnz = v; }, std::vector<int>{0, 256, 512, 1024, 2048, 4096, 8192});
-        if (!is_lsh)
+        if (kind == dm::kSketch)
             try_set([](Choice &c, float v) { c.large_work = v; },
                     std::vector<float>{0.f, 16384.f, 32768.f, 65536.f, 131072.f});
         try_set([](Choice &c, int v) { c.form = v; }, std::vector<int>{0, 2});
@@ -697,14 +711,14 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
     if ((rc = dm_sync_status(ctx, stream)) != DM_OK) return rc;
     bool found = false;
     for (auto &t : ctx->tuned)
-        if (t.lsh == is_lsh && t.k == k && t.K == K && t.b == b) {
+        if (t.kind == kind && t.k == k && t.K == K && t.b == b) {
             t.c = best;
             found = true;
         }
-    if (!found) ctx->tuned.push_back(TunedEntry{is_lsh, k, K, b, best});
+    if (!found) ctx->tuned.push_back(TunedEntry{kind, k, K, b, best});
     if (result) {
         result->form = best.form;
-        result->warps_per_block = best.wpb > 0 ? best.wpb : auto_warps(is_lsh, k, K);
+        result->warps_per_block = best.wpb > 0 ? best.wpb : auto_warps(kind, k, K);
         result->phi0_1024 = (int32_t)(best.phi0 * 1024.0f + 0.5f);
         result->large_nnz = best.large_nnz;
         result->large_work = (int32_t)best.large_work;

@@ -8,6 +8,9 @@
 
 namespace dm {
 
+// What a call computes: k minhash keys (Theorem 1), (L, K) LSH values, or a bottom-k sketch.
+enum Kind : int { kSketch = 0, kLsh = 1, kBottomK = 2 };
+
 struct SketchParams {
     const int64_t *indptr;
     const uint32_t *indices;
@@ -45,17 +48,17 @@ struct SketchParams {
 
 // Shared memory per warp of the fast (mode 0) or general (mode 1) kernel, and of its sink
 // (k buckets of minima, or L buckets of bottom-K candidates for LSH).
-size_t warp_bytes(bool lsh, int k, int K, int mode);
-size_t sink_bytes(bool lsh, int k, int K);
+size_t warp_bytes(int kind, int k, int K, int mode);
+size_t sink_bytes(int kind, int k, int K);
 
 // Resident blocks per SM of a kernel.
-int blocks_per_sm(bool lsh, int mode, bool bbit, int warps_per_block, size_t smem);
+int blocks_per_sm(int kind, int mode, bool bbit, int warps_per_block, size_t smem);
 
 cudaError_t upload_poisson_table(const uint32_t *T);
 
 // Plain form: zeroes the queue and work counters, then launches the fast kernel over all sets
 // (one warp each, in input order) and the general kernel over the sets it queued.
-cudaError_t launch_sets(const SketchParams &p, bool lsh, bool bbit, bool count, int grid_fast, int grid_general,
+cudaError_t launch_sets(const SketchParams &p, int kind, bool bbit, bool count, int grid_fast, int grid_general,
                         cudaStream_t st);
 
 // Batched form: classification (fast / general / large, costliest first by a Lemma 2 work
@@ -68,7 +71,7 @@ struct SideStream {
     cudaStream_t st;
     cudaEvent_t fork, join;
 };
-cudaError_t launch_batched(const SketchParams &p, bool lsh, bool bbit, bool count, int grid_fast,
+cudaError_t launch_batched(const SketchParams &p, int kind, bool bbit, bool count, int grid_fast,
                            int grid_general, int grid_large, cudaStream_t st, const SideStream *side = nullptr);
 
 // Shared memory of the large-set kernel's blocks.

@@ -83,7 +83,7 @@ extern "C" int dm_sketch_noalloc(const int64_t *indptr, const uint32_t *indices,
     cudaStream_t st = (cudaStream_t)stream;
 
     // warps per block: as many as fit 96 KB of shared memory, at most 8
-    const size_t wf = dm::warp_bytes(false, k, 0, 0), wg = dm::warp_bytes(false, k, 0, 1);
+    const size_t wf = dm::warp_bytes(dm::kSketch, k, 0, 0), wg = dm::warp_bytes(dm::kSketch, k, 0, 1);
     int wpb = (int)((96 * 1024) / (wf > wg ? wf : wg));
     wpb = wpb > 8 ? 8 : (wpb < 1 ? 1 : wpb);
 
@@ -100,19 +100,19 @@ extern "C" int dm_sketch_noalloc(const int64_t *indptr, const uint32_t *indices,
     p.warps_per_block = wpb;
     p.warp_bytes = (int32_t)wg;
     p.warp_bytes_fast = (int32_t)wf;
-    p.sink_bytes = (int32_t)dm::sink_bytes(false, k, 0);
+    p.sink_bytes = (int32_t)dm::sink_bytes(dm::kSketch, k, 0);
     p.queue = (int32_t *)ds->scratch;
     p.queue_count = (unsigned int *)(ds->scratch + kQueueBytes);     // count, then the work counters
     p.work_next = p.queue_count + 1;
     p.status = (int *)(ds->scratch + kQueueBytes + 16);
 
     const int64_t blocks = (n_sets + wpb - 1) / wpb;
-    const int64_t cap0 = (int64_t)ds->sm_count * dm::blocks_per_sm(false, 0, false, wpb, wf * wpb);
-    const int64_t cap1 = (int64_t)ds->sm_count * dm::blocks_per_sm(false, 1, false, wpb, wg * wpb);
+    const int64_t cap0 = (int64_t)ds->sm_count * dm::blocks_per_sm(dm::kSketch, 0, false, wpb, wf * wpb);
+    const int64_t cap1 = (int64_t)ds->sm_count * dm::blocks_per_sm(dm::kSketch, 1, false, wpb, wg * wpb);
     // the status word keeps the previous call's value: clear it (launch_sets clears the counters)
     cudaError_t e = cudaMemsetAsync(p.status, 0, sizeof(int), st);
     if (e == cudaSuccess)
-        e = dm::launch_sets(p, false, false, false, (int)(blocks < cap0 ? blocks : cap0),
+        e = dm::launch_sets(p, dm::kSketch, false, false, (int)(blocks < cap0 ? blocks : cap0),
                             (int)(blocks < cap1 ? blocks : cap1), st);
     // return the first error the kernels recorded (the call is synchronous)
     int status = 0;

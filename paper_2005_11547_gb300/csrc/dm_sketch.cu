@@ -237,6 +237,90 @@ struct LshSink {
     }
 };
 
+// The k smallest keys of a set's darts (Section 3, "Bottom-k minhash": t = k, phi raised until
+// at least k darts).  Candidates (keys below tau) are appended to a buffer of C slots; when a
+// batch of at most 32 puts brings it within 32 of full, the warp sorts it (bitonic) and keeps
+// the k smallest, tau becoming the k-th.  Band passes must not add a dart twice, so darts
+// below the previous limit are cut.
+__host__ __device__ inline uint32_t bottomk_cap(int k) {
+    uint32_t c = 64;
+    while (c < 2u * (uint32_t)k || c < (uint32_t)k + 32u) c <<= 1;
+    return c;
+}
+size_t bottomk_sink_bytes(int k) { return (size_t)bottomk_cap(k) * 8 + 16; }
+
+// Ascending bitonic sort of n (a power of two) keys in shared memory by one warp.
+__device__ void warp_bitonic_sort(uint64_t *a, uint32_t n, int lane) {
+    for (uint32_t size = 2; size <= n; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride; stride >>= 1) {
+            for (uint32_t i = (uint32_t)lane; i < n / 2; i += 32) {
+                const uint32_t lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1)), hi = lo + stride;
+                const uint64_t x = a[lo], y = a[hi];
+                if ((x > y) == ((lo & size) == 0)) {
+                    a[lo] = y;
+                    a[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+struct BottomKSink {
+    uint64_t *buf, *tau;
+    uint32_t *cnt;
+    uint32_t k, C;
+    static constexpr bool kLowerCut = true;
+    static constexpr bool kRing = true;
+
+    __device__ void bind(unsigned char *base, const SketchParams &p) {
+        k = (uint32_t)p.k;
+        C = bottomk_cap(p.k);
+        buf = reinterpret_cast<uint64_t *>(base);
+        tau = buf + C;
+        cnt = reinterpret_cast<uint32_t *>(tau + 1);
+    }
+    __device__ void reset(int lane) {
+        if (lane == 0) {
+            *cnt = 0;
+            *tau = ~0ull;
+        }
+        __syncwarp();
+    }
+    // Returns true when the buffer is within 32 of full: after_batch must compact.
+    __device__ __forceinline__ bool put(uint64_t qh, uint32_t code) {
+        const uint64_t key = ((uint64_t)code << 32) | (uint32_t)qh;
+        if (key >= *tau) return false;
+        const uint32_t pos = atomicAdd(cnt, 1u);          // < C: at most 32 puts per batch
+        buf[pos] = key;
+        return pos + 33 > C;
+    }
+    __device__ void compact(int lane) {
+        __syncwarp();
+        const uint32_t n = *cnt;
+        for (uint32_t j = n + (uint32_t)lane; j < C; j += 32) buf[j] = ~0ull;
+        __syncwarp();
+        warp_bitonic_sort(buf, C, lane);
+        if (lane == 0) {
+            *cnt = n < k ? n : k;
+            if (n >= k) *tau = buf[k - 1];
+        }
+        __syncwarp();
+    }
+    __device__ void after_batch(int lane, bool need) {
+        if (__any_sync(kFull, need)) compact(lane);
+    }
+    __device__ bool filled(int) { return *cnt >= k; }
+    __device__ void clear_to_error(int) {}
+    template <bool BBIT>
+    __device__ void finish(const SketchParams &p, int64_t set, bool err, int lane) {
+        compact(lane);
+        const uint32_t n = *cnt;
+        uint64_t *o = p.out_keys + set * (int64_t)k;
+        for (uint32_t j = (uint32_t)lane; j < k; j += 32) o[j] = (!err && j < n) ? buf[j] : ~0ull;
+    }
+};
+
 // ==========================================================================================
 // Fast path: passes with a rank limit theta <= 1.  Every region (nu, 0) is one column of rows
 // [rlo(nu), rhi(nu)) with rlo = floor(g_prev 2^nu) (0 on the first pass) and rhi =
@@ -1054,23 +1138,28 @@ static cudaError_t launch_mode(const SketchParams &p, bool bbit, bool count, int
     return count ? launch_t<Sink, false, true, MODE>(p, grid, st) : launch_t<Sink, false, false, MODE>(p, grid, st);
 }
 
-cudaError_t launch_sets(const SketchParams &p, bool lsh, bool bbit, bool count, int grid_fast, int grid_general,
+cudaError_t launch_sets(const SketchParams &p, int kind, bool bbit, bool count, int grid_fast, int grid_general,
                         cudaStream_t st) {
     // queue count and the two work counters are contiguous
     cudaError_t e = cudaMemsetAsync(p.queue_count, 0, 4 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    if (lsh) {
+    if (kind == kLsh) {
         if ((e = launch_mode<LshSink, 0>(p, false, count, grid_fast, st)) != cudaSuccess) return e;
         return launch_mode<LshSink, 1>(p, false, count, grid_general, st);
+    }
+    if (kind == kBottomK) {
+        if ((e = launch_mode<BottomKSink, 0>(p, false, count, grid_fast, st)) != cudaSuccess) return e;
+        return launch_mode<BottomKSink, 1>(p, false, count, grid_general, st);
     }
     if ((e = launch_mode<SketchSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
     return launch_mode<SketchSink, 1>(p, bbit, count, grid_general, st);
 }
 
-cudaError_t launch_batched(const SketchParams &p0, bool lsh, bool bbit, bool count, int grid_fast,
+cudaError_t launch_batched(const SketchParams &p0, int kind, bool bbit, bool count, int grid_fast,
                            int grid_general, int grid_large, cudaStream_t st, const SideStream *side) {
     SketchParams p = p0;
     p.sched = 2;
+    const bool lsh = kind != kSketch;           // bucket sinks: no block-per-set class
     if (lsh || grid_large <= 0) {
         p.large_nnz = 0;
         p.large_work = 0.f;
@@ -1100,9 +1189,13 @@ cudaError_t launch_batched(const SketchParams &p0, bool lsh, bool bbit, bool cou
             != cudaSuccess)
             return e;
     }
-    if (lsh) {
+    if (kind == kLsh) {
         if ((e = launch_mode<LshSink, 0>(p, false, count, grid_fast, st)) != cudaSuccess) return e;
         return launch_mode<LshSink, 1>(p, false, count, grid_general, st);
+    }
+    if (kind == kBottomK) {
+        if ((e = launch_mode<BottomKSink, 0>(p, false, count, grid_fast, st)) != cudaSuccess) return e;
+        return launch_mode<BottomKSink, 1>(p, false, count, grid_general, st);
     }
     if ((e = launch_mode<SketchSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
     if ((e = launch_mode<SketchSink, 1>(p, bbit, count, grid_general, st)) != cudaSuccess) return e;
@@ -1114,16 +1207,20 @@ cudaError_t launch_batched(const SketchParams &p0, bool lsh, bool bbit, bool cou
     return cudaSuccess;
 }
 
-size_t warp_bytes(bool lsh, int k, int K, int mode) {
-    const size_t sink = lsh ? lsh_sink_bytes(k, K) : sketch_sink_bytes(k);
-    return sink + (mode == 0 ? kFastPathBytes + (lsh ? kFastRingBytes : 0) : kGenPathBytes);
+size_t sink_bytes(int kind, int k, int K) {
+    return kind == kLsh ? lsh_sink_bytes(k, K) : (kind == kBottomK ? bottomk_sink_bytes(k) : sketch_sink_bytes(k));
 }
 
-size_t sink_bytes(bool lsh, int k, int K) { return lsh ? lsh_sink_bytes(k, K) : sketch_sink_bytes(k); }
+size_t warp_bytes(int kind, int k, int K, int mode) {
+    const size_t sink = (sink_bytes(kind, k, K) + 15) & ~(size_t)15;
+    return sink + (mode == 0 ? kFastPathBytes + (kind != kSketch ? kFastRingBytes : 0) : kGenPathBytes);
+}
 
-int blocks_per_sm(bool lsh, int mode, bool bbit, int warps_per_block, size_t smem) {
+int blocks_per_sm(int kind, int mode, bool bbit, int warps_per_block, size_t smem) {
     const void *fn;
-    if (lsh) fn = mode == 0 ? kernel_fn<LshSink, false, false, 0>() : kernel_fn<LshSink, false, false, 1>();
+    if (kind == kLsh) fn = mode == 0 ? kernel_fn<LshSink, false, false, 0>() : kernel_fn<LshSink, false, false, 1>();
+    else if (kind == kBottomK)
+        fn = mode == 0 ? kernel_fn<BottomKSink, false, false, 0>() : kernel_fn<BottomKSink, false, false, 1>();
     else if (mode == 0) fn = bbit ? kernel_fn<SketchSink, true, false, 0>() : kernel_fn<SketchSink, false, false, 0>();
     else fn = bbit ? kernel_fn<SketchSink, true, false, 1>() : kernel_fn<SketchSink, false, false, 1>();
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
