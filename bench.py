@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dm", "reference"], default="dm")
     ap.add_argument("--sets", type=int, default=None, help="prefix of the workload (profiling only)")
-    ap.add_argument("--workload", choices=["W1", "W2", "W3", "W4"], default="W1",
+    ap.add_argument("--workload", choices=["W1", "W2", "W3", "W4", "W1B"], default="W1",
                     help="W1 (default, the headline): k=256 keys + 1-bit words; W2: k=1024 heavy-tailed batch; "
-                         "W3: (L, K) = (64, 8) LSH; W4: serving loop on a Poisson request trace")
+                         "W3: (L, K) = (64, 8) LSH; W4: serving loop on a Poisson request trace; "
+                         "W1B: bottom-k sketches (k=256) of the W1 sets")
     ap.add_argument("--duration", type=float, default=20.0, help="W4: seconds of 50,000/s arrivals to replay")
     ap.add_argument("--form", choices=["batched", "plain", "persistent"], default="batched",
                     help="launch form (the plain form is the one-warp-per-set reference)")
@@ -245,14 +246,14 @@ def gpu_arm(args):
     props = torch.cuda.get_device_properties(local)
 
     wl = args.workload
-    if wl == "W1":
+    if wl in ("W1", "W1B"):
         b = workloads.workload1(args.sets or 1_000_000)
     elif wl == "W2":
         b = workloads.workload2(args.sets or 200_000)
     else:
         b = workloads.workload3(args.sets or 1_000_000)
     n = b.n_sets
-    kk = {"W1": K_SLOTS, "W2": 1024, "W3": 64}[wl]
+    kk = {"W1": K_SLOTS, "W2": 1024, "W3": 64, "W1B": K_SLOTS}[wl]
     words = (K_SLOTS * B_BITS + 63) // 64
     ip = torch.from_numpy(b.indptr).cuda()
     ix = torch.from_numpy(b.indices.view(np.int32)).cuda()
@@ -282,6 +283,8 @@ def gpu_arm(args):
             dmx.dm_sketch_bbit(c, ip, ix, w, K_SLOTS, B_BITS, SEED, out_words=outw, out_keys=keys, stream=stream)
         elif wl == "W2":
             dmx.dm_sketch(c, ip, ix, w, 1024, SEED, out=keys, stream=stream)
+        elif wl == "W1B":
+            dmx.dm_bottomk(c, ip, ix, w, K_SLOTS, SEED, out=keys, stream=stream)
         else:
             dmx.dm_lsh(c, ip, ix, w, 64, 8, SEED, out=keys, stream=stream)
 
@@ -292,6 +295,8 @@ def gpu_arm(args):
             tuning = dmx.dm_autotune(ctx, ip, ix, w, K_SLOTS, SEED, b=B_BITS, stream=stream)
         elif wl == "W2":
             tuning = dmx.dm_autotune(ctx, ip, ix, w, 1024, SEED, max_sets=n, stream=stream)
+        elif wl == "W1B":
+            tuning = dmx.dm_autotune(ctx, ip, ix, w, K_SLOTS, SEED, bottomk=True, stream=stream)
         else:
             tuning = dmx.dm_autotune(ctx, ip, ix, w, 64, SEED, lsh_K=8, stream=stream)
     if not args.no_graph:
@@ -414,7 +419,8 @@ def gpu_arm(args):
             "W2": "W2: 200,000 heavy-tailed sets (nnz log-normal median 100, sigma 1.5; ||x||_1 log-uniform "
                   "1e-3..1e3), d=2^24; k=1024 uint64 keys",
             "W3": "W3: 1,000,000 tf-idf-like sets (Zipf(1.1) tokens, nnz U{200..2000}), d=2^20; (L, K) = (64, 8) "
-                  "LSH uint32 values"}[wl]
+                  "LSH uint32 values",
+            "W1B": "W1 sets (1,000,000 x 256 elements, Exp(1) weights); bottom-k sketches, k=256 sorted uint64 keys"}[wl]
     if rank == 0:
         line = {
             "metric": METRIC if wl == "W1" else f"weighted sets/s ({wl})",
@@ -430,7 +436,7 @@ def gpu_arm(args):
             "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
             "plain_form": plain, "tuning": tuning,
             "gpu_launches": (2 if (tuning["form"] if tuning else form_id) != dmx.FORM_BATCHED
-                             else (5 if wl == "W3" else 6)) * args.steps,
+                             else (5 if wl in ("W3", "W1B") else 6)) * args.steps,
             "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)
