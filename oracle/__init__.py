@@ -267,6 +267,32 @@ def bottomk(indptr, indices, weights, k: int, seed: int, *, phi0: float = 1.0, t
     return (out, wk) if work else out
 
 
+def compare(a, c, k: int, bits: int = 0, mode: str = "pairs"):
+    """Similarity counts of sketches (Section 1.1, "Similarity estimation"): for each pair, the
+    number m of the k minhash slots whose values agree.  bits = 0: rows of k uint64 keys
+    (Eq. 1: E[m] = k J); bits = b in {1, 2, 4, 8, 16, 32}: rows of packed b-bit values, slot j at
+    bit (j b) mod 64 of word floor(j b / 64) (E[m] = k (J + (1 - J) 2^-b)).  mode "pairs": row i
+    of a with row i of c (uint32[n]); "cross": every row of a with every row of c
+    (uint32[n_a, n_c]).  Written out slot by slot."""
+    a = np.asarray(a, dtype=np.uint64)
+    c = np.asarray(c, dtype=np.uint64)
+
+    def values(rows):
+        if bits == 0:
+            return rows.reshape(len(rows), k)
+        out = np.zeros((len(rows), k), dtype=np.uint64)
+        mask = np.uint64((1 << bits) - 1)
+        for j in range(k):
+            word, off = (j * bits) // 64, (j * bits) % 64
+            out[:, j] = (rows[:, word] >> np.uint64(off)) & mask
+        return out
+
+    va, vc = values(a), values(c)
+    if mode == "pairs":
+        return (va == vc).sum(axis=1).astype(np.uint32)
+    return np.stack([(va[i][None, :] == vc).sum(axis=1) for i in range(len(va))]).astype(np.uint32)
+
+
 DART_DTYPE = np.dtype({
     "names": ["pos", "i", "nu", "rho", "w", "r", "j", "u", "v", "code", "q"],
     "formats": [np.int64, np.uint32, np.int32, np.int32, np.uint64, np.uint64, np.int32,
