@@ -105,6 +105,18 @@ int dm_lsh(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const fl
 int dm_bottomk(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
                int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream);
 
+/* Similarity counts of sketches (Section 1.1, "Similarity estimation"): for each pair of rows,
+ * the number m of the k slots whose values agree.  bits = 0: rows of k uint64 keys from dm_sketch
+ * (E[m] = k J, Eq. 1, so m / k estimates the weighted Jaccard similarity J); bits = b in
+ * {1, 2, 4, 8, 16, 32}: rows of W = ceil(k b / 64) packed words from dm_sketch_bbit
+ * (E[m] = k (J + (1 - J) 2^-b), so J is estimated by (m / k - 2^-b) / (1 - 2^-b)).  Both batches
+ * must come from the same k, b and seed.  mode 0 (pairs): n_a == n_c, out[i] compares row i of a
+ * with row i of c (uint32[n_a]); mode 1 (cross): out[i * n_c + j] compares row i of a with row j
+ * of c (uint32[n_a * n_c]; n_a <= 2,097,120, and W <= 64 for b-bit rows).  Device pointers,
+ * asynchronous on `stream`. */
+int dm_compare(dm_ctx *ctx, const uint64_t *a, const uint64_t *c, int64_t n_a, int64_t n_c, int32_t k,
+               int32_t bits, int32_t mode, uint32_t *out, void *stream);
+
 /* dm_sketch / dm_sketch_bbit with HOST arrays: indptr, indices, weights, out_keys and
  * out_words are host pointers (page-locked memory gives full copy speed).  b = 0 computes keys
  * only (out_keys required, out_words ignored); b in {1, 2, 4, 8, 16, 32} also writes the b-bit

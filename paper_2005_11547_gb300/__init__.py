@@ -19,7 +19,7 @@ import threading
 from .build import LIB, build
 
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
-           "dm_sketch_host", "dm_bottomk", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
+           "dm_sketch_host", "dm_bottomk", "dm_compare", "estimate_jaccard", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
            "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
            "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "OPT_LARGE_WORK", "FORM_BATCHED",
            "FORM_PLAIN", "FORM_PERSISTENT", "dm_autotune", "Tuning", "Server", "EAGAIN"]
@@ -57,6 +57,7 @@ def load(path: str | None = None):
             "dm_sketch_bbit": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_lsh": ([P, P, P, P, i64, i32, i32, u64, P, P], ctypes.c_int),
             "dm_bottomk": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
+            "dm_compare": ([P, P, P, i64, i64, i32, i32, i32, P, P], ctypes.c_int),
             "dm_sketch_host": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_sync_status": ([P, P], ctypes.c_int),
             "dm_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -196,6 +197,31 @@ def dm_bottomk(ctx: Context, indptr, indices, weights, k: int, seed: int, out=No
     _check(load().dm_bottomk(ctx.handle, ip, ix, w, n, int(k), int(seed) & (2**64 - 1),
                              _dev_ptr(out, "uint64", "out"), _stream(stream)), "dm_bottomk")
     return out
+
+
+def dm_compare(ctx: Context, a, c, k: int, bits: int = 0, cross: bool = False, out=None, stream=None):
+    """Agreeing slots per pair of sketch rows (uint32 as int32 tensor): rows of a with the same
+    rows of c, or (cross=True) every row of a with every row of c.  a, c: int64 tensors holding
+    uint64 keys [n, k] (bits = 0) or packed b-bit words [n, ceil(k b / 64)]."""
+    import torch
+    na, nc = a.shape[0], c.shape[0]
+    if not cross and na != nc:
+        raise ValueError("pairs need the same number of rows")
+    if out is None:
+        out = torch.empty((na, nc) if cross else (na,), dtype=torch.int32, device=a.device)
+    _check(load().dm_compare(ctx.handle, _dev_ptr(a, "uint64", "a"), _dev_ptr(c, "uint64", "c"), na, nc, int(k),
+                             int(bits), 1 if cross else 0, _dev_ptr(out, "uint32", "out"), _stream(stream)),
+           "dm_compare")
+    return out
+
+
+def estimate_jaccard(matches, k: int, bits: int = 0):
+    """J estimate from agreeing-slot counts: m / k for keys, (m / k - 2^-b) / (1 - 2^-b) for b bits."""
+    p = matches / float(k)
+    if bits == 0:
+        return p
+    r = 2.0 ** -bits
+    return (p - r) / (1.0 - r)
 
 
 def dm_sketch_host(ctx: Context, indptr, indices, weights, k: int, seed: int, out_keys=None, b: int = 0,

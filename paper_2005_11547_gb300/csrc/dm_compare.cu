@@ -1,0 +1,159 @@
+// Similarity estimation from sketches (Section 1.1, "Similarity estimation"): the number of the k
+// minhash slots whose values agree between two sets.  For uint64 keys the expected count is k J
+// (Eq. 1); for b-bit values it is k (J + (1 - J) 2^-b).  Row-aligned pairs stream both batches
+// once (HBM-bound); the cross form compares every row of one batch with every row of another,
+// staging tiles of both in shared memory.
+#include <cstdint>
+
+#include "dm_internal.h"
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Equal b-bit fields among the first f fields of x = a ^ c (a field is equal iff it is zero).
+__device__ __forceinline__ uint32_t equal_fields(uint64_t x, int bits, uint32_t f) {
+    // fold each field onto its lowest bit, then count the fields that are nonzero
+    for (int s = 1; s < bits; s <<= 1) x |= x >> s;
+    uint64_t low = 0;                            // bit 0 of every field
+    switch (bits) {
+        case 1: low = ~0ull; break;
+        case 2: low = 0x5555555555555555ull; break;
+        case 4: low = 0x1111111111111111ull; break;
+        case 8: low = 0x0101010101010101ull; break;
+        case 16: low = 0x0001000100010001ull; break;
+        default: low = 0x0000000100000001ull; break;
+    }
+    const uint32_t per = 64u / (uint32_t)bits;
+    if (f < per) low &= (1ull << (f * (uint32_t)bits)) - 1;   // fields past k are not counted
+    return f - (uint32_t)__popcll(x & low);
+}
+
+// Row-aligned key pairs: a warp per pair, lanes striding the k slots.
+__global__ void __launch_bounds__(256) pairs_keys(const uint64_t *a, const uint64_t *c, int64_t n, int k,
+                                                  uint32_t *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+        const uint64_t *ra = a + i * k, *rc = c + i * k;
+        uint32_t m = 0;
+        for (int j = lane; j < k; j += 32) m += ra[j] == rc[j];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m += __shfl_xor_sync(kFull, m, o);
+        if (lane == 0) out[i] = m;
+    }
+}
+
+// Row-aligned b-bit pairs: a thread per pair over its W words.
+__global__ void __launch_bounds__(256) pairs_words(const uint64_t *a, const uint64_t *c, int64_t n, int k, int bits,
+                                                   int W, uint32_t *out) {
+    const uint32_t per = 64u / (uint32_t)bits;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t m = 0;
+        for (int w = 0; w < W; ++w) {
+            const uint32_t left = (uint32_t)k - (uint32_t)w * per;
+            m += equal_fields(a[i * W + w] ^ c[i * W + w], bits, left < per ? left : per);
+        }
+        out[i] = m;
+    }
+}
+
+// Cross form, keys: a block computes a 32 x 32 tile of pairs (8 per thread), the k slots taken
+// in chunks of 32 staged in shared memory.
+constexpr int kTile = 32, kChunk = 32;
+
+__global__ void __launch_bounds__(128) cross_keys(const uint64_t *a, const uint64_t *c, int64_t na, int64_t nc, int k,
+                                                  uint32_t *out) {
+    __shared__ uint64_t sa[kTile][kChunk + 1], sc[kTile][kChunk + 1];
+    const int64_t i0 = (int64_t)blockIdx.y * kTile, j0 = (int64_t)blockIdx.x * kTile;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;       // ty: 0..3, rows ty, ty+4, ...
+    uint32_t m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q0 = 0; q0 < k; q0 += kChunk) {
+        for (int r = ty; r < kTile; r += 4) {
+            const int q = q0 + tx;
+            sa[r][tx] = (i0 + r < na && q < k) ? a[(i0 + r) * k + q] : 0ull;
+            sc[r][tx] = (j0 + r < nc && q < k) ? c[(j0 + r) * k + q] : 1ull;   // never equal past k
+        }
+        __syncthreads();
+        const int qn = k - q0 < kChunk ? k - q0 : kChunk;
+        for (int q = 0; q < qn; ++q) {
+            const uint64_t vc = sc[tx][q];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) m[s] += sa[ty + 4 * s][q] == vc;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int64_t i = i0 + ty + 4 * s, j = j0 + tx;
+        if (i < na && j < nc) out[i * nc + j] = m[s];
+    }
+}
+
+// Cross form, b-bit words: a thread per pair, rows of both sides staged per 32 x 32 tile.
+constexpr int kMaxWords = 64;                   // k b / 64 <= 64 words per row in this form
+
+__global__ void __launch_bounds__(128) cross_words(const uint64_t *a, const uint64_t *c, int64_t na, int64_t nc, int k,
+                                                   int bits, int W, uint32_t *out) {
+    extern __shared__ uint64_t sm[];
+    uint64_t *sa = sm, *sc = sm + (size_t)kTile * W;
+    const int64_t i0 = (int64_t)blockIdx.y * kTile, j0 = (int64_t)blockIdx.x * kTile;
+    for (int e = threadIdx.x; e < kTile * W; e += blockDim.x) {
+        const int r = e / W, w = e % W;
+        sa[e] = i0 + r < na ? a[(i0 + r) * W + w] : 0ull;
+        sc[e] = j0 + r < nc ? c[(j0 + r) * W + w] : 0ull;
+    }
+    __syncthreads();
+    const uint32_t per = 64u / (uint32_t)bits;
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+        const int r = e / kTile, s = e % kTile;
+        const int64_t i = i0 + r, j = j0 + s;
+        if (i >= na || j >= nc) continue;
+        uint32_t m = 0;
+        for (int w = 0; w < W; ++w) {
+            const uint32_t left = (uint32_t)k - (uint32_t)w * per;
+            m += equal_fields(sa[r * W + w] ^ sc[s * W + w], bits, left < per ? left : per);
+        }
+        out[i * nc + j] = m;
+    }
+}
+
+}  // namespace
+
+extern "C" int dm_compare(dm_ctx *ctx, const uint64_t *a, const uint64_t *c, int64_t n_a, int64_t n_c, int32_t k,
+                          int32_t bits, int32_t mode, uint32_t *out, void *stream) {
+    if (!ctx || n_a < 0 || n_c < 0 || k < 1 || k > 8192 || (mode != 0 && mode != 1)) return DM_EINVAL;
+    if (!(bits == 0 || bits == 1 || bits == 2 || bits == 4 || bits == 8 || bits == 16 || bits == 32)) return DM_EINVAL;
+    if (mode == 0 && n_a != n_c) return DM_EINVAL;
+    const int64_t pairs = mode == 0 ? n_a : n_a * n_c;
+    if (pairs == 0) return DM_OK;
+    if (!a || !c || !out) return DM_EINVAL;
+    const int W = bits ? (int)(((int64_t)k * bits + 63) / 64) : 0;
+    if (mode == 1 && bits && W > kMaxWords) return DM_EINVAL;
+    if (mode == 1 && (n_a > ((int64_t)65535 * kTile) || (n_c + kTile - 1) / kTile > 0x7FFFFFFF)) return DM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DM_ECUDA;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (mode == 0) {
+        if (bits == 0) {
+            const int64_t blocks = (n_a + 7) / 8;
+            pairs_keys<<<(int)(blocks < 64LL * sms ? blocks : 64LL * sms), 256, 0, st>>>(a, c, n_a, k, out);
+        } else {
+            const int64_t blocks = (n_a + 255) / 256;
+            pairs_words<<<(int)(blocks < 64LL * sms ? blocks : 64LL * sms), 256, 0, st>>>(a, c, n_a, k, bits, W, out);
+        }
+    } else {
+        const dim3 grid((unsigned)((n_c + kTile - 1) / kTile), (unsigned)((n_a + kTile - 1) / kTile));
+        if (bits == 0) {
+            cross_keys<<<grid, 128, 0, st>>>(a, c, n_a, n_c, k, out);
+        } else {
+            const size_t smem = (size_t)2 * kTile * W * sizeof(uint64_t);
+            cross_words<<<grid, 128, smem, st>>>(a, c, n_a, n_c, k, bits, W, out);
+        }
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DM_OK : DM_ECUDA;
+}
