@@ -48,10 +48,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dm", "reference"], default="dm")
     ap.add_argument("--sets", type=int, default=None, help="prefix of the workload (profiling only)")
-    ap.add_argument("--workload", choices=["W1", "W2", "W3", "W4", "W1B"], default="W1",
+    ap.add_argument("--workload", choices=["W1", "W2", "W3", "W4", "W1B", "CMP"], default="W1",
                     help="W1 (default, the headline): k=256 keys + 1-bit words; W2: k=1024 heavy-tailed batch; "
                          "W3: (L, K) = (64, 8) LSH; W4: serving loop on a Poisson request trace; "
-                         "W1B: bottom-k sketches (k=256) of the W1 sets")
+                         "W1B: bottom-k sketches (k=256) of the W1 sets; CMP: similarity counts of sketch pairs")
     ap.add_argument("--duration", type=float, default=20.0, help="W4: seconds of 50,000/s arrivals to replay")
     ap.add_argument("--form", choices=["batched", "plain", "persistent"], default="batched",
                     help="launch form (the plain form is the one-warp-per-set reference)")
@@ -552,12 +552,100 @@ def serve_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------
+# CMP: similarity counts of sketches (dm_compare)
+# ------------------------------------------------------------------------------------------
+def compare_arm(args):
+    """Row-aligned pairs of k = 256 key sketches (1,000,000 pairs: 4.1 GB read per step, HBM
+    bound), plus the cross form of 2,048 query rows against 131,072 rows (k = 256 keys and 1-bit
+    words).  Sketch values are random: the counts do not depend on where the keys came from."""
+    import numpy as np
+    import torch
+
+    import paper_2005_11547_gb300 as dmx
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, True)
+    dmx.build()
+    dmx.load()
+    n, k = args.sets or 1_000_000, 256
+    g = torch.Generator(device="cuda").manual_seed(5)
+    a = torch.randint(-2 ** 62, 2 ** 62, (n, k), device="cuda", dtype=torch.int64, generator=g)
+    c = a.clone()
+    flip = torch.rand((n, k), device="cuda", generator=g) < 0.5
+    c[flip] ^= 1 << 40
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx = dmx.dm_create(local)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        dmx.dm_compare(ctx, a, c, k, out=out, stream=stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(dist, True)
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        dmx.dm_compare(ctx, a, c, k, out=out, stream=stream)
+    ev[1].record(stream)
+    barrier(dist, True)
+    clocks = sampler.stop()
+    t = max_over_ranks(dist, ev[0].elapsed_time(ev[1]) / 1e3, True)
+    per = t / args.steps
+    bytes_launch = 2 * n * k * 8 + n * 4
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    value = sum_over_ranks(dist, float(n * args.steps), True) / t
+    # cross form
+    qa, qc = a[:2048].contiguous(), c[:131072].contiguous()
+    cross = torch.empty((2048, 131072), dtype=torch.int32, device="cuda")
+    dmx.dm_compare(ctx, qa, qc, k, cross=True, out=cross, stream=stream)
+    e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e2[0].record(stream)
+    for _ in range(3):
+        dmx.dm_compare(ctx, qa, qc, k, cross=True, out=cross, stream=stream)
+    e2[1].record(stream)
+    torch.cuda.synchronize()
+    cross_s = e2[0].elapsed_time(e2[1]) / 3e3
+    wa = torch.randint(-2 ** 62, 2 ** 62, (2048, 4), device="cuda", dtype=torch.int64, generator=g)
+    wc = torch.randint(-2 ** 62, 2 ** 62, (131072, 4), device="cuda", dtype=torch.int64, generator=g)
+    dmx.dm_compare(ctx, wa, wc, k, bits=1, cross=True, out=cross, stream=stream)
+    e2[0].record(stream)
+    for _ in range(3):
+        dmx.dm_compare(ctx, wa, wc, k, bits=1, cross=True, out=cross, stream=stream)
+    e2[1].record(stream)
+    torch.cuda.synchronize()
+    cross1_s = e2[0].elapsed_time(e2[1]) / 3e3
+    ctx.close()
+    if rank == 0:
+        line = {
+            "metric": "sketch pairs compared/s (k=256 uint64 keys, row-aligned pairs)", "value": value,
+            "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"CMP: {n} pairs of k=256 uint64 key rows (random, half the slots agreeing)",
+                       "l2": "4.1 GB read per step, > 129 MB L2: no flush needed"},
+            "roofline": {"bound": "hbm", "achieved": bytes_launch / per / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": bytes_launch / per / 1e9 / hbm, "traffic": None,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"},
+            "cross": {"keys_pairs_per_s": 2048 * 131072 / cross_s, "one_bit_pairs_per_s": 2048 * 131072 / cross1_s,
+                      "shape": "2,048 x 131,072 rows, k = 256"},
+            "cpu_baseline": None, "e2e": None, "clocks": clocks, "gpu_launches": args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
     elif args.workload == "W4":
         serve_arm(args)
+    elif args.workload == "CMP":
+        compare_arm(args)
     else:
         gpu_arm(args)
 
