@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import ctypes
 import decimal
+import math
 import os
 import subprocess
 import threading
@@ -79,6 +80,8 @@ def _load():
         lib.dmo_sketch_bbit.restype = ctypes.c_int
         lib.dmo_lsh.argtypes = [P, P, P, i64, i32, i32, u64, P, dbl, P, P]
         lib.dmo_lsh.restype = ctypes.c_int
+        lib.dmo_lsh_scaled.argtypes = [P, P, P, i64, i32, i32, u64, P, dbl, P, P, P]
+        lib.dmo_lsh_scaled.restype = ctypes.c_int
         lib.dmo_bottomk.argtypes = [P, P, P, i64, i32, u64, P, dbl, P, P]
         lib.dmo_bottomk.restype = ctypes.c_int
         lib.dmo_darthash.argtypes = [P, P, i64, i64, u64, P, flt, P, i64, P]
@@ -227,23 +230,45 @@ def sketch_bbit(indptr, indices, weights, k: int, b: int, seed: int, *, threads:
 
 
 def lsh(indptr, indices, weights, L: int, K: int, seed: int, *, phi0: float = 1.0,
-        threads: int = 1, work: bool = False):
-    """(L, K) LSH values uint32[n, L] (t = L K, L buckets, hash of the sorted bottom-K keys)."""
+        threads: int = 1, work: bool = False, scale=None):
+    """(L, K) LSH values uint32[n, L] (t = L K, L buckets, hash of the sorted bottom-K keys).
+    scale (int32[n], optional): set s's weights count as x_i 2^scale[s] (Section 3's weight-class
+    normalisation, exact)."""
     lib = _load()
     indptr, indices, weights = _csr(indptr, indices, weights)
     n = len(indptr) - 1
     out = np.empty((n, L), dtype=np.uint32)
     wk = np.zeros((n, 4), dtype=np.int64)
     T = _table()
+    sc = None if scale is None else np.ascontiguousarray(scale, dtype=np.int32)
 
     def fn(a, b):
         ip = indptr[a:b + 1]
-        return lib.dmo_lsh(_ptr(ip), _ptr(indices), _ptr(weights), b - a, L, K, seed & (2**64 - 1),
-                           _ptr(T), float(phi0), ctypes.c_void_p(out.ctypes.data + a * L * 4),
-                           ctypes.c_void_p(wk.ctypes.data + a * 32))
+        return lib.dmo_lsh_scaled(_ptr(ip), _ptr(indices), _ptr(weights), b - a, L, K, seed & (2**64 - 1),
+                                  _ptr(T), float(phi0), None if sc is None else ctypes.c_void_p(sc.ctypes.data + a * 4),
+                                  ctypes.c_void_p(out.ctypes.data + a * L * 4),
+                                  ctypes.c_void_p(wk.ctypes.data + a * 32))
 
     _run_chunked(n, threads, fn)
     return (out, wk) if work else out
+
+
+def weight_class(indptr, weights):
+    """Weight class of each set (Section 3): c = floor(log2 ||x||_1) with ||x||_1 summed in
+    double; sets with no positive weight get 0.  Normalising a class to ||x||_1 in [1, 2) means
+    scale = -c."""
+    indptr = np.asarray(indptr, dtype=np.int64)
+    w = np.asarray(weights, dtype=np.float64)
+    out = np.zeros(len(indptr) - 1, dtype=np.int32)
+    for s in range(len(out)):
+        l1 = float(w[indptr[s]:indptr[s + 1]].sum())
+        if l1 > 0:
+            out[s] = math.floor(math.log2(l1))
+            while 2.0 ** out[s] > l1:
+                out[s] -= 1
+            while 2.0 ** (out[s] + 1) <= l1:
+                out[s] += 1
+    return out
 
 
 def bottomk(indptr, indices, weights, k: int, seed: int, *, phi0: float = 1.0, threads: int = 1,

@@ -147,13 +147,16 @@ typedef void (*dart_sink)(void *ctx, const dmo_dart *d);
 
 typedef struct { int64_t areas, darts, kept; } dmo_work;
 
-static int darthash(const uint32_t *idx, const float *wt, int64_t nnz, int64_t t, uint64_t sigma,
-                    const uint32_t *T, float theta, dart_sink sink, void *ctx, dmo_work *work) {
+/* Algorithm 1.  scale: every weight counts as x_i 2^scale (the exact power-of-two normalisation
+   of a weight class, Section 3); 0 for the plain method. */
+static int darthash_s(const uint32_t *idx, const float *wt, int64_t nnz, int64_t t, uint64_t sigma,
+                      const uint32_t *T, float theta, int scale, dart_sink sink, void *ctx, dmo_work *work) {
     dy th = dy_of_float(theta);
     for (int64_t p = 0; p < nnz; p++) {
         float xi = wt[p];
         if (!(xi > 0.0f)) continue;                               /* i in {j | x_j > 0} */
         dy xf = dy_of_float(xi);
+        xf.e += scale;                                            /* x_i 2^scale, exact */
         dy y = { (u128)t * xf.m, xf.e };                          /* t * x_i, exact */
         uint64_t e = element_key(sigma, idx[p]);
         /* nu = 0 .. floor(log2(1 + t x_i)):  continue while 2^nu - 1 <= t x_i */
@@ -203,6 +206,11 @@ static int darthash(const uint32_t *idx, const float *wt, int64_t nnz, int64_t t
         }
     }
     return DMO_OK;
+}
+
+static int darthash(const uint32_t *idx, const float *wt, int64_t nnz, int64_t t, uint64_t sigma,
+                    const uint32_t *T, float theta, dart_sink sink, void *ctx, dmo_work *work) {
+    return darthash_s(idx, wt, nnz, t, sigma, T, theta, 0, sink, ctx, work);
 }
 
 static uint32_t fastrange32(uint32_t h, uint32_t n) { return (uint32_t)(((uint64_t)h * n) >> 32); }
@@ -334,9 +342,11 @@ static int cmp_u64(const void *a, const void *b) {
     return (x > y) - (x < y);
 }
 
-int dmo_lsh(const int64_t *indptr, const uint32_t *indices, const float *weights, int64_t n_sets,
-            int32_t L, int32_t K, uint64_t seed, const uint32_t *T, double phi0,
-            uint32_t *out, int64_t *work) {
+/* (L, K) LSH; scale (may be NULL): set s's weights count as x_i 2^scale[s] (weight classes
+   normalised to ||x||_1 in [1, 2), Section 3). */
+int dmo_lsh_scaled(const int64_t *indptr, const uint32_t *indices, const float *weights, int64_t n_sets,
+                   int32_t L, int32_t K, uint64_t seed, const uint32_t *T, double phi0, const int32_t *scale,
+                   uint32_t *out, int64_t *work) {
     if (L < 1 || K < 1) return DMO_EINVAL;
     int64_t t = (int64_t)L * K;
     uint64_t sigma = seed_key(seed);
@@ -356,12 +366,13 @@ int dmo_lsh(const int64_t *indptr, const uint32_t *indices, const float *weights
         dmo_work W = {0, 0, 0};
         int64_t passes = 0;
         if (!rc && l1 > 0.0) {
+            const int sc = scale ? scale[s] : 0;
             for (double phi = phi0; ; phi *= 2.0) {
                 if (phi > DMO_PHI_MAX) { rc = DMO_EOVERFLOW; break; }
-                float theta = (float)(phi / l1);
+                float theta = (float)(phi / ldexp(l1, sc));
                 if (!(theta > 0.0f) || isinf(theta)) { rc = DMO_ERANGE; break; }
                 c.n = 0;
-                rc = darthash(idx, wt, nnz, t, sigma, T, theta, lsh_sink, &c, &W);
+                rc = darthash_s(idx, wt, nnz, t, sigma, T, theta, sc, lsh_sink, &c, &W);
                 passes++;
                 if (c.oom) rc = DMO_ENOMEM;
                 if (rc) break;
@@ -391,6 +402,12 @@ int dmo_lsh(const int64_t *indptr, const uint32_t *indices, const float *weights
     }
     free(c.key); free(c.bucket); free(tmp); free(cnt);
     return status;
+}
+
+int dmo_lsh(const int64_t *indptr, const uint32_t *indices, const float *weights, int64_t n_sets,
+            int32_t L, int32_t K, uint64_t seed, const uint32_t *T, double phi0,
+            uint32_t *out, int64_t *work) {
+    return dmo_lsh_scaled(indptr, indices, weights, n_sets, L, K, seed, T, phi0, NULL, out, work);
 }
 
 /* ------------------------------------------------------------------------------------ */
