@@ -94,6 +94,22 @@ int dm_sketch_bbit(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
 int dm_lsh(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
            int64_t n_sets, int32_t L, int32_t K, uint64_t seed, uint32_t *out, void *stream);
 
+/* dm_lsh on weight-class-normalised data (Section 3: split the data into classes
+ * ||x||_1 in [2^c, 2^(c+1)) and normalise each class to ||x||_1 in [1, 2), which bounds the work of
+ * sets with very large or very small norms).  scale_exp: device int32[n_sets]; set s's weights
+ * count as x_i 2^scale_exp[s], exactly (the scaling acts on the exponent, so no weight is rounded).
+ * Normalising class c means scale_exp = -c; a query probes a neighbouring class c' by hashing with
+ * -c'.  The same (row, scale) always gives the same values; scale 0 equals dm_lsh. */
+int dm_lsh_scaled(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+                  int64_t n_sets, int32_t L, int32_t K, uint64_t seed, const int32_t *scale_exp, uint32_t *out,
+                  void *stream);
+
+/* Weight class of each set: out[s] = floor(log2 ||x||_1) with ||x||_1 summed in fp32 by the GPU
+ * (so a norm within rounding of a power of two may land in either neighbouring class); 0 for a
+ * set without a positive weight.  Device int32 out[n_sets]. */
+int dm_weight_classes(dm_ctx *ctx, const int64_t *indptr, const float *weights, int64_t n_sets, int32_t *out,
+                      void *stream);
+
 /* Bottom-k weighted sketch (Section 3, "Bottom-k minhash and fast approximate near neighbor
  * search": with t = k, raise phi until DartHash returns at least k darts and keep them sorted by
  * rank).  out: uint64[n_sets * k]; row s holds the k smallest keys of set s's darts (the same

@@ -19,7 +19,7 @@ import threading
 from .build import LIB, build
 
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
-           "dm_sketch_host", "dm_bottomk", "dm_compare", "estimate_jaccard", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
+           "dm_sketch_host", "dm_bottomk", "dm_compare", "dm_lsh_scaled", "dm_weight_classes", "estimate_jaccard", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
            "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
            "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "OPT_LARGE_WORK", "FORM_BATCHED",
            "FORM_PLAIN", "FORM_PERSISTENT", "dm_autotune", "Tuning", "Server", "EAGAIN"]
@@ -58,6 +58,8 @@ def load(path: str | None = None):
             "dm_lsh": ([P, P, P, P, i64, i32, i32, u64, P, P], ctypes.c_int),
             "dm_bottomk": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
             "dm_compare": ([P, P, P, i64, i64, i32, i32, i32, P, P], ctypes.c_int),
+            "dm_lsh_scaled": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
+            "dm_weight_classes": ([P, P, P, i64, P, P], ctypes.c_int),
             "dm_sketch_host": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_sync_status": ([P, P], ctypes.c_int),
             "dm_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -102,7 +104,8 @@ def _dev_ptr(t, dtype_name, what):
         raise TypeError(f"{what} must be a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError(f"{what} must be contiguous")
-    want = {"int64": (torch.int64,), "uint32": (torch.int32, torch.uint32), "float32": (torch.float32,),
+    want = {"int64": (torch.int64,), "int32": (torch.int32,), "uint32": (torch.int32, torch.uint32),
+            "float32": (torch.float32,),
             "uint64": (torch.int64, torch.uint64)}[dtype_name]
     if t.dtype not in want:
         raise TypeError(f"{what} must be {dtype_name} (got {t.dtype})")
@@ -182,6 +185,33 @@ def dm_lsh(ctx: Context, indptr, indices, weights, L: int, K: int, seed: int, ou
         out = torch.empty((n, L), dtype=torch.int32, device=indptr.device)
     _check(load().dm_lsh(ctx.handle, ip, ix, w, n, int(L), int(K), int(seed) & (2**64 - 1),
                          _dev_ptr(out, "uint32", "out"), _stream(stream)), "dm_lsh")
+    return out
+
+
+def dm_lsh_scaled(ctx: Context, indptr, indices, weights, L: int, K: int, seed: int, scale_exp, out=None,
+                  stream=None):
+    """dm_lsh with set s's weights counted as x_i 2^scale_exp[s] (int32 CUDA tensor)."""
+    import torch
+    n, ip, ix, w = _csr_ptrs(indptr, indices, weights)
+    if out is None:
+        out = torch.empty((n, L), dtype=torch.int32, device=indptr.device)
+    if scale_exp.numel() != n:
+        raise ValueError("one scale per set")
+    _check(load().dm_lsh_scaled(ctx.handle, ip, ix, w, n, int(L), int(K), int(seed) & (2**64 - 1),
+                                _dev_ptr(scale_exp, "int32", "scale_exp"), _dev_ptr(out, "uint32", "out"),
+                                _stream(stream)), "dm_lsh_scaled")
+    return out
+
+
+def dm_weight_classes(ctx: Context, indptr, weights, out=None, stream=None):
+    """int32 weight class floor(log2 ||x||_1) of each set (fp32 norm)."""
+    import torch
+    n = indptr.numel() - 1
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=indptr.device)
+    _check(load().dm_weight_classes(ctx.handle, _dev_ptr(indptr, "int64", "indptr"),
+                                    _dev_ptr(weights, "float32", "weights"), n, _dev_ptr(out, "int32", "out"),
+                                    _stream(stream)), "dm_weight_classes")
     return out
 
 

@@ -212,7 +212,8 @@ Choice choose(const dm_ctx *ctx, int kind, int k, int K, int b) {
 // nothing to launch.
 int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
               int64_t n_sets, int kind, int32_t k, int32_t K, int32_t b, uint64_t seed, uint64_t *out_words,
-              uint64_t *out_keys, uint32_t *out_lsh, void *queue, const Choice &ch, Plan &pl) {
+              uint64_t *out_keys, uint32_t *out_lsh, void *queue, const Choice &ch, Plan &pl,
+              const int32_t *scale = nullptr) {
     const bool lsh = kind == dm::kLsh;
     std::memset(&pl, 0, sizeof(pl));
     if (!ctx) return DM_EINVAL;
@@ -255,6 +256,7 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
     p.t = (uint32_t)t;
     p.sigma = dm::mix64(seed ^ dm::kSeedSalt);
     p.phi0 = ch.phi0;
+    p.scale = scale;
     p.b = bbit ? b : 0;
     p.words = bbit ? (int32_t)(((int64_t)k * b + 63) / 64) : 0;
     p.out_keys = out_keys;
@@ -392,12 +394,12 @@ int run_plan(dm_ctx *ctx, const Plan &pl, cudaStream_t st) {
 int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
              int64_t n_sets, int kind, int32_t k, int32_t K, int32_t b, uint64_t seed, uint64_t *out_words,
              uint64_t *out_keys, uint32_t *out_lsh, cudaStream_t st, void *queue = nullptr,
-             const Choice *force = nullptr) {
+             const Choice *force = nullptr, const int32_t *scale = nullptr) {
     if (!ctx) return DM_EINVAL;
     const Choice ch = force ? *force : choose(ctx, kind, k, K, b);
     Plan pl;
     int rc = plan_call(ctx, indptr, indices, weights, n_sets, kind, k, K, b, seed, out_words, out_keys, out_lsh,
-                       queue, ch, pl);
+                       queue, ch, pl, scale);
     if (rc || pl.p.n_sets == 0) return rc;
     return run_plan(ctx, pl, st);
 }
@@ -515,6 +517,24 @@ int dm_lsh(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const fl
            int64_t n_sets, int32_t L, int32_t K, uint64_t seed, uint32_t *out, void *stream) {
     return run_sets(ctx, indptr, indices, weights, n_sets, dm::kLsh, L, K, 0, seed, nullptr, nullptr, out,
                     (cudaStream_t)stream);
+}
+
+int dm_lsh_scaled(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
+                  int64_t n_sets, int32_t L, int32_t K, uint64_t seed, const int32_t *scale_exp, uint32_t *out,
+                  void *stream) {
+    if (n_sets > 0 && !scale_exp) return DM_EINVAL;
+    return run_sets(ctx, indptr, indices, weights, n_sets, dm::kLsh, L, K, 0, seed, nullptr, nullptr, out,
+                    (cudaStream_t)stream, nullptr, nullptr, scale_exp);
+}
+
+int dm_weight_classes(dm_ctx *ctx, const int64_t *indptr, const float *weights, int64_t n_sets, int32_t *out,
+                      void *stream) {
+    if (!ctx || n_sets < 0) return DM_EINVAL;
+    if (n_sets == 0) return DM_OK;
+    if (!indptr || !weights || !out) return DM_EINVAL;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = dm::launch_weight_classes(indptr, weights, n_sets, out, ctx->sm_count, (cudaStream_t)stream);
+    return cuda_fail(e);
 }
 
 int dm_bottomk(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,

@@ -31,12 +31,14 @@ __device__ __forceinline__ int bitlen64(uint64_t x) { return 64 - __clzll((long 
 // Per-element weight geometry.  Returns nu_top = floor(log2(1 + t x)) (the last weight
 // region, Algorithm 1's nu bound) and F = floor(f 2^64) where f in [0, 1) is the position of
 // y = t x inside region nu_top:  y = 2^nu_top - 1 + f 2^nu_top.  Returns -1 for x == 0 and -2
-// when nu_top would exceed kMaxRegion.  x must be finite and >= 0.
-__device__ __forceinline__ int weight_geometry(uint32_t xbits, uint32_t t, uint64_t &F) {
+// when nu_top would exceed kMaxRegion.  x must be finite and >= 0.  escale: the weight counts as
+// x 2^escale (the exact normalisation of a weight class, Section 3).
+__device__ __forceinline__ int weight_geometry(uint32_t xbits, uint32_t t, uint64_t &F, int escale = 0) {
     uint32_t ex = (xbits >> 23) & 0xFFu, fr = xbits & 0x7FFFFFu;
     if (ex == 0 && fr == 0) return -1;
     uint64_t M = ex ? (uint64_t)(fr | 0x800000u) : (uint64_t)fr;
-    int E = ex ? (int)ex - 150 : -149;             // x = M 2^E exactly
+    int E = (ex ? (int)ex - 150 : -149) + escale;  // x 2^escale = M 2^E exactly
+    if (E > 64) return -2;                          // y >= 2^64 (and keeps the shifts below defined)
     uint64_t Z = (uint64_t)t * M;                  // y = Z 2^E, Z < 2^41
     if (E >= 0) {
         if (bitlen64(Z) + E > kMaxRegion + 1) return -2;     // y >= 2^39

@@ -21,6 +21,7 @@ struct SketchParams {
     uint32_t t;           // Theorem 1: ceil(k ln k) + k; LSH: L K
     uint64_t sigma;       // seed key
     float phi0;           // initial phi of Theorem 1's loop
+    const int32_t *scale; // optional per-set weight scale exponents (weight classes, Section 3)
     int32_t b;            // b-bit width (bbit mode)
     int32_t words;        // uint64 words per set in bbit mode
     uint64_t *out_keys;   // n_sets * k keys (may be null in bbit mode)
@@ -73,6 +74,11 @@ struct SideStream {
 };
 cudaError_t launch_batched(const SketchParams &p, int kind, bool bbit, bool count, int grid_fast,
                            int grid_general, int grid_large, cudaStream_t st, const SideStream *side = nullptr);
+
+// Weight class of each set (Section 3): floor(log2 |x|_1) of the fp32 sum, 0 for sets without
+// a positive weight.
+cudaError_t launch_weight_classes(const int64_t *indptr, const float *weights, int64_t n_sets, int32_t *out,
+                                  int sm_count, cudaStream_t st);
 
 // Shared memory of the large-set kernel's blocks.
 size_t large_block_bytes(int k, int warps);

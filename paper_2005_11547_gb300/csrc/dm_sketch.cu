@@ -475,8 +475,8 @@ __device__ __forceinline__ void fast_put(const FastMem &m, Sink &sink, uint32_t 
 // Returns 0, an error code, or kDefer.
 template <class Sink, bool COUNT>
 __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, int64_t end, const PassCut &pc,
-                         const FastMem &m, Sink &sink, int lane, unsigned long long *cnt, int part = 0,
-                         int nparts = 1) {
+                         const FastMem &m, Sink &sink, int lane, unsigned long long *cnt, int escale = 0,
+                         int part = 0, int nparts = 1) {
     constexpr bool LOWER = Sink::kLowerCut;
     __syncwarp();
     for (int nu = lane; nu < kRowTab; nu += 32) {
@@ -501,7 +501,7 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
             int nutop = -1;
             uint64_t F = 0, e = 0;
             if (pos < end) {
-                nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F);
+                nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F, escale);
                 if (nutop >= 0) e = mix64(p.sigma + kGolden * ((uint64_t)p.indices[pos] + 1));
             }
             if (__any_sync(kFull, nutop == -2)) return DM_ERANGE;
@@ -736,15 +736,15 @@ struct WalkG {
 // tile's areas split among nparts warps (this one is number part).  Returns 0 or an error code.
 template <class Sink, bool COUNT>
 __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, int64_t end, const PassCut &pc,
-                        const GenMem &m, Sink &sink, int lane, unsigned long long *cnt, int part = 0,
-                        int nparts = 1) {
+                        const GenMem &m, Sink &sink, int lane, unsigned long long *cnt, int escale = 0,
+                        int part = 0, int nparts = 1) {
     constexpr bool LOWER = Sink::kLowerCut;
     for (int64_t tile = first; tile < end; tile += stride) {
         const int64_t pos = tile + lane;
         int nutop = -1;
         uint64_t F = 0, e = 0;
         if (pos < end) {
-            nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F);
+            nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F, escale);
             if (nutop >= 0) e = mix64(p.sigma + kGolden * ((uint64_t)p.indices[pos] + 1));
         }
         if (__any_sync(kFull, nutop == -2)) return DM_ERANGE;
@@ -852,8 +852,10 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) set_kernel(const Sketc
         unsigned long long cnt[3] = {0, 0, 0};
         unsigned long long passes = 0;
         bool deferred = false;
+        const int sc = p.scale ? p.scale[set] : 0;
         if (!err && l1 > 0.f) {
-            uint32_t th = __float_as_uint(__fdiv_rn(p.phi0, l1));
+            // first limit phi0 / (|x|_1 2^sc); any positive value gives the same result
+            uint32_t th = __float_as_uint(sc ? scalbnf(__fdiv_rn(p.phi0, l1), -sc) : __fdiv_rn(p.phi0, l1));
             PassCut pc;
             pc.rho_lo = 0;
             pc.gfl_lo = 0;
@@ -866,8 +868,8 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) set_kernel(const Sketc
                 pc.gm1 = rc.gm1;
                 pc.cthr = th;
                 if (MODE == 0 && pc.rho_top != 0) { deferred = true; break; }
-                err = MODE == 0 ? fast_pass<Sink, COUNT>(p, beg, 32, end, pc, fm, sink, lane, cnt)
-                                : gen_pass<Sink, COUNT>(p, beg, 32, end, pc, gm, sink, lane, cnt);
+                err = MODE == 0 ? fast_pass<Sink, COUNT>(p, beg, 32, end, pc, fm, sink, lane, cnt, sc)
+                                : gen_pass<Sink, COUNT>(p, beg, 32, end, pc, gm, sink, lane, cnt, sc);
                 ++passes;
                 if (err == kDefer) { err = 0; deferred = true; break; }
                 if (err) break;
@@ -939,13 +941,31 @@ __global__ void __launch_bounds__(256) classify_kernel(const SketchParams p) {
             int c;
             if (p.large_nnz > 0 && nnz >= p.large_nnz) c = 2;
             else if (p.large_work > 0.f && nnz > 0 && est >= p.large_work) c = 2;
-            else c = (!(l1 > 0.f) || __fdiv_rn(p.phi0, l1) < 1.0f) ? 0 : 1;   // zero/invalid rows: fast
+            else c = (!(l1 > 0.f) || scalbnf(__fdiv_rn(p.phi0, l1), p.scale ? -p.scale[s] : 0) < 1.0f) ? 0 : 1;
             // floor(log2(est)) from the exponent field (est >= 1, finite or +inf)
             int lg = (int)((__float_as_uint(est) >> 23) & 0xFFu) - 127;
             const int bin = 31 - (lg > 31 ? 31 : lg);
             p.cls[s] = (uint8_t)(c * kBins + (bin < 0 ? 0 : bin));
             atomicAdd(&p.hist[c * kBins + (bin < 0 ? 0 : bin)], 1u);
         }
+    }
+}
+
+// Weight class c = floor(log2 |x|_1) per set (Section 3's split of the data into classes
+// |x|_1 in [2^c, 2^(c+1))); the norm is the warp's fp32 sum.
+__global__ void __launch_bounds__(256) weight_class_kernel(const int64_t *indptr, const float *weights,
+                                                           int64_t n_sets, int32_t *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n_sets; s += nw) {
+        float l1 = 0.f;
+        for (int64_t i = indptr[s] + lane; i < indptr[s + 1]; i += 32) {
+            const float x = weights[i];
+            if (x > 0.f && x < 3.0e38f) l1 += x;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(kFull, l1, o);
+        if (lane == 0) out[s] = (l1 > 0.f && l1 < 3.0e38f) ? ilogbf(l1) : 0;
     }
 }
 
@@ -1021,8 +1041,9 @@ __global__ void __launch_bounds__(256, 2) large_kernel(const SketchParams p) {
         for (int w = 0; w < nwarps; ++w) l1 += wsum[w];
         unsigned long long cnt[3] = {0, 0, 0};
         unsigned long long passes = 0;
+        const int sc = p.scale ? p.scale[set] : 0;
         if (!err && l1 > 0.f) {
-            uint32_t th = __float_as_uint(__fdiv_rn(p.phi0, l1));
+            uint32_t th = __float_as_uint(sc ? scalbnf(__fdiv_rn(p.phi0, l1), -sc) : __fdiv_rn(p.phi0, l1));
             PassCut pc;
             pc.rho_lo = 0;
             pc.gfl_lo = 0;
@@ -1036,12 +1057,12 @@ __global__ void __launch_bounds__(256, 2) large_kernel(const SketchParams p) {
                 pc.cthr = th;
                 int e = kDefer;
                 if (pc.rho_top == 0)
-                    e = split ? fast_pass<SketchSink, COUNT>(p, beg, 32, end, pc, fm, sink, lane, cnt, wid, nwarps)
-                              : fast_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, fm, sink, lane, cnt);
+                    e = split ? fast_pass<SketchSink, COUNT>(p, beg, 32, end, pc, fm, sink, lane, cnt, sc, wid, nwarps)
+                              : fast_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, fm, sink, lane, cnt, sc);
                 const int any_defer = __syncthreads_or(e == kDefer);
                 if (any_defer)
-                    e = split ? gen_pass<SketchSink, COUNT>(p, beg, 32, end, pc, gm, sink, lane, cnt, wid, nwarps)
-                              : gen_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, gm, sink, lane, cnt);
+                    e = split ? gen_pass<SketchSink, COUNT>(p, beg, 32, end, pc, gm, sink, lane, cnt, sc, wid, nwarps)
+                              : gen_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, gm, sink, lane, cnt, sc);
                 ++passes;
                 if (__syncthreads_or(e == DM_ERANGE)) { err = DM_ERANGE; break; }
                 int empty = 0;
@@ -1093,6 +1114,13 @@ int large_blocks_per_sm(bool bbit, int warps, size_t smem) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * warps, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_weight_classes(const int64_t *indptr, const float *weights, int64_t n_sets, int32_t *out,
+                                  int sm_count, cudaStream_t st) {
+    const int64_t blocks = (n_sets + 7) / 8, cap = 16LL * (sm_count > 0 ? sm_count : 1);
+    weight_class_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(indptr, weights, n_sets, out);
+    return cudaGetLastError();
 }
 
 size_t call_scratch_bytes(int64_t n_sets) {

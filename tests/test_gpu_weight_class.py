@@ -1,0 +1,74 @@
+"""GPU parity of the weight-class normalised LSH (Section 3): dm_lsh_scaled equals the oracle's
+exactly scaled LSH for every set and scale, scale 0 equals dm_lsh, and dm_weight_classes gives
+floor(log2 ||x||_1) (the oracle's class wherever the norm is not within fp32 rounding of a power
+of two)."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+THREADS = 16
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def dmx(torch_mod):
+    import paper_2005_11547_gb300 as dmx
+    dmx.build()
+    dmx.load()
+    return dmx
+
+
+def to_dev(torch, b):
+    return (torch.from_numpy(np.ascontiguousarray(b.indptr, dtype=np.int64)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(b.indices, dtype=np.uint32).view(np.int32)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(b.weights, dtype=np.float32)).cuda())
+
+
+@pytest.mark.parametrize("form", [0, 2])
+def test_scaled_lsh_matches_oracle(dmx, torch_mod, oracle_mod, form):
+    torch = torch_mod
+    b = workloads.random_sets(400, 0, 200, 1 << 22, seed=61, scale_lo=1e-4, scale_hi=1e4)
+    ctx = dmx.dm_create(0)
+    dmx.dm_set_option(ctx, dmx.OPT_FORM, form)
+    ip, ix, w = to_dev(torch, b)
+    cls = dmx.dm_weight_classes(ctx, ip, w)
+    scale = -cls                                        # normalise every class to [1, 2)
+    got = dmx.dm_lsh_scaled(ctx, ip, ix, w, 32, 4, 77, scale)
+    assert dmx.dm_sync_status(ctx, raise_on_error=False) == 0
+    exp = oracle_mod.lsh(b.indptr, b.indices, b.weights, 32, 4, 77, scale=scale.cpu().numpy(), threads=THREADS)
+    assert np.array_equal(got.cpu().numpy().view(np.uint32), exp)
+    # probing the neighbouring classes of each set (a query's view)
+    for d in (-1, 1):
+        got = dmx.dm_lsh_scaled(ctx, ip, ix, w, 32, 4, 77, scale + d)
+        exp = oracle_mod.lsh(b.indptr, b.indices, b.weights, 32, 4, 77, scale=(scale + d).cpu().numpy(),
+                             threads=THREADS)
+        assert np.array_equal(got.cpu().numpy().view(np.uint32), exp)
+    zero = torch.zeros_like(scale)
+    assert torch.equal(dmx.dm_lsh_scaled(ctx, ip, ix, w, 32, 4, 77, zero), dmx.dm_lsh(ctx, ip, ix, w, 32, 4, 77))
+    ctx.close()
+
+
+def test_weight_classes(dmx, torch_mod, oracle_mod):
+    torch = torch_mod
+    b = workloads.random_sets(2000, 0, 100, 1 << 22, seed=62, scale_lo=1e-8, scale_hi=1e8)
+    ctx = dmx.dm_create(0)
+    ip, ix, w = to_dev(torch, b)
+    got = dmx.dm_weight_classes(ctx, ip, w).cpu().numpy()
+    ctx.close()
+    exp = oracle_mod.weight_class(b.indptr, b.weights)
+    l1 = np.array([b.weights[b.indptr[s]:b.indptr[s + 1]].astype(np.float64).sum() for s in range(b.n_sets)])
+    frac = np.where(l1 > 0, np.log2(np.maximum(l1, 1e-300)) - exp, 0.5)
+    clear = (frac > 1e-5) & (frac < 1 - 1e-5)           # not within fp32 rounding of a power of two
+    assert clear.sum() > 1900
+    assert np.array_equal(got[clear], exp[clear])
+    assert np.all(np.abs(got - exp) <= 1)
