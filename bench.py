@@ -48,11 +48,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dm", "reference"], default="dm")
     ap.add_argument("--sets", type=int, default=None, help="prefix of the workload (profiling only)")
-    ap.add_argument("--workload", choices=["W1", "W2", "W3", "W4", "W1B", "CMP"], default="W1",
+    ap.add_argument("--workload", choices=["W1", "W2", "W3", "W4", "W1B", "CMP", "W3S"], default="W1",
                     help="W1 (default, the headline): k=256 keys + 1-bit words; W2: k=1024 heavy-tailed batch; "
                          "W3: (L, K) = (64, 8) LSH; W4: serving loop on a Poisson request trace; "
-                         "W1B: bottom-k sketches (k=256) of the W1 sets; CMP: similarity counts of sketch pairs")
+                         "W1B: bottom-k sketches (k=256) of the W1 sets; CMP: similarity counts of sketch pairs; "
+                         "W3S: W3 with each set's weight class normalised to ||x||_1 in [1, 2)")
     ap.add_argument("--duration", type=float, default=20.0, help="W4: seconds of 50,000/s arrivals to replay")
+    ap.add_argument("--norm-exp", type=int, default=2,
+                    help="W3S: normalise each weight class to ||x||_1 in [2^e, 2^(e+1)) (2: first limit below 1)")
     ap.add_argument("--form", choices=["batched", "plain", "persistent"], default="batched",
                     help="launch form (the plain form is the one-warp-per-set reference)")
     ap.add_argument("--large-nnz", type=int, default=None, help="batched form: element count of a large set")
@@ -252,25 +255,28 @@ def gpu_arm(args):
         b = workloads.workload2(args.sets or 200_000)
     else:
         b = workloads.workload3(args.sets or 1_000_000)
+    lsh_kind = wl in ("W3", "W3S")
     n = b.n_sets
-    kk = {"W1": K_SLOTS, "W2": 1024, "W3": 64, "W1B": K_SLOTS}[wl]
+    kk = {"W1": K_SLOTS, "W2": 1024, "W3": 64, "W1B": K_SLOTS, "W3S": 64}[wl]
     words = (K_SLOTS * B_BITS + 63) // 64
     ip = torch.from_numpy(b.indptr).cuda()
     ix = torch.from_numpy(b.indices.view(np.int32)).cuda()
     w = torch.from_numpy(b.weights).cuda()
-    if wl == "W3":
+    if lsh_kind:
         keys = torch.empty((n, 64), dtype=torch.int32, device="cuda")
         outw = None
     else:
         keys = torch.empty((n, kk), dtype=torch.int64, device="cuda")
         outw = torch.empty((n, words), dtype=torch.int64, device="cuda") if wl == "W1" else None
+    cls = torch.empty(n, dtype=torch.int32, device="cuda")
+    scl = torch.empty(n, dtype=torch.int32, device="cuda")
     form_id = {"batched": dmx.FORM_BATCHED, "plain": dmx.FORM_PLAIN, "persistent": dmx.FORM_PERSISTENT}[args.form]
     def manual_settings(c):
         dmx.dm_set_option(c, dmx.OPT_FORM, form_id)
         if args.large_nnz is not None:
             dmx.dm_set_option(c, dmx.OPT_LARGE_NNZ, args.large_nnz)
         if args.phi0 is not None:
-            dmx.dm_set_option(c, dmx.OPT_LSH_PHI0 if wl == "W3" else dmx.OPT_PHI0, int(round(args.phi0 * 1024)))
+            dmx.dm_set_option(c, dmx.OPT_LSH_PHI0 if lsh_kind else dmx.OPT_PHI0, int(round(args.phi0 * 1024)))
         if args.wpb is not None:
             dmx.dm_set_option(c, dmx.OPT_WARPS_PER_BLOCK, args.wpb)
 
@@ -285,6 +291,10 @@ def gpu_arm(args):
             dmx.dm_sketch(c, ip, ix, w, 1024, SEED, out=keys, stream=stream)
         elif wl == "W1B":
             dmx.dm_bottomk(c, ip, ix, w, K_SLOTS, SEED, out=keys, stream=stream)
+        elif wl == "W3S":
+            # classes, then the class-normalised values (both inside the step)
+            dmx.dm_weight_classes(c, ip, w, out=cls, scale_out=scl, norm_exp=args.norm_exp, stream=stream)
+            dmx.dm_lsh_scaled(c, ip, ix, w, 64, 8, SEED, scl, out=keys, stream=stream)
         else:
             dmx.dm_lsh(c, ip, ix, w, 64, 8, SEED, out=keys, stream=stream)
 
@@ -297,6 +307,8 @@ def gpu_arm(args):
             tuning = dmx.dm_autotune(ctx, ip, ix, w, 1024, SEED, max_sets=n, stream=stream)
         elif wl == "W1B":
             tuning = dmx.dm_autotune(ctx, ip, ix, w, K_SLOTS, SEED, bottomk=True, stream=stream)
+        elif wl == "W3S":
+            tuning = None                             # the tuner does not model the scaled calls
         else:
             tuning = dmx.dm_autotune(ctx, ip, ix, w, 64, SEED, lsh_K=8, stream=stream)
     if not args.no_graph:
@@ -316,7 +328,7 @@ def gpu_arm(args):
         dmx.dm_set_option(cctx, dmx.OPT_WARPS_PER_BLOCK, tuning["warps_per_block"])
         dmx.dm_set_option(cctx, dmx.OPT_LARGE_NNZ, tuning["large_nnz"])
         dmx.dm_set_option(cctx, dmx.OPT_LARGE_WORK, tuning["large_work"])
-        dmx.dm_set_option(cctx, dmx.OPT_LSH_PHI0 if wl == "W3" else dmx.OPT_PHI0, tuning["phi0_1024"])
+        dmx.dm_set_option(cctx, dmx.OPT_LSH_PHI0 if lsh_kind else dmx.OPT_PHI0, tuning["phi0_1024"])
     launch(cctx)
     dmx.dm_sync_status(cctx)
     areas, darts, kept, passes = [int(v) for v in cnt.cpu().tolist()]
@@ -420,7 +432,9 @@ def gpu_arm(args):
                   "1e-3..1e3), d=2^24; k=1024 uint64 keys",
             "W3": "W3: 1,000,000 tf-idf-like sets (Zipf(1.1) tokens, nnz U{200..2000}), d=2^20; (L, K) = (64, 8) "
                   "LSH uint32 values",
-            "W1B": "W1 sets (1,000,000 x 256 elements, Exp(1) weights); bottom-k sketches, k=256 sorted uint64 keys"}[wl]
+            "W1B": "W1 sets (1,000,000 x 256 elements, Exp(1) weights); bottom-k sketches, k=256 sorted uint64 keys",
+            "W3S": f"W3 sets with each set's weight class normalised to ||x||_1 in [2^{args.norm_exp}, "
+                   f"2^{args.norm_exp + 1}) (Section 3); (L, K) = (64, 8) LSH uint32 values"}[wl]
     if rank == 0:
         line = {
             "metric": METRIC if wl == "W1" else f"weighted sets/s ({wl})",
@@ -436,7 +450,7 @@ def gpu_arm(args):
             "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
             "plain_form": plain, "tuning": tuning,
             "gpu_launches": (2 if (tuning["form"] if tuning else form_id) != dmx.FORM_BATCHED
-                             else (5 if wl in ("W3", "W1B") else 6)) * args.steps,
+                             else (5 if wl in ("W3", "W1B") else (6 if wl == "W3S" else 6))) * args.steps,
             "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)

@@ -106,9 +106,12 @@ int dm_lsh_scaled(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, c
 
 /* Weight class of each set: out[s] = floor(log2 ||x||_1) with ||x||_1 summed in fp32 by the GPU
  * (so a norm within rounding of a power of two may land in either neighbouring class); 0 for a
- * set without a positive weight.  Device int32 out[n_sets]. */
+ * set without a positive weight.  Device int32 out[n_sets] (may be NULL); scale_out (may be
+ * NULL) receives norm_exp - out[s], the scale for dm_lsh_scaled that puts the class's norms in
+ * [2^norm_exp, 2^(norm_exp+1)) (Section 3 normalises to [1, 2), norm_exp = 0; a larger range keeps
+ * the first rank limit phi0 / ||x||_1 below 1, where the enumeration is cheapest). */
 int dm_weight_classes(dm_ctx *ctx, const int64_t *indptr, const float *weights, int64_t n_sets, int32_t *out,
-                      void *stream);
+                      int32_t *scale_out, int32_t norm_exp, void *stream);
 
 /* Bottom-k weighted sketch (Section 3, "Bottom-k minhash and fast approximate near neighbor
  * search": with t = k, raise phi until DartHash returns at least k darts and keep them sorted by

@@ -59,7 +59,7 @@ def load(path: str | None = None):
             "dm_bottomk": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
             "dm_compare": ([P, P, P, i64, i64, i32, i32, i32, P, P], ctypes.c_int),
             "dm_lsh_scaled": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
-            "dm_weight_classes": ([P, P, P, i64, P, P], ctypes.c_int),
+            "dm_weight_classes": ([P, P, P, i64, P, P, i32, P], ctypes.c_int),
             "dm_sketch_host": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_sync_status": ([P, P], ctypes.c_int),
             "dm_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -203,15 +203,17 @@ def dm_lsh_scaled(ctx: Context, indptr, indices, weights, L: int, K: int, seed: 
     return out
 
 
-def dm_weight_classes(ctx: Context, indptr, weights, out=None, stream=None):
-    """int32 weight class floor(log2 ||x||_1) of each set (fp32 norm)."""
+def dm_weight_classes(ctx: Context, indptr, weights, out=None, scale_out=None, norm_exp: int = 0, stream=None):
+    """int32 weight class floor(log2 ||x||_1) of each set (fp32 norm); scale_out, when given,
+    receives norm_exp - class, the scales that put every class's norms in [2^norm_exp, 2^(norm_exp+1))."""
     import torch
     n = indptr.numel() - 1
     if out is None:
         out = torch.empty(n, dtype=torch.int32, device=indptr.device)
     _check(load().dm_weight_classes(ctx.handle, _dev_ptr(indptr, "int64", "indptr"),
                                     _dev_ptr(weights, "float32", "weights"), n, _dev_ptr(out, "int32", "out"),
-                                    _stream(stream)), "dm_weight_classes")
+                                    _dev_ptr(scale_out, "int32", "scale_out") if scale_out is not None else None,
+                                    int(norm_exp), _stream(stream)), "dm_weight_classes")
     return out
 
 

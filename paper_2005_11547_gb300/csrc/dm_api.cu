@@ -528,12 +528,14 @@ int dm_lsh_scaled(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, c
 }
 
 int dm_weight_classes(dm_ctx *ctx, const int64_t *indptr, const float *weights, int64_t n_sets, int32_t *out,
-                      void *stream) {
+                      int32_t *scale_out, int32_t norm_exp, void *stream) {
     if (!ctx || n_sets < 0) return DM_EINVAL;
     if (n_sets == 0) return DM_OK;
-    if (!indptr || !weights || !out) return DM_EINVAL;
+    if (!indptr || !weights || (!out && !scale_out)) return DM_EINVAL;
     cudaError_t e = cudaSetDevice(ctx->device);
-    if (e == cudaSuccess) e = dm::launch_weight_classes(indptr, weights, n_sets, out, ctx->sm_count, (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = dm::launch_weight_classes(indptr, weights, n_sets, out, scale_out, norm_exp, ctx->sm_count,
+                                      (cudaStream_t)stream);
     return cuda_fail(e);
 }
 

@@ -78,7 +78,7 @@ cudaError_t launch_batched(const SketchParams &p, int kind, bool bbit, bool coun
 // Weight class of each set (Section 3): floor(log2 |x|_1) of the fp32 sum, 0 for sets without
 // a positive weight.
 cudaError_t launch_weight_classes(const int64_t *indptr, const float *weights, int64_t n_sets, int32_t *out,
-                                  int sm_count, cudaStream_t st);
+                                  int32_t *scale_out, int32_t norm_exp, int sm_count, cudaStream_t st);
 
 // Shared memory of the large-set kernel's blocks.
 size_t large_block_bytes(int k, int warps);

@@ -954,7 +954,8 @@ __global__ void __launch_bounds__(256) classify_kernel(const SketchParams p) {
 // Weight class c = floor(log2 |x|_1) per set (Section 3's split of the data into classes
 // |x|_1 in [2^c, 2^(c+1))); the norm is the warp's fp32 sum.
 __global__ void __launch_bounds__(256) weight_class_kernel(const int64_t *indptr, const float *weights,
-                                                           int64_t n_sets, int32_t *out) {
+                                                           int64_t n_sets, int32_t *out, int32_t *scale_out,
+                                                           int32_t norm_exp) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n_sets; s += nw) {
@@ -965,7 +966,11 @@ __global__ void __launch_bounds__(256) weight_class_kernel(const int64_t *indptr
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(kFull, l1, o);
-        if (lane == 0) out[s] = (l1 > 0.f && l1 < 3.0e38f) ? ilogbf(l1) : 0;
+        if (lane == 0) {
+            const int c = (l1 > 0.f && l1 < 3.0e38f) ? ilogbf(l1) : 0;
+            if (out) out[s] = c;
+            if (scale_out) scale_out[s] = norm_exp - c;
+        }
     }
 }
 
@@ -1117,9 +1122,10 @@ int large_blocks_per_sm(bool bbit, int warps, size_t smem) {
 }
 
 cudaError_t launch_weight_classes(const int64_t *indptr, const float *weights, int64_t n_sets, int32_t *out,
-                                  int sm_count, cudaStream_t st) {
+                                  int32_t *scale_out, int32_t norm_exp, int sm_count, cudaStream_t st) {
     const int64_t blocks = (n_sets + 7) / 8, cap = 16LL * (sm_count > 0 ? sm_count : 1);
-    weight_class_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(indptr, weights, n_sets, out);
+    weight_class_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(indptr, weights, n_sets, out, scale_out,
+                                                                             norm_exp);
     return cudaGetLastError();
 }
 

@@ -41,8 +41,9 @@ def test_scaled_lsh_matches_oracle(dmx, torch_mod, oracle_mod, form):
     ctx = dmx.dm_create(0)
     dmx.dm_set_option(ctx, dmx.OPT_FORM, form)
     ip, ix, w = to_dev(torch, b)
-    cls = dmx.dm_weight_classes(ctx, ip, w)
-    scale = -cls                                        # normalise every class to [1, 2)
+    scale = torch.empty(b.n_sets, dtype=torch.int32, device="cuda")
+    cls = dmx.dm_weight_classes(ctx, ip, w, scale_out=scale)
+    assert torch.equal(scale, -cls)                     # normalise every class to [1, 2)
     got = dmx.dm_lsh_scaled(ctx, ip, ix, w, 32, 4, 77, scale)
     assert dmx.dm_sync_status(ctx, raise_on_error=False) == 0
     exp = oracle_mod.lsh(b.indptr, b.indices, b.weights, 32, 4, 77, scale=scale.cpu().numpy(), threads=THREADS)
@@ -64,6 +65,9 @@ def test_weight_classes(dmx, torch_mod, oracle_mod):
     ctx = dmx.dm_create(0)
     ip, ix, w = to_dev(torch, b)
     got = dmx.dm_weight_classes(ctx, ip, w).cpu().numpy()
+    sc = torch.empty(b.n_sets, dtype=torch.int32, device="cuda")
+    dmx.dm_weight_classes(ctx, ip, w, scale_out=sc, norm_exp=2)
+    assert np.array_equal(sc.cpu().numpy(), 2 - got)
     ctx.close()
     exp = oracle_mod.weight_class(b.indptr, b.weights)
     l1 = np.array([b.weights[b.indptr[s]:b.indptr[s + 1]].astype(np.float64).sum() for s in range(b.n_sets)])
