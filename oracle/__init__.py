@@ -253,6 +253,34 @@ def lsh(indptr, indices, weights, L: int, K: int, seed: int, *, phi0: float = 1.
     return (out, wk) if work else out
 
 
+def lsh_index_query(values, ids, queries, max_candidates: int):
+    """Approximate near neighbor candidates of the (L, K) LSH tables (Section 1.2, "Fast similarity
+    search"; Section 3): point p collides with query q in table l when value_l(p) == value_l(q);
+    q's candidates are the distinct ids of every point colliding with it in at least one table.
+    Returns (counts int32[m], ids int64[m, max_candidates]): the number of distinct candidates and
+    the smallest max_candidates of them in increasing order, padded with -1.  values uint32[n, L],
+    ids int64[n], queries uint32[m, L]."""
+    values = np.asarray(values, dtype=np.uint32)
+    queries = np.asarray(queries, dtype=np.uint32)
+    ids = np.asarray(ids, dtype=np.int64)
+    L = values.shape[1] if values.ndim == 2 else queries.shape[1]
+    tables = [dict() for _ in range(L)]
+    for p in range(values.shape[0]):
+        for l in range(L):
+            tables[l].setdefault(int(values[p, l]), []).append(int(ids[p]))
+    m = queries.shape[0]
+    counts = np.zeros(m, dtype=np.int32)
+    out = np.full((m, max_candidates), -1, dtype=np.int64)
+    for q in range(m):
+        cand = set()
+        for l in range(L):
+            cand.update(tables[l].get(int(queries[q, l]), ()))
+        c = sorted(cand)
+        counts[q] = len(c)
+        out[q, :min(len(c), max_candidates)] = c[:max_candidates]
+    return counts, out
+
+
 def weight_class(indptr, weights):
     """Weight class of each set (Section 3): c = floor(log2 ||x||_1) with ||x||_1 summed in
     double; sets with no positive weight get 0.  Normalising a class to ||x||_1 in [1, 2) means
