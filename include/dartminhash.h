@@ -124,6 +124,27 @@ int dm_weight_classes(dm_ctx *ctx, const int64_t *indptr, const float *weights, 
 int dm_bottomk(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
                int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream);
 
+/* LSH tables for approximate near neighbor search (Section 1.2, "Fast similarity search", and
+ * Section 3): L hash tables keyed by the L values dm_lsh / dm_lsh_scaled give each point.  A query
+ * gets every point that shares a value with it in at least one table (for a point at weighted
+ * Jaccard similarity J, with probability 1 - (1 - J^K)^L).  The index lives on `device` and holds
+ * up to `capacity` points (capacity * L <= 2^31 - 1; about 24 L bytes per point of capacity).
+ *   create: empty index.  insert: n points, values uint32[n * L] (row-major, device), ids int64[n]
+ *   (device; NULL = consecutive ids from the number of points already inserted); DM_ENOMEM past
+ *   the capacity.  query: m queries, values uint32[m * L]; counts int32[m] receives the number of
+ *   distinct candidates (-1 if a query gathers more than 2,048 (point, table) collisions), out_ids
+ *   int64[m * max_candidates] the smallest max_candidates candidate ids in increasing order, padded
+ *   with -1 (1 <= max_candidates <= 2,048).  All asynchronous on `stream`; status returns (and
+ *   clears) an insertion error recorded by the device (DM_EOVERFLOW: a table probe gave up). */
+typedef struct dm_lsh_index dm_lsh_index;
+int dm_lsh_index_create(dm_lsh_index **out, int device, int32_t L, int64_t capacity);
+int dm_lsh_index_insert(dm_lsh_index *ix, const uint32_t *values, const int64_t *ids, int64_t n, void *stream);
+int dm_lsh_index_query(dm_lsh_index *ix, const uint32_t *queries, int64_t m, int32_t max_candidates,
+                       int32_t *counts, int64_t *out_ids, void *stream);
+int dm_lsh_index_size(dm_lsh_index *ix, int64_t *n);
+int dm_lsh_index_status(dm_lsh_index *ix, void *stream);
+int dm_lsh_index_destroy(dm_lsh_index *ix);
+
 /* Similarity counts of sketches (Section 1.1, "Similarity estimation"): for each pair of rows,
  * the number m of the k slots whose values agree.  bits = 0: rows of k uint64 keys from dm_sketch
  * (E[m] = k J, Eq. 1, so m / k estimates the weighted Jaccard similarity J); bits = b in

@@ -19,7 +19,7 @@ import threading
 from .build import LIB, build
 
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
-           "dm_sketch_host", "dm_bottomk", "dm_compare", "dm_lsh_scaled", "dm_weight_classes", "estimate_jaccard", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
+           "dm_sketch_host", "dm_bottomk", "dm_compare", "dm_lsh_scaled", "dm_weight_classes", "LshIndex", "estimate_jaccard", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
            "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
            "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "OPT_LARGE_WORK", "FORM_BATCHED",
            "FORM_PLAIN", "FORM_PERSISTENT", "dm_autotune", "Tuning", "Server", "EAGAIN"]
@@ -59,6 +59,12 @@ def load(path: str | None = None):
             "dm_bottomk": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
             "dm_compare": ([P, P, P, i64, i64, i32, i32, i32, P, P], ctypes.c_int),
             "dm_lsh_scaled": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
+            "dm_lsh_index_create": ([ctypes.POINTER(P), ctypes.c_int, i32, i64], ctypes.c_int),
+            "dm_lsh_index_insert": ([P, P, P, i64, P], ctypes.c_int),
+            "dm_lsh_index_query": ([P, P, i64, i32, P, P, P], ctypes.c_int),
+            "dm_lsh_index_size": ([P, P], ctypes.c_int),
+            "dm_lsh_index_status": ([P, P], ctypes.c_int),
+            "dm_lsh_index_destroy": ([P], ctypes.c_int),
             "dm_weight_classes": ([P, P, P, i64, P, P, i32, P], ctypes.c_int),
             "dm_sketch_host": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_sync_status": ([P, P], ctypes.c_int),
@@ -201,6 +207,51 @@ def dm_lsh_scaled(ctx: Context, indptr, indices, weights, L: int, K: int, seed: 
                                 _dev_ptr(scale_exp, "int32", "scale_exp"), _dev_ptr(out, "uint32", "out"),
                                 _stream(stream)), "dm_lsh_scaled")
     return out
+
+
+class LshIndex:
+    """Owns a dm_lsh_index*: L hash tables of LSH values on a device."""
+
+    def __init__(self, L: int, capacity: int, device: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().dm_lsh_index_create(ctypes.byref(h), int(device), int(L), int(capacity)), "dm_lsh_index_create")
+        self.handle, self.L = h, L
+
+    def insert(self, values, ids=None, stream=None):
+        n = values.shape[0]
+        _check(load().dm_lsh_index_insert(self.handle, _dev_ptr(values, "uint32", "values"),
+                                          _dev_ptr(ids, "int64", "ids") if ids is not None else None, n,
+                                          _stream(stream)), "dm_lsh_index_insert")
+
+    def query(self, values, max_candidates: int, stream=None):
+        """(counts int32[m], ids int64[m, max_candidates]) as CUDA tensors."""
+        import torch
+        m = values.shape[0]
+        counts = torch.empty(m, dtype=torch.int32, device=values.device)
+        ids = torch.empty((m, max_candidates), dtype=torch.int64, device=values.device)
+        _check(load().dm_lsh_index_query(self.handle, _dev_ptr(values, "uint32", "values"), m, int(max_candidates),
+                                         _dev_ptr(counts, "int32", "counts"), _dev_ptr(ids, "int64", "ids"),
+                                         _stream(stream)), "dm_lsh_index_query")
+        return counts, ids
+
+    def size(self) -> int:
+        n = ctypes.c_int64()
+        _check(load().dm_lsh_index_size(self.handle, ctypes.cast(ctypes.byref(n), ctypes.c_void_p)), "dm_lsh_index_size")
+        return n.value
+
+    def status(self, stream=None) -> int:
+        return int(load().dm_lsh_index_status(self.handle, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            load().dm_lsh_index_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dm_weight_classes(ctx: Context, indptr, weights, out=None, scale_out=None, norm_exp: int = 0, stream=None):

@@ -148,6 +148,24 @@ __device__ __forceinline__ int poisson1(uint32_t u, const uint32_t *T) {
     return x;
 }
 
+// Ascending bitonic sort of n (a power of two) 64-bit keys in shared memory by one warp.
+template <class T>
+__device__ inline void warp_bitonic_sort(T *a, uint32_t n, int lane) {
+    for (uint32_t size = 2; size <= n; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride; stride >>= 1) {
+            for (uint32_t i = (uint32_t)lane; i < n / 2; i += 32) {
+                const uint32_t lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1)), hi = lo + stride;
+                const T x = a[lo], y = a[hi];
+                if ((x > y) == ((lo & size) == 0)) {
+                    a[lo] = y;
+                    a[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
 __device__ __forceinline__ void set_status(int *status, int code) {
     if (status) atomicCAS(status, 0, code);
 }

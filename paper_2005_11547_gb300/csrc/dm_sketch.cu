@@ -249,23 +249,6 @@ __host__ __device__ inline uint32_t bottomk_cap(int k) {
 }
 size_t bottomk_sink_bytes(int k) { return (size_t)bottomk_cap(k) * 8 + 16; }
 
-// Ascending bitonic sort of n (a power of two) keys in shared memory by one warp.
-__device__ void warp_bitonic_sort(uint64_t *a, uint32_t n, int lane) {
-    for (uint32_t size = 2; size <= n; size <<= 1) {
-        for (uint32_t stride = size >> 1; stride; stride >>= 1) {
-            for (uint32_t i = (uint32_t)lane; i < n / 2; i += 32) {
-                const uint32_t lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1)), hi = lo + stride;
-                const uint64_t x = a[lo], y = a[hi];
-                if ((x > y) == ((lo & size) == 0)) {
-                    a[lo] = y;
-                    a[hi] = x;
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
 struct BottomKSink {
     uint64_t *buf, *tau;
     uint32_t *cnt;
