@@ -66,7 +66,7 @@ def test_index_explicit_ids_and_limits(dmx, torch_mod, oracle_mod):
     rng = np.random.default_rng(41)
     L = 8
     vals = rng.integers(0, 50, size=(1000, L), dtype=np.uint32)        # many shared values
-    ids = rng.permutation(10 ** 9)[:1000].astype(np.int64)
+    ids = rng.choice(10 ** 9, size=1000, replace=False).astype(np.int64)
     q = rng.integers(0, 50, size=(64, L), dtype=np.uint32)
     dv = torch.from_numpy(vals.view(np.int32)).cuda()
     ix = dmx.LshIndex(L, 1000)
