@@ -383,14 +383,16 @@ __device__ __forceinline__ uint64_t ceil_scaled(uint32_t bits, int S) {
     return (m + (1ull << -sh) - 1) >> -sh;
 }
 
-__device__ __forceinline__ uint32_t clamp_u(uint64_t pt, uint64_t rb) {
-    return pt <= rb ? 0u : (uint32_t)min(pt - rb, (uint64_t)(1u << 25));
+// u threshold of the current area from its remaining rank room p = pthr - r 2^24.
+__device__ __forceinline__ uint32_t clamp_u(int64_t p) {
+    return p <= 0 ? 0u : (uint32_t)min(p, (int64_t)(1 << 25));
 }
 
 struct WalkF {
     int el, nu, nutop;
     uint32_t r, rhi, vtop, vmax;
-    uint64_t e, ctr, pthr, plo;
+    uint64_t e, ctr;
+    int64_t pr, pl;           // pthr - r 2^24 and plo - r 2^24 of the current area
 
     __device__ __forceinline__ void region(const FastMem &m) {
         const uint4 a = *reinterpret_cast<const uint4 *>(&m.ra[nu]);          // kt, pthr
@@ -398,8 +400,8 @@ struct WalkF {
         r = b.x;
         rhi = b.y;
         ctr = e + (((uint64_t)a.y << 32) | a.x);
-        pthr = ((uint64_t)a.w << 32) | a.z;
-        plo = ((uint64_t)b.w << 32) | b.z;
+        pr = (int64_t)(((uint64_t)a.w << 32) | a.z) - ((int64_t)r << 24);
+        pl = (int64_t)(((uint64_t)b.w << 32) | b.z) - ((int64_t)r << 24);
         vmax = nu == nutop ? vtop : kUMask;
     }
     __device__ __forceinline__ void load(const FastMem &m) {
@@ -425,11 +427,17 @@ struct WalkF {
         region(m);
         r += li;
         ctr += kGolden * (uint64_t)li;
+        pr -= (int64_t)li << 24;
+        pl -= (int64_t)li << 24;
     }
+    // Next area.  Every region of a pass has at least one row (rlo = floor(g_prev 2^nu) <
+    // ceil(g 2^nu) = rhi because g_prev < g), so one region step suffices.
     __device__ __forceinline__ void advance(int n_el, const FastMem &m) {
         ++r;
         ctr += kGolden;
-        while (r == rhi) {
+        pr -= 1ll << 24;
+        pl -= 1ll << 24;
+        if (r == rhi) {
             if (++nu > nutop) {
                 nu = 0;
                 do { ++el; } while (el < n_el && (signed char)(m.el[el].vn >> 24) < 0);
@@ -523,9 +531,8 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
                 --left;
                 c = mix64(s.ctr);
                 nx = (uint32_t)poisson1((uint32_t)(c >> 32), c_pois);
-                const uint64_t rb = (uint64_t)s.r << 24;
-                uthr = clamp_u(s.pthr, rb);
-                if (LOWER) ulo = clamp_u(s.plo, rb);
+                uthr = clamp_u(s.pr);
+                if (LOWER) ulo = clamp_u(s.pl);
                 if (COUNT) { cnt[0]++; cnt[1] += nx; }
             }
             bool keep = false;
