@@ -269,3 +269,62 @@ def csr_of(rows) -> Batch:
     idx = np.concatenate([np.asarray(r[0], dtype=np.uint32) for r in rows]) if rows else np.zeros(0, np.uint32)
     w = np.concatenate([np.asarray(r[1], dtype=np.float32) for r in rows]) if rows else np.zeros(0, np.float32)
     return Batch(ip, idx.astype(np.uint32), w.astype(np.float32), "rows")
+
+
+# ------------------------------------------------------------------------------------------
+# 64-bit ids and binary64 weights (Section 4, "Synthetic data", as the paper states it; Table 1)
+# ------------------------------------------------------------------------------------------
+@dataclass
+class WideBatch:
+    indptr: np.ndarray      # int64[n + 1]
+    indices: np.ndarray     # uint64[nnz]
+    weights: np.ndarray     # float64[nnz]
+    name: str = ""
+
+    @property
+    def n_sets(self) -> int:
+        return len(self.indptr) - 1
+
+
+def wide_ids(rng, n: int) -> np.ndarray:
+    """n distinct uniform 64-bit element ids (sorted)."""
+    while True:
+        ids = np.unique(rng.integers(0, 2 ** 64, size=n, dtype=np.uint64, endpoint=False))
+        if len(ids) == n:
+            return ids
+
+
+def wide_set(rng, nnz: int, l1: float):
+    """A uniform point of the probability simplex (normalised Exp(1) draws) scaled to
+    ||x||_1 = l1 (an exact power-of-two scaling for l1 = 2^e), on nnz distinct random 64-bit ids."""
+    e = rng.standard_exponential(nnz)
+    return wide_ids(rng, nnz), (e / e.sum()) * np.float64(l1)
+
+
+def wide_pair(rng, nnz: int, b: float, l1: float):
+    """The pair recipe at norm l1: x = wide_set, y_i = b x_i on supp(x) and y_j = (1 - b) l1 on
+    one fresh id j, so J(x, y) = b / (2 - b) and ||y||_1 = ||x||_1.  Returns (ix, wx, iy, wy)."""
+    ids = wide_ids(rng, nnz + 1)
+    perm = rng.permutation(nnz + 1)
+    ix, extra = np.sort(ids[perm[:nnz]]), ids[perm[nnz]]
+    e = rng.standard_exponential(nnz)
+    wx = (e / e.sum()) * np.float64(l1)
+    iy = np.concatenate([ix, [extra]])
+    wy = np.concatenate([b * wx, [(1.0 - b) * np.float64(l1)]])
+    o = np.argsort(iy)
+    return ix, wx, iy[o], wy[o]
+
+
+def wide_csr(rows, name: str = "rows") -> WideBatch:
+    lens = np.array([len(r[0]) for r in rows], dtype=np.int64)
+    ip = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(lens, out=ip[1:])
+    idx = np.concatenate([np.asarray(r[0], dtype=np.uint64) for r in rows]) if rows else np.zeros(0, np.uint64)
+    w = np.concatenate([np.asarray(r[1], dtype=np.float64) for r in rows]) if rows else np.zeros(0, np.float64)
+    return WideBatch(ip, idx, w, name)
+
+
+def table1_batch(n: int, nnz: int, l1: float, seed: int) -> WideBatch:
+    """Table 1's rows: n sets of nnz elements at ||x||_1 = l1 (Section 4's recipe)."""
+    rng = _rng(seed)
+    return wide_csr([wide_set(rng, nnz, l1) for _ in range(n)], f"table1 nnz={nnz} l1={l1!r}")
