@@ -48,12 +48,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dm", "reference"], default="dm")
     ap.add_argument("--sets", type=int, default=None, help="prefix of the workload (profiling only)")
-    ap.add_argument("--workload", choices=["W1", "W2", "W3", "W4", "W1B", "CMP", "W3S", "IDX"], default="W1",
+    ap.add_argument("--workload", choices=["W1", "W2", "W3", "W4", "W1B", "CMP", "W3S", "IDX", "T1"], default="W1",
                     help="W1 (default, the headline): k=256 keys + 1-bit words; W2: k=1024 heavy-tailed batch; "
                          "W3: (L, K) = (64, 8) LSH; W4: serving loop on a Poisson request trace; "
                          "W1B: bottom-k sketches (k=256) of the W1 sets; CMP: similarity counts of sketch pairs; "
                          "W3S: W3 with each set's weight class normalised to ||x||_1 in [1, 2); "
-                         "IDX: LSH-table index build and query over the W3 values")
+                         "IDX: LSH-table index build and query over the W3 values; "
+                         "T1: Table 1's sets (1,024 elements, 64-bit ids, binary64 weights, k=256) at "
+                         "||x||_1 = 1, 2^64, 2^-64, 2^512, 2^-512 through dm_sketch_f64")
     ap.add_argument("--duration", type=float, default=20.0, help="W4: seconds of 50,000/s arrivals to replay")
     ap.add_argument("--norm-exp", type=int, default=2,
                     help="W3S: normalise each weight class to ||x||_1 in [2^e, 2^(e+1)) (2: first limit below 1)")
@@ -730,6 +732,99 @@ def index_arm(args):
         dist.destroy_process_group()
 
 
+T1_NORMS = [("1", 1.0), ("2^64", 2.0 ** 64), ("2^-64", 2.0 ** -64), ("2^512", 2.0 ** 512),
+            ("2^-512", 2.0 ** -512)]
+
+
+def wide_arm(args):
+    """Table 1's workload through the wide-range entry: per norm, n sets of 1,024 elements on the
+    simplex scaled to ||x||_1 (Section 4's recipe, 64-bit ids), k = 256.  A step sketches the
+    whole batch (all norms) in one call; each norm is also timed alone."""
+    import numpy as np
+    import torch
+
+    import paper_2005_11547_gb300 as dmx
+    import workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, True)
+    dmx.build()
+    dmx.load()
+    props = torch.cuda.get_device_properties(local)
+    per, nnz, k = args.sets or 4000, 1024, K_SLOTS
+    parts = [workloads.table1_batch(per, nnz, l1, 700 + i + 16 * rank) for i, (_, l1) in enumerate(T1_NORMS)]
+    ip = torch.from_numpy(np.concatenate([[0]] + [p.indptr[1:] + nnz * per * i for i, p in enumerate(parts)])).cuda()
+    ix = torch.from_numpy(np.concatenate([p.indices for p in parts]).view(np.int64)).cuda()
+    w = torch.from_numpy(np.concatenate([p.weights for p in parts])).cuda()
+    n = per * len(parts)
+    out = torch.empty((n, k), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = dmx.dm_create(local)
+
+    # work counts of one launch (counting kernel variant, outside the timed region)
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    cctx = dmx.dm_create(local)
+    dmx.dm_set_option(cctx, dmx.OPT_COUNTERS, cnt.data_ptr())
+    dmx.dm_sketch_f64(cctx, ip, ix, w, k, SEED, out=out)
+    dmx.dm_sync_status(cctx)
+    areas, darts, kept, passes = [int(v) for v in cnt.cpu().tolist()]
+    cctx.close()
+
+    def timed(lo, hi, steps):
+        sub_ip = ip[lo:hi + 1] if lo == 0 else (ip[lo:hi + 1] - ip[lo]).contiguous()
+        e0 = ip[lo].item()
+        sub_ix, sub_w = ix[e0:].contiguous() if lo else ix, w[e0:].contiguous() if lo else w
+        sub_out = out[lo:hi]
+        for _ in range(max(3, args.warmup)):
+            dmx.dm_sketch_f64(ctx, sub_ip, sub_ix, sub_w, k, SEED, out=sub_out)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        barrier(dist, True)
+        ev[0].record(stream)
+        for _ in range(steps):
+            dmx.dm_sketch_f64(ctx, sub_ip, sub_ix, sub_w, k, SEED, out=sub_out)
+        ev[1].record(stream)
+        barrier(dist, True)
+        dmx.dm_sync_status(ctx)
+        return ev[0].elapsed_time(ev[1]) / 1e3 / steps
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_step = timed(0, n, args.steps)
+    clocks = sampler.stop()
+    per_norm = {}
+    for i, (name, _) in enumerate(T1_NORMS):
+        t = timed(i * per, (i + 1) * per, max(1, min(args.steps, 3)))
+        per_norm[name] = {"sets_per_s": per / t, "us_per_set_per_gpu": t / per * 1e6}
+    t_max = max_over_ranks(dist, t_step, True)
+    all_sets = sum_over_ranks(dist, float(n), True)
+    ops = areas * OPS_PER_AREA + darts * OPS_PER_DART + kept * OPS_PER_KEPT
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak_ops = props.multi_processor_count * INT_LANES_PER_SM * sm_max * 1e6
+    if rank == 0:
+        line = {
+            "metric": "weighted sets/s (Table 1 norms, k=256 wide-range minhash keys, bit-exact)",
+            "value": all_sets / t_max, "unit": "sets/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"T1: {per} sets per norm x 5 norms (1, 2^64, 2^-64, 2^512, 2^-512), "
+                                   f"{nnz} distinct 64-bit ids per set, binary64 simplex weights scaled to the norm",
+                       "k": k, "seed": SEED,
+                       "l2": f"inputs {n * nnz * 16 / 1e6:.0f} MB per step, > 129 MB L2: no flush needed"},
+            "per_norm": per_norm,
+            "roofline": {"bound": "alu", "achieved": ops / t_step / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                         "frac": ops / t_step / peak_ops, "traffic": None, "ops_per_launch": ops,
+                         "units_per_launch": {"areas": areas, "darts": darts, "kept": kept, "passes": passes},
+                         "peak_source": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int32 lanes x "
+                                        f"{sm_max:.0f} MHz (max SM clock)"},
+            "cpu_baseline": None, "e2e": None, "clocks": clocks, "gpu_launches": args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -740,6 +835,8 @@ def main():
         compare_arm(args)
     elif args.workload == "IDX":
         index_arm(args)
+    elif args.workload == "T1":
+        wide_arm(args)
     else:
         gpu_arm(args)
 

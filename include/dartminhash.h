@@ -157,6 +157,24 @@ int dm_lsh_index_destroy(dm_lsh_index *ix);
 int dm_compare(dm_ctx *ctx, const uint64_t *a, const uint64_t *c, int64_t n_a, int64_t n_c, int32_t k,
                int32_t bits, int32_t mode, uint32_t *out, void *stream);
 
+/* Wide-range minhash keys: 64-bit element ids and binary64 weights, for the norms the binary32
+ * entry points cannot reach (Section 4, "Synthetic data", hashes 64-bit ids with double weights;
+ * Table 1 runs ||x||_1 = 2^{+-64} and 2^{+-512}).  Same dart process as dm_sketch (Section 2,
+ * Algorithm 1, Theorem 1), with keys of their own (so they never compare with dm_sketch's):
+ *   - area (nu, rho, w, r) of element i is hashed in two levels, region key
+ *     z = M(e_i + gamma (1 + 2^16 nu + rho)) and area key a = M(z + gamma (1 + 2^32 w + r));
+ *   - a key is (code << 32) | (q mod 2^32), where code is the upper 32 bits of the binary64 pattern
+ *     of the dart's rank rounded toward zero (sign, 11 exponent and 20 fraction bits).
+ * indptr int64[n_sets + 1], indices uint64[nnz], weights float64[nnz]: device arrays, CSR as for
+ * dm_sketch; out: uint64[n_sets * k] device array.  1 <= k <= 1024.  Asynchronous on `stream`.
+ * Errors recorded for dm_sync_status (the set's row then holds all ones): DM_EINVAL for a
+ * negative, NaN or infinite weight; DM_ERANGE for a weight >= 2^960 or a set whose largest weight
+ * is positive and below 2^-990 (both keep every rank and limit a normal binary64 number);
+ * DM_EOVERFLOW after 17 passes of the doubling loop.  A set without a positive weight gets all
+ * ones.  DM_OPT_COUNTERS, when set, accumulates areas, darts, kept darts and passes. */
+int dm_sketch_f64(dm_ctx *ctx, const int64_t *indptr, const uint64_t *indices, const double *weights,
+                  int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream);
+
 /* dm_sketch / dm_sketch_bbit with HOST arrays: indptr, indices, weights, out_keys and
  * out_words are host pointers (page-locked memory gives full copy speed).  b = 0 computes keys
  * only (out_keys required, out_words ignored); b in {1, 2, 4, 8, 16, 32} also writes the b-bit

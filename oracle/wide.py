@@ -187,19 +187,19 @@ def element_darts(index: int, x: float, t: int, sigma: int, theta, T, work=None,
 
 
 def check_row(weights) -> tuple[int, float]:
-    """(status, ||x||_1 as a binary64 sum in row order)."""
-    l1 = 0.0
-    mx = 0.0
-    for x in weights:
-        x = float(x)
-        if not (x >= 0.0) or x == float("inf"):
-            return EINVAL, 0.0
-        if x >= X_MAX:
-            return ERANGE, 0.0
-        l1 += x
-        mx = max(mx, x)
+    """(status, ||x||_1 as a binary64 sum in row order).  An invalid weight anywhere in the row
+    gives EINVAL, before any range check."""
+    ws = [float(x) for x in weights]
+    if any(not (x >= 0.0) or x == float("inf") for x in ws):
+        return EINVAL, 0.0
+    if any(x >= X_MAX for x in ws):
+        return ERANGE, 0.0
+    mx = max(ws, default=0.0)
     if 0.0 < mx < X_MIN_MAX:
         return ERANGE, 0.0
+    l1 = 0.0
+    for x in ws:
+        l1 += x
     return OK, l1
 
 

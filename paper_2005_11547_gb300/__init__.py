@@ -67,6 +67,7 @@ def load(path: str | None = None):
             "dm_lsh_index_destroy": ([P], ctypes.c_int),
             "dm_weight_classes": ([P, P, P, i64, P, P, i32, P], ctypes.c_int),
             "dm_sketch_host": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
+            "dm_sketch_f64": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
             "dm_sync_status": ([P, P], ctypes.c_int),
             "dm_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "dm_set_option": ([P, ctypes.c_int, i64], ctypes.c_int),
@@ -111,7 +112,7 @@ def _dev_ptr(t, dtype_name, what):
     if not t.is_contiguous():
         raise ValueError(f"{what} must be contiguous")
     want = {"int64": (torch.int64,), "int32": (torch.int32,), "uint32": (torch.int32, torch.uint32),
-            "float32": (torch.float32,),
+            "float32": (torch.float32,), "float64": (torch.float64,),
             "uint64": (torch.int64, torch.uint64)}[dtype_name]
     if t.dtype not in want:
         raise TypeError(f"{what} must be {dtype_name} (got {t.dtype})")
@@ -164,6 +165,23 @@ def dm_sketch(ctx: Context, indptr, indices, weights, k: int, seed: int, out=Non
         raise ValueError("out has the wrong size")
     _check(load().dm_sketch(ctx.handle, ip, ix, w, n, int(k), int(seed) & (2**64 - 1),
                             _dev_ptr(out, "uint64", "out"), _stream(stream)), "dm_sketch")
+    return out
+
+
+def dm_sketch_f64(ctx: Context, indptr, indices, weights, k: int, seed: int, out=None, stream=None):
+    """Wide-range minhash keys uint64[n_sets, k] (int64 tensor holding the same bits) of sets with
+    64-bit ids (int64 or uint64 tensor) and binary64 weights (float64 tensor)."""
+    import torch
+    n = indptr.numel() - 1
+    ip = _dev_ptr(indptr, "int64", "indptr")
+    ix = _dev_ptr(indices, "uint64", "indices")
+    w = _dev_ptr(weights, "float64", "weights")
+    if out is None:
+        out = torch.empty((n, k), dtype=torch.int64, device=indptr.device)
+    elif out.numel() != n * k:
+        raise ValueError("out has the wrong size")
+    _check(load().dm_sketch_f64(ctx.handle, ip, ix, w, n, int(k), int(seed) & (2**64 - 1),
+                                _dev_ptr(out, "uint64", "out"), _stream(stream)), "dm_sketch_f64")
     return out
 
 

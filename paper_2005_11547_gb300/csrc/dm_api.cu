@@ -470,7 +470,7 @@ int dm_create(dm_ctx **out, int device, size_t mem_budget_bytes) {
     if ((e = cudaMalloc(&c->d_status, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(c->d_status, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaMallocHost(&c->h_status, sizeof(int))) != cudaSuccess ||
-        (e = dm::upload_poisson_table(T)) != cudaSuccess ||
+        (e = dm::upload_poisson_table(T)) != cudaSuccess || (e = dm::upload_wide_table(T)) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
         dm_destroy(c);
         return cuda_fail(e);
@@ -543,6 +543,28 @@ int dm_bottomk(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, cons
                int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream) {
     return run_sets(ctx, indptr, indices, weights, n_sets, dm::kBottomK, k, 0, 0, seed, nullptr, out, nullptr,
                     (cudaStream_t)stream);
+}
+
+int dm_sketch_f64(dm_ctx *ctx, const int64_t *indptr, const uint64_t *indices, const double *weights,
+                  int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream) {
+    if (!ctx || n_sets < 0 || k < 1 || k > 1024) return DM_EINVAL;
+    if (n_sets == 0) return DM_OK;
+    if (!indptr || !indices || !weights || !out) return DM_EINVAL;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e);
+    dm::WideParams wp;
+    wp.indptr = indptr;
+    wp.indices = indices;
+    wp.weights = weights;
+    wp.n_sets = n_sets;
+    wp.k = k;
+    wp.t = (uint32_t)t_of_k(k);
+    wp.sigma = dm::mix64(seed ^ dm::kSeedSalt);
+    wp.phi0 = (double)ctx->phi0;
+    wp.out = out;
+    wp.status = ctx->d_status;
+    wp.counters = ctx->counters;
+    return cuda_fail(dm::launch_wide(wp, ctx->counters != nullptr, ctx->sm_count, (cudaStream_t)stream));
 }
 
 int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,

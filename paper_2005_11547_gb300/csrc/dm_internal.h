@@ -88,6 +88,23 @@ int large_blocks_per_sm(bool bbit, int warps, size_t smem);
 size_t call_scratch_bytes(int64_t n_sets);
 void carve_call_scratch(void *base, int64_t n_sets, SketchParams &p);
 
+// Wide-range sketches (binary64 weights, 64-bit ids; dm_wide.cu).
+struct WideParams {
+    const int64_t *indptr;
+    const uint64_t *indices;
+    const double *weights;
+    int64_t n_sets;
+    int32_t k;
+    uint32_t t;            // ceil(k ln k) + k
+    uint64_t sigma;        // seed key
+    double phi0;           // initial phi of Theorem 1's loop
+    uint64_t *out;         // n_sets * k keys
+    int *status;
+    unsigned long long *counters;   // optional: areas, darts, kept, passes
+};
+cudaError_t upload_wide_table(const uint32_t *T);
+cudaError_t launch_wide(const WideParams &wp, bool count, int sm_count, cudaStream_t st);
+
 // Serving loop helpers (dm_api.cu).  serve_sketch: one dm_sketch call with the call's scratch at
 // `queue` (call_scratch_bytes(n_sets) bytes), the given launch form and large-set threshold
 // (-1: the context's).  status_to_host queues a

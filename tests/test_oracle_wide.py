@@ -185,6 +185,7 @@ def test_errors_and_sentinels():
     assert wide.sketch_one([1, 2], [0.5, -1.0], 8, 1, T_)[0] == wide.EINVAL
     assert wide.sketch_one([1, 2], [0.5, float("inf")], 8, 1, T_)[0] == wide.EINVAL
     assert wide.sketch_one([1, 2], [0.5, 2.0 ** 960], 8, 1, T_)[0] == wide.ERANGE
+    assert wide.sketch_one([1, 2], [2.0 ** 961, float("nan")], 8, 1, T_)[0] == wide.EINVAL
     assert wide.sketch_one([1, 2], [2.0 ** -991, 5e-324], 8, 1, T_)[0] == wide.ERANGE
     st, out = wide.sketch_one([1, 2], [0.0, 0.0], 8, 1, T_)
     assert st == 0 and out == [wide.EMPTY] * 8
