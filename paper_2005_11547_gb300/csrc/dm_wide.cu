@@ -52,6 +52,13 @@ DM_HD inline int clz64(uint64_t x) {
 #endif
 }
 DM_HD inline int wbitlen64(uint64_t x) { return x ? 64 - clz64(x) : 0; }
+DM_HD inline int ctz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+    return __ffsll((long long)x) - 1;
+#else
+    return __builtin_ctzll(x);
+#endif
+}
 DM_HD inline int bitlen128(u128 x) {
     const uint64_t hi = (uint64_t)(x >> 64), lo = (uint64_t)x;
     return hi ? 128 - clz64(hi) : wbitlen64(lo);
@@ -110,6 +117,27 @@ DM_HD uint64_t dy_ceil(const Dy &v, int s) {
     if (v.tiny && v.et + s < 0) frac = true;
     return frac ? f + 1 : f;
 }
+
+// Bit of weight 2^-j (j >= 1) of v.
+DM_HD inline uint32_t dy_bit(const Dy &v, int j) {
+    const int i = -j - v.ez;
+    uint32_t b = (i >= 0 && i < 128) ? (uint32_t)(v.Z >> i) & 1u : 0u;
+    if (v.tiny && v.et == -j) b = 1u;
+    return b;
+}
+
+// Exponent of the lowest set bit of v > 0.
+DM_HD inline int dy_lsb(const Dy &v) {
+    if (v.tiny) return v.et;
+    const uint64_t lo = (uint64_t)v.Z;
+    return v.ez + (lo ? ctz64(lo) : 64 + ctz64((uint64_t)(v.Z >> 64)));
+}
+
+// Running floors floor(v 2^s) for s = s0, s0 + 1, ... are doubled and given the next bit; they
+// saturate here (every value from 2^56 on is out of range for its use).
+constexpr uint64_t kBig = 1ull << 60;
+DM_HD inline uint64_t dbl(uint64_t R, uint32_t b) { return R >= kBig ? kBig : 2 * R + b; }
+DM_HD inline uint64_t capped(uint64_t R) { return R >= kBig ? kBig : R; }
 
 // Weight geometry of x > 0 (binary64 bits xb): y = t x, nu_top = floor(log2(1 + y)) (Algorithm
 // 1's last weight region) and f with y = 2^nu_top - 1 + f 2^nu_top, 0 <= f < 1.
@@ -213,16 +241,22 @@ DM_HD uint32_t wide_code(uint64_t P, int rho, int nu) {
 // Limits of one pass: rows and regions below the previous limit are skipped (band).
 struct WideCut {
     int rho_lo, rho_top;
-    Dy G, Gp;          // of theta_p and theta_{p-1} (Gp = 0 on the first pass)
+    Dy G, Gp;          // of theta_p and theta_{p-1} (Gp = 0 on the first pass; Gp < 1)
+    uint64_t RG0;      // floor(G 2^24)
+    int lsbG;          // G 2^s is an integer iff lsbG >= -s
 };
 
 // One lane's walk over the areas of its elements (positions first, first + 32, ... < end).
+// Per element, the walk keeps three running floors instead of re-deriving each region's bounds:
+// RG = floor(G 2^(nu+24)) (rows and row limits of region rho_top), RP = floor(Gp 2^nu) (first row
+// of the band in region rho_lo) and, in region nu_top, Fv = floor(f 2^(rho+24)) (columns and the
+// last column's v limit).
 struct WideWalk {
     int64_t p, end;
     uint64_t e;
     Dy f;
     int nu_top, nu, rho;
-    uint64_t w, ncols, r, r0, r1, z, ctr, Q;
+    uint64_t w, ncols, r, r0, r1, z, ctr, Q, RG, RP, Fv;
     uint32_t vtop;
     bool top;
 
@@ -235,6 +269,9 @@ struct WideWalk {
                 e = mix64(wp.sigma + kGolden * (wp.indices[p] + 1));
                 nu = 0;
                 rho = cut.rho_lo;
+                RG = cut.RG0;
+                RP = 0;
+                if (nu_top == 0) Fv = capped(dy_floor(f, rho + 24));
                 return true;
             }
         }
@@ -243,21 +280,20 @@ struct WideWalk {
     // enter region (nu, rho) at its first area; returns 0 or DM_ERANGE
     DM_HD int region(const WideCut &cut) {
         if (nu == nu_top) {
-            const uint64_t wm = dy_floor(f, rho);
-            if (wm >= (1ull << 32)) return DM_ERANGE;
-            vtop = (uint32_t)(dy_floor(f, rho + 24) - (wm << 24));
-            ncols = wm + 1;
+            if (Fv >= (1ull << 56)) return DM_ERANGE;           // a column index 2^32
+            vtop = (uint32_t)Fv & kUMask;
+            ncols = (Fv >> 24) + 1;
         } else {
             if (rho > 32) return DM_ERANGE;
             ncols = 1ull << rho;
             vtop = kUMask;
         }
         top = rho == cut.rho_top;
-        r0 = rho == cut.rho_lo ? dy_floor(cut.Gp, nu) : 0;
+        r0 = rho == cut.rho_lo ? RP : 0;
         if (top) {
-            r1 = dy_ceil(cut.G, nu);
+            r1 = (RG >> 24) + (cut.lsbG < -nu ? 1 : 0);           // ceil(G 2^nu)
             if (r1 > (1ull << 32)) return DM_ERANGE;
-            Q = dy_ceil(cut.G, nu + 24);
+            Q = RG + (cut.lsbG < -(nu + 24) ? 1 : 0);             // ceil(G 2^(nu+24))
         } else {
             if (nu > 32) return DM_ERANGE;
             r1 = 1ull << nu;
@@ -289,7 +325,13 @@ struct WideWalk {
             if (++nu > nu_top) {
                 p += 32;
                 if (!element(wp, cut)) return false;
+            } else {
+                RG = dbl(RG, dy_bit(cut.G, nu + 24));
+                RP = dbl(RP, dy_bit(cut.Gp, nu));
+                if (nu == nu_top) Fv = capped(dy_floor(f, rho + 24));
             }
+        } else if (nu == nu_top) {
+            Fv = dbl(Fv, dy_bit(f, rho + 24));
         }
         err = region(cut);
         return err == 0;
@@ -388,6 +430,8 @@ __global__ void __launch_bounds__(32 * kWarps) wide_kernel(WideParams wp) {
                     break;
                 }
                 wide_pass_cut(c, cut.rho_top, cut.G);
+                cut.RG0 = capped(dy_floor(cut.G, 24));
+                cut.lsbG = dy_lsb(cut.G);
                 err = wide_walk<COUNT>(wp, beg, end, cut, slots, lane, cnt);
                 if (COUNT && lane == 0) cnt[3]++;
                 __syncwarp();
