@@ -752,7 +752,7 @@ def wide_arm(args):
     dmx.build()
     dmx.load()
     props = torch.cuda.get_device_properties(local)
-    per, nnz, k = args.sets or 4000, 1024, K_SLOTS
+    per, nnz, k = args.sets or 8000, 1024, K_SLOTS
     parts = [workloads.table1_batch(per, nnz, l1, 700 + i + 16 * rank) for i, (_, l1) in enumerate(T1_NORMS)]
     ip = torch.from_numpy(np.concatenate([[0]] + [p.indptr[1:] + nnz * per * i for i, p in enumerate(parts)])).cuda()
     ix = torch.from_numpy(np.concatenate([p.indices for p in parts]).view(np.int64)).cuda()

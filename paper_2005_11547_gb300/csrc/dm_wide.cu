@@ -388,7 +388,7 @@ __device__ int wide_walk(const WideParams &wp, int64_t beg, int64_t end, const W
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(32 * kWarps) wide_kernel(WideParams wp) {
+__global__ void __launch_bounds__(32 * kWarps, 6) wide_kernel(WideParams wp) {
     extern __shared__ unsigned long long wide_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long *slots = wide_smem + (size_t)wid * wp.k;
