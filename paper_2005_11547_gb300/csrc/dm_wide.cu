@@ -107,17 +107,6 @@ DM_HD uint64_t dy_floor(const Dy &v, int s) {
     return ip;
 }
 
-// ceil(v 2^s), saturated
-DM_HD uint64_t dy_ceil(const Dy &v, int s) {
-    const uint64_t f = dy_floor(v, s);
-    if (f == kSat) return kSat;
-    const int a = v.ez + s;
-    bool frac = false;
-    if (a < 0) frac = -a >= 128 ? v.Z != 0 : (v.Z & (((u128)1 << -a) - 1)) != 0;
-    if (v.tiny && v.et + s < 0) frac = true;
-    return frac ? f + 1 : f;
-}
-
 // Bit of weight 2^-j (j >= 1) of v.
 DM_HD inline uint32_t dy_bit(const Dy &v, int j) {
     const int i = -j - v.ez;
