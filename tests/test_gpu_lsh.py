@@ -39,7 +39,8 @@ def gpu_lsh(dmx, torch, ctx, b, L, K, seed):
     return out.cpu().numpy().view(np.uint32), rc
 
 
-@pytest.mark.parametrize("L,K", [(1, 1), (8, 2), (16, 4), (64, 8), (33, 3), (100, 5), (7, 16)])
+@pytest.mark.parametrize("L,K", [(1, 1), (8, 2), (16, 4), (64, 8), (33, 3), (100, 5), (7, 16), (1024, 2),
+                                 (700, 32)])
 def test_lsh_parity_random_sets(dmx, torch_mod, ctx, oracle_mod, L, K):
     """Ragged sets with ||x||_1 over six decades (both kernels), several (L, K)."""
     b = workloads.random_sets(200, 0, 200, 1 << 24, seed=100 + L + K)

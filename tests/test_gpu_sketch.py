@@ -74,6 +74,26 @@ def test_ragged_sets_parity(dmx, torch_mod, ctx, oracle_mod, k):
     assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 12345, threads=THREADS), f"k={k}")
 
 
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_largest_k_parity(dmx, torch_mod, oracle_mod, form):
+    """The largest bucket counts the library takes (k up to 8,192: 64 KB of buckets per set),
+    keys and 1-bit words, in every launch form."""
+    b = workloads.random_sets(40, 0, 300, 1 << 24, seed=77)
+    c = dmx.dm_create(0)
+    dmx.dm_set_option(c, dmx.OPT_FORM, form)
+    ip, ix, w = to_dev(torch_mod, b)
+    for k in (4097, 8192):
+        got, rc = gpu_sketch(dmx, torch_mod, c, b, k, 4242)
+        assert rc == 0
+        exp = oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 4242, threads=THREADS)
+        assert_same(got, exp, f"k={k} form={form}")
+    words = dmx.dm_sketch_bbit(c, ip, ix, w, 8192, 1, 4242)
+    assert dmx.dm_sync_status(c, raise_on_error=False) == 0
+    ew = oracle_mod.sketch_bbit(b.indptr, b.indices, b.weights, 8192, 1, 4242, threads=THREADS)
+    assert np.array_equal(words.cpu().numpy().view(np.uint64), ew)
+    c.close()
+
+
 def test_extreme_norms_parity(dmx, torch_mod, ctx, oracle_mod):
     """||x||_1 from 1e-6 to 1e6: many rank regions (small norms) or many weight regions."""
     rows = []

@@ -57,7 +57,7 @@ def varied_batch(seed):
     return workloads.wide_csr(rows)
 
 
-@pytest.mark.parametrize("k", [1, 7, 64, 256, 1000])
+@pytest.mark.parametrize("k", [1, 7, 64, 256, 1000, 1024])
 def test_varied_sets_match_oracle(dmx, torch_mod, k):
     from oracle import wide
     b = varied_batch(100 + k)
