@@ -73,26 +73,38 @@ DM_HD inline uint64_t bits_of(double x) {
 #endif
 }
 
+DM_HD inline int bitlen_of(u128 x) { return bitlen128(x); }
+DM_HD inline int bitlen_of(uint64_t x) { return wbitlen64(x); }
+DM_HD inline int ctz_of(uint64_t x) { return ctz64(x); }
+
 // A dyadic value Z 2^ez, plus 2^et when `tiny` is set.  The tiny term always lies below the
 // lowest bit of Z 2^ez (et < ez), so it never carries into the integer part at any scale.
-struct Dy {
-    u128 Z;
+// Weight positions need a 128-bit Z; rank fractions fit a 64-bit one.
+template <class T>
+struct DyT {
+    T Z;
     int ez, et;
     bool tiny;
 };
+using Dy = DyT<u128>;
+using Dy64 = DyT<uint64_t>;
 
 // floor(v 2^s), saturated at 2^64 - 1
-DM_HD uint64_t dy_floor(const Dy &v, int s) {
+template <class T>
+DM_HD uint64_t dy_floor(const DyT<T> &v, int s) {
+    constexpr int W = 8 * (int)sizeof(T);
     const int a = v.ez + s;
     uint64_t ip;
     if (v.Z == 0) {
         ip = 0;
     } else if (a >= 0) {
-        if (bitlen128(v.Z) + a > 64) return kSat;
+        if (bitlen_of(v.Z) + a > 64) return kSat;
         ip = (uint64_t)(v.Z << a);
     } else {
-        const u128 q = -a >= 128 ? (u128)0 : (v.Z >> -a);
-        if ((uint64_t)(q >> 64) != 0) return kSat;
+        const T q = -a >= W ? (T)0 : (T)(v.Z >> -a);
+        if constexpr (sizeof(T) > 8) {
+            if ((uint64_t)(q >> 64) != 0) return kSat;
+        }
         ip = (uint64_t)q;
     }
     if (v.tiny) {
@@ -108,18 +120,19 @@ DM_HD uint64_t dy_floor(const Dy &v, int s) {
 }
 
 // Bit of weight 2^-j (j >= 1) of v.
-DM_HD inline uint32_t dy_bit(const Dy &v, int j) {
+template <class T>
+DM_HD inline uint32_t dy_bit(const DyT<T> &v, int j) {
+    constexpr int W = 8 * (int)sizeof(T);
     const int i = -j - v.ez;
-    uint32_t b = (i >= 0 && i < 128) ? (uint32_t)(v.Z >> i) & 1u : 0u;
+    uint32_t b = (i >= 0 && i < W) ? (uint32_t)(v.Z >> i) & 1u : 0u;
     if (v.tiny && v.et == -j) b = 1u;
     return b;
 }
 
 // Exponent of the lowest set bit of v > 0.
-DM_HD inline int dy_lsb(const Dy &v) {
-    if (v.tiny) return v.et;
-    const uint64_t lo = (uint64_t)v.Z;
-    return v.ez + (lo ? ctz64(lo) : 64 + ctz64((uint64_t)(v.Z >> 64)));
+template <class T>
+DM_HD inline int dy_lsb(const DyT<T> &v) {
+    return v.tiny ? v.et : v.ez + ctz_of(v.Z);
 }
 
 // Running floors floor(v 2^s) for s = s0, s0 + 1, ... are doubled and given the next bit; they
@@ -172,7 +185,7 @@ DM_HD int wide_geometry(uint64_t xb, uint32_t t, Dy &f) {
 
 // Rank geometry of a limit with code c: rho_top = max{rho : 2^rho - 1 < theta} and the fraction
 // G = (theta + 1 - 2^rho_top) / 2^rho_top in (0, 1] of region rho_top below theta.
-DM_HD void wide_pass_cut(uint32_t c, int &rho_top, Dy &G) {
+DM_HD void wide_pass_cut(uint32_t c, int &rho_top, Dy64 &G) {
     const int E = (int)(c >> 20) - 1023;
     const uint64_t Mt = (1ull << 20) | (c & 0xFFFFFu);  // theta = Mt 2^(E - 20)
     G.tiny = false;
@@ -230,7 +243,7 @@ DM_HD uint32_t wide_code(uint64_t P, int rho, int nu) {
 // Limits of one pass: rows and regions below the previous limit are skipped (band).
 struct WideCut {
     int rho_lo, rho_top;
-    Dy G, Gp;          // of theta_p and theta_{p-1} (Gp = 0 on the first pass; Gp < 1)
+    Dy64 G, Gp;        // of theta_p and theta_{p-1} (Gp = 0 on the first pass; Gp < 1)
     uint64_t RG0;      // floor(G 2^24)
     int lsbG;          // G 2^s is an integer iff lsbG >= -s
 };
@@ -337,10 +350,9 @@ __device__ int wide_walk(const WideParams &wp, int64_t beg, int64_t end, const W
     bool live = s.start(wp, cut, err), fresh = true;
     uint32_t nx = 0, uthr = 0, vmax = 0;
     uint64_t c = 0;
-    for (;;) {
-        const unsigned bad = __ballot_sync(kFull, err != 0);
-        if (bad) return __shfl_sync(kFull, err, __ffs(bad) - 1);
-        if (!__any_sync(kFull, live || nx)) return 0;
+    // A lane that meets a range error stops (its walk returns false); the others finish the
+    // pass, whose buckets are then discarded.
+    while (__any_sync(kFull, live || nx)) {
         if (nx == 0 && live) {
             if (!fresh) live = s.advance(wp, cut, err);
             fresh = false;
@@ -374,6 +386,8 @@ __device__ int wide_walk(const WideParams &wp, int64_t beg, int64_t end, const W
             }
         }
     }
+    const unsigned bad = __ballot_sync(kFull, err != 0);
+    return bad ? __shfl_sync(kFull, err, __ffs(bad) - 1) : 0;
 }
 
 template <bool COUNT>
@@ -412,7 +426,7 @@ __global__ void __launch_bounds__(32 * kWarps, 6) wide_kernel(WideParams wp) {
             uint32_t c = (uint32_t)(bits_of(wp.phi0 / l1) >> 32);
             WideCut cut;
             cut.rho_lo = 0;
-            cut.Gp = Dy{0, 0, 0, false};
+            cut.Gp = Dy64{0, 0, 0, false};
             for (int pass = 0;; ++pass) {
                 if (pass == kPasses) {
                     err = DM_EOVERFLOW;
@@ -429,10 +443,10 @@ __global__ void __launch_bounds__(32 * kWarps, 6) wide_kernel(WideParams wp) {
                 for (int j = lane; j < wp.k; j += 32) empty |= slots[j] == ~0ull;
                 if (!__any_sync(kFull, empty)) break;
                 // the next band starts where this limit ended
-                const bool one = !cut.G.tiny && cut.G.ez < 0 && cut.G.ez > -128 &&
-                                 cut.G.Z == ((u128)1 << -cut.G.ez);                  // G == 1
+                const bool one = !cut.G.tiny && cut.G.ez < 0 && cut.G.ez > -64 &&
+                                 cut.G.Z == (1ull << -cut.G.ez);                     // G == 1
                 cut.rho_lo = one ? cut.rho_top + 1 : cut.rho_top;
-                cut.Gp = one ? Dy{0, 0, 0, false} : cut.G;
+                cut.Gp = one ? Dy64{0, 0, 0, false} : cut.G;
                 c += 1u << 20;
             }
         }
