@@ -188,6 +188,23 @@ def ncu_traffic_per_set():
     return d.get("dram_bytes_per_set")
 
 
+def mix_ceiling(dmx, props, peak_ops, stream):
+    """What pure hashing reaches: SplitMix64 chains alone (dm_mix64_burn, full occupancy), in the
+    same op count per mix as the roofline's work model, against the same peak."""
+    import torch
+    blocks, iters = props.multi_processor_count * 8, 20000
+    out = dmx.dm_mix64_burn(blocks, 100, stream=stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    dmx.dm_mix64_burn(blocks, iters, out=out, stream=stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    s = ev[0].elapsed_time(ev[1]) / 1e3
+    mixes = 4 * iters * 256 * blocks
+    return {"kernel": "dm_mix64_burn", "mix64_per_s": mixes / s, "gop_per_s": mixes * OPS_MIX / s / 1e9,
+            "frac_of_peak": mixes * OPS_MIX / s / peak_ops}
+
+
 # ------------------------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline leg and the reference arm)
 # ------------------------------------------------------------------------------------------
@@ -420,7 +437,8 @@ def gpu_arm(args):
                 "hbm_gbs_algorithmic": (b.indptr.nbytes + b.indices.nbytes + b.weights.nbytes
                                         + out_bytes) / mean_launch_s / 1e9,
                 "peak_source": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int32 lanes x "
-                               f"{sm_max:.0f} MHz (max SM clock)"}
+                               f"{sm_max:.0f} MHz (max SM clock)",
+                "peak_check": mix_ceiling(dmx, props, peak_ops, stream)}
 
     cpu_baseline = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and wl == "W1":

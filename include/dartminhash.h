@@ -175,6 +175,13 @@ int dm_compare(dm_ctx *ctx, const uint64_t *a, const uint64_t *c, int64_t n_a, i
 int dm_sketch_f64(dm_ctx *ctx, const int64_t *indptr, const uint64_t *indices, const double *weights,
                   int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream);
 
+/* Measurement helper (no paper counterpart): the integer-issue ceiling of the counter-based hash.
+ * Launches `blocks` blocks of 256 threads; each thread applies SplitMix64's output function
+ * 4 * iters times (four independent chains) and writes the xor of its chains to out[thread]
+ * (device uint64[blocks * 256]).  Asynchronous on `stream`: time it with events on that stream.
+ * 4 * iters * 256 * blocks mixes, 18 int32 operations each, against SMs x 128 lanes x clock. */
+int dm_mix64_burn(int64_t blocks, int32_t iters, uint64_t seed, uint64_t *out, void *stream);
+
 /* dm_sketch / dm_sketch_bbit with HOST arrays: indptr, indices, weights, out_keys and
  * out_words are host pointers (page-locked memory gives full copy speed).  b = 0 computes keys
  * only (out_keys required, out_words ignored); b in {1, 2, 4, 8, 16, 32} also writes the b-bit

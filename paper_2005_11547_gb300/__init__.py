@@ -68,6 +68,7 @@ def load(path: str | None = None):
             "dm_weight_classes": ([P, P, P, i64, P, P, i32, P], ctypes.c_int),
             "dm_sketch_host": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_sketch_f64": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
+            "dm_mix64_burn": ([i64, i32, u64, P, P], ctypes.c_int),
             "dm_sync_status": ([P, P], ctypes.c_int),
             "dm_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "dm_set_option": ([P, ctypes.c_int, i64], ctypes.c_int),
@@ -182,6 +183,17 @@ def dm_sketch_f64(ctx: Context, indptr, indices, weights, k: int, seed: int, out
         raise ValueError("out has the wrong size")
     _check(load().dm_sketch_f64(ctx.handle, ip, ix, w, n, int(k), int(seed) & (2**64 - 1),
                                 _dev_ptr(out, "uint64", "out"), _stream(stream)), "dm_sketch_f64")
+    return out
+
+
+def dm_mix64_burn(blocks: int, iters: int, seed: int = 1, out=None, stream=None):
+    """The hash's integer-issue ceiling: 4 * iters chained mixes per thread, blocks * 256 threads
+    (see the C declaration).  Returns the output tensor (int64[blocks * 256])."""
+    import torch
+    if out is None:
+        out = torch.empty(blocks * 256, dtype=torch.int64, device="cuda")
+    _check(load().dm_mix64_burn(int(blocks), int(iters), int(seed) & (2**64 - 1), _dev_ptr(out, "uint64", "out"),
+                                _stream(stream)), "dm_mix64_burn")
     return out
 
 
