@@ -244,10 +244,13 @@ enum dm_option {
     DM_OPT_TUNED = 8,           /* 1 (default): calls use the settings dm_autotune stored for their
                                    (kind, k, K, b), in place of the options above; 0: ignore them;
                                    2: forget them */
-    DM_OPT_LARGE_WORK = 9       /* batched form: a set whose Lemma 2 estimate of the areas it
+    DM_OPT_LARGE_WORK = 9,      /* batched form: a set whose Lemma 2 estimate of the areas it
                                    inspects (phi0 t + sum_i (log2(1 + t x_i) + 1) +
                                    nnz log2(1 + phi0/|x|_1)) reaches this value also gets a block of
                                    8 warps (default 0 = never; dm_lsh never does) */
+    DM_OPT_HOST_CHUNKS = 10     /* dm_sketch_host: number of chunks (1..256, default 8) a batch is
+                                   split into, so that one chunk's copies overlap another's kernels
+                                   (chunks hold at least 4,096 sets) */
 };
 int dm_set_option(dm_ctx *ctx, int option, int64_t value);
 

@@ -66,6 +66,7 @@ struct dm_ctx {
     int warps_per_block = 0;       // 0 = automatic
     int large_nnz = 2048;          // batched form: sets with this many elements get a block
     float large_work = 0.f;        // batched form: sets with this work estimate get a block
+    int host_chunks = 8;           // host-buffer entry: chunks a batch is split into
     // staging for the host-buffer entry points
     void *d_stage = nullptr;
     size_t d_stage_bytes = 0;
@@ -581,14 +582,28 @@ int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
     if (e != cudaSuccess) return cuda_fail(e);
     if (indptr[0] != 0 || indptr[n_sets] < 0) return DM_EINVAL;
     const int64_t words = b > 0 ? ((int64_t)k * b + 63) / 64 : 0;
-    // chunks of about 1/8 of the batch (at least 16k sets), two buffer sets in flight
-    int64_t cs = (n_sets + 7) / 8;
-    if (cs < 16384) cs = 16384;
+    // chunks of about 1/host_chunks of the batch (at least 4,096 sets), two buffer sets in flight;
+    // the first two and the last two chunks are a quarter and a half of that, so that the copy
+    // in before the first kernel and the copy out after the last one stay short
+    int64_t cs = (n_sets + ctx->host_chunks - 1) / ctx->host_chunks;
+    if (cs < 4096) cs = 4096;
     if (cs > n_sets) cs = n_sets;
+    std::vector<int64_t> bounds{0};
+    if (n_sets >= 4 * cs && cs / 4 >= 4096) {
+        bounds.push_back(cs / 4);
+        bounds.push_back(cs / 4 + cs / 2);
+        const int64_t end_mid = n_sets - cs / 2 - cs / 4, mid = end_mid - bounds.back();
+        const int64_t nm = (mid + cs - 1) / cs;
+        for (int64_t i = 1; i <= nm; ++i) bounds.push_back(bounds[2] + mid * i / nm);
+        bounds.push_back(n_sets - cs / 4);
+        bounds.push_back(n_sets);
+    } else {
+        for (int64_t s0 = cs; s0 < n_sets; s0 += cs) bounds.push_back(s0);
+        bounds.push_back(n_sets);
+    }
     int64_t max_nnz = 0;
-    for (int64_t s0 = 0; s0 < n_sets; s0 += cs) {
-        int64_t s1 = s0 + cs < n_sets ? s0 + cs : n_sets;
-        int64_t z = indptr[s1] - indptr[s0];
+    for (size_t i = 0; i + 1 < bounds.size(); ++i) {
+        const int64_t z = indptr[bounds[i + 1]] - indptr[bounds[i]];
         if (z < 0) return DM_EINVAL;
         if (z > max_nnz) max_nnz = z;
     }
@@ -617,9 +632,8 @@ int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
     if ((e = cudaEventRecord(ctx->ev_start, st)) != cudaSuccess) return cuda_fail(e);
     for (int i = 0; i < 2; ++i)
         if ((e = cudaStreamWaitEvent(ctx->copy_stream[i], ctx->ev_start, 0)) != cudaSuccess) return cuda_fail(e);
-    int chunk = 0;
-    for (int64_t s0 = 0; s0 < n_sets; s0 += cs, ++chunk) {
-        const int64_t s1 = s0 + cs < n_sets ? s0 + cs : n_sets, n = s1 - s0;
+    for (int chunk = 0; chunk + 1 < (int)bounds.size(); ++chunk) {
+        const int64_t s0 = bounds[chunk], s1 = bounds[chunk + 1], n = s1 - s0;
         const int64_t z0 = indptr[s0], z = indptr[s1] - z0;
         cudaStream_t cst = ctx->copy_stream[chunk & 1];
         char *base = (char *)ctx->d_stage + (size_t)(chunk & 1) * per;
@@ -824,6 +838,10 @@ int dm_set_option(dm_ctx *ctx, int option, int64_t value) {
         case DM_OPT_LARGE_WORK:
             if (value < 0 || value > (1ll << 40)) return DM_EINVAL;
             ctx->large_work = (float)value;
+            return DM_OK;
+        case DM_OPT_HOST_CHUNKS:
+            if (value < 1 || value > 256) return DM_EINVAL;
+            ctx->host_chunks = (int)value;
             return DM_OK;
         case DM_OPT_LSH_PHI0:
             if (value < 1 || value > 1024 * 1024) return DM_EINVAL;
