@@ -175,6 +175,14 @@ int dm_compare(dm_ctx *ctx, const uint64_t *a, const uint64_t *c, int64_t n_a, i
 int dm_sketch_f64(dm_ctx *ctx, const int64_t *indptr, const uint64_t *indices, const double *weights,
                   int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream);
 
+/* b-bit sketches of the wide-range keys: the words dm_sketch_bbit would write for these keys
+ * (b in {1, 2, 4, 8, 16, 32}; out_words uint64[n_sets * ceil(k b / 64)], same layout).  b = 0
+ * writes keys only.  out_keys (may be NULL when b > 0) receives the keys of dm_sketch_f64.  The
+ * rows of sets with an error hold 0xFF bytes, in both outputs. */
+int dm_sketch_f64_bbit(dm_ctx *ctx, const int64_t *indptr, const uint64_t *indices, const double *weights,
+                       int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_words, uint64_t *out_keys,
+                       void *stream);
+
 /* Measurement helper (no paper counterpart): the integer-issue ceiling of the counter-based hash.
  * Launches `blocks` blocks of 256 threads; each thread applies SplitMix64's output function
  * 4 * iters times (four independent chains) and writes the xor of its chains to out[thread]

@@ -293,3 +293,29 @@ def _code_of_fraction(v) -> int:
     top = int(v / Fraction(2) ** (E - 20))
     assert (1 << 20) <= top < (1 << 21)
     return ((E + 1023) << 20) | (top - (1 << 20))
+
+
+# ------------------------------------------------------------------------------------------
+# b-bit minhash (Section 1.1, "Similarity estimation") of the wide-range keys
+# ------------------------------------------------------------------------------------------
+BBIT_SALT = 0xA4093822299F31D0
+
+
+def sketch_bbit(indptr, indices, weights, k: int, b: int, seed: int, phi0: float = 1.0):
+    """(words uint64[n, ceil(k b / 64)], keys uint64[n, k], status): each minhash is mapped to
+    the low b bits of M(key xor BBIT_SALT); slot j sits at bit (j b) mod 64 of word
+    floor(j b / 64), least significant bit first.  Rows of sets with an error are all ones."""
+    assert b in (1, 2, 4, 8, 16, 32)
+    keys, status = sketch(indptr, indices, weights, k, seed, phi0)
+    n, W = len(indptr) - 1, (k * b + 63) // 64
+    words = np.zeros((n, W), dtype=np.uint64)
+    for s in range(n):
+        if status[s]:
+            words[s] = np.uint64(MASK)
+            continue
+        row = [0] * W
+        for j in range(k):
+            beta = mix64(int(keys[s, j]) ^ BBIT_SALT) & ((1 << b) - 1)
+            row[(j * b) // 64] |= beta << ((j * b) % 64)
+        words[s] = np.array(row, dtype=np.uint64)
+    return words, keys, status

@@ -68,6 +68,7 @@ def load(path: str | None = None):
             "dm_weight_classes": ([P, P, P, i64, P, P, i32, P], ctypes.c_int),
             "dm_sketch_host": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_sketch_f64": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
+            "dm_sketch_f64_bbit": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_mix64_burn": ([i64, i32, u64, P, P], ctypes.c_int),
             "dm_sync_status": ([P, P], ctypes.c_int),
             "dm_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -184,6 +185,25 @@ def dm_sketch_f64(ctx: Context, indptr, indices, weights, k: int, seed: int, out
     _check(load().dm_sketch_f64(ctx.handle, ip, ix, w, n, int(k), int(seed) & (2**64 - 1),
                                 _dev_ptr(out, "uint64", "out"), _stream(stream)), "dm_sketch_f64")
     return out
+
+
+def dm_sketch_f64_bbit(ctx: Context, indptr, indices, weights, k: int, b: int, seed: int, out_words=None,
+                       out_keys=None, stream=None):
+    """b-bit words uint64[n_sets, ceil(k b / 64)] (int64 tensor) of the wide-range keys; fills
+    out_keys too when given."""
+    import torch
+    n = indptr.numel() - 1
+    ip = _dev_ptr(indptr, "int64", "indptr")
+    ix = _dev_ptr(indices, "uint64", "indices")
+    w = _dev_ptr(weights, "float64", "weights")
+    words = (k * b + 63) // 64
+    if out_words is None:
+        out_words = torch.empty((n, words), dtype=torch.int64, device=indptr.device)
+    kp = _dev_ptr(out_keys, "uint64", "out_keys") if out_keys is not None else None
+    _check(load().dm_sketch_f64_bbit(ctx.handle, ip, ix, w, n, int(k), int(b), int(seed) & (2**64 - 1),
+                                     _dev_ptr(out_words, "uint64", "out_words"), kp, _stream(stream)),
+           "dm_sketch_f64_bbit")
+    return out_words
 
 
 def dm_mix64_burn(blocks: int, iters: int, seed: int = 1, out=None, stream=None):

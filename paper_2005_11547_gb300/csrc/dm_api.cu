@@ -548,9 +548,18 @@ int dm_bottomk(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, cons
 
 int dm_sketch_f64(dm_ctx *ctx, const int64_t *indptr, const uint64_t *indices, const double *weights,
                   int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream) {
+    if (!out && n_sets > 0) return DM_EINVAL;
+    return dm_sketch_f64_bbit(ctx, indptr, indices, weights, n_sets, k, 0, seed, nullptr, out, stream);
+}
+
+int dm_sketch_f64_bbit(dm_ctx *ctx, const int64_t *indptr, const uint64_t *indices, const double *weights,
+                       int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_words, uint64_t *out_keys,
+                       void *stream) {
     if (!ctx || n_sets < 0 || k < 1 || k > 1024) return DM_EINVAL;
+    if (!(b == 0 || b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32)) return DM_EINVAL;
     if (n_sets == 0) return DM_OK;
-    if (!indptr || !indices || !weights || !out) return DM_EINVAL;
+    if (!indptr || !indices || !weights || (b == 0 && !out_keys) || (b > 0 && !out_words)) return DM_EINVAL;
+    uint64_t *out = out_keys;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e);
     dm::WideParams wp;
@@ -563,6 +572,9 @@ int dm_sketch_f64(dm_ctx *ctx, const int64_t *indptr, const uint64_t *indices, c
     wp.sigma = dm::mix64(seed ^ dm::kSeedSalt);
     wp.phi0 = (double)ctx->phi0;
     wp.out = out;
+    wp.out_words = b > 0 ? out_words : nullptr;
+    wp.b = b;
+    wp.words = b > 0 ? (int32_t)(((int64_t)k * b + 63) / 64) : 0;
     wp.status = ctx->d_status;
     wp.counters = ctx->counters;
     return cuda_fail(dm::launch_wide(wp, ctx->counters != nullptr, ctx->sm_count, (cudaStream_t)stream));

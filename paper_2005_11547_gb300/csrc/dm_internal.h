@@ -98,7 +98,9 @@ struct WideParams {
     uint32_t t;            // ceil(k ln k) + k
     uint64_t sigma;        // seed key
     double phi0;           // initial phi of Theorem 1's loop
-    uint64_t *out;         // n_sets * k keys
+    uint64_t *out;         // n_sets * k keys (may be null when out_words is set)
+    uint64_t *out_words;   // optional b-bit words, n_sets * words
+    int32_t b, words;      // b-bit width and words per set (0 without out_words)
     int *status;
     unsigned long long *counters;   // optional: areas, darts, kept, passes
 };

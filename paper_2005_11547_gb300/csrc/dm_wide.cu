@@ -451,8 +451,35 @@ __global__ void __launch_bounds__(32 * kWarps, 6) wide_kernel(WideParams wp) {
             }
         }
         if (err && lane == 0) dm::set_status(wp.status, err);
-        uint64_t *o = wp.out + set * (int64_t)wp.k;
-        for (int j = lane; j < wp.k; j += 32) o[j] = err ? ~0ull : slots[j];
+        if (wp.out) {
+            uint64_t *o = wp.out + set * (int64_t)wp.k;
+            for (int j = lane; j < wp.k; j += 32) o[j] = err ? ~0ull : slots[j];
+        }
+        if (wp.out_words) {
+            // b-bit values (Section 1.1): low b bits of the mixed key, slot j at bit j b
+            uint64_t *ow = wp.out_words + set * (int64_t)wp.words;
+            const uint32_t k = (uint32_t)wp.k, b = (uint32_t)wp.b;
+            if (err) {
+                for (int wd = lane; wd < wp.words; wd += 32) ow[wd] = ~0ull;
+            } else if (b == 1) {
+                for (uint32_t j0 = 0; j0 < k; j0 += 64) {
+                    const uint32_t j1 = j0 + lane, j2 = j0 + 32 + lane;
+                    const bool b1 = j1 < k && (mix64(slots[j1] ^ kBbitSalt) & 1);
+                    const bool b2 = j2 < k && (mix64(slots[j2] ^ kBbitSalt) & 1);
+                    const unsigned lo = __ballot_sync(kFull, b1), hi = __ballot_sync(kFull, b2);
+                    if (lane == 0) ow[j0 >> 6] = (uint64_t)lo | ((uint64_t)hi << 32);
+                }
+            } else {
+                const uint32_t g = 64u / b;                 // slots per word, 2..32
+                const uint64_t mask = (1ull << b) - 1;
+                for (uint32_t j0 = 0; j0 < k; j0 += 32) {
+                    const uint32_t j = j0 + lane;
+                    uint64_t v = j < k ? (mix64(slots[j] ^ kBbitSalt) & mask) << ((j * b) & 63) : 0ull;
+                    for (uint32_t o = 1; o < g; o <<= 1) v |= __shfl_xor_sync(kFull, v, o);
+                    if ((lane & (g - 1)) == 0 && j < k) ow[(j * b) >> 6] = v;
+                }
+            }
+        }
         __syncwarp();
     }
     if (COUNT && wp.counters) {

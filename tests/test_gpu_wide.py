@@ -72,6 +72,25 @@ def test_varied_sets_match_oracle(dmx, torch_mod, k):
     ctx.close()
 
 
+@pytest.mark.parametrize("bits", [1, 2, 4, 8, 16, 32])
+def test_bbit_words_match_oracle(dmx, torch_mod, bits):
+    from oracle import wide
+    rng = np.random.default_rng(200 + bits)
+    rows = [workloads.wide_set(rng, int(rng.integers(1, 30)), l1) for l1 in NORMS for _ in range(3)]
+    rows.append((np.array([4], np.uint64), np.array([0.0])))                      # no positive weight
+    rows.append((np.array([8, 9], np.uint64), np.array([0.5, float("nan")])))       # error row
+    b = workloads.wide_csr(rows)
+    ctx = dmx.dm_create(0)
+    for k in (7, 100, 256):
+        ew, ek, st = wide.sketch_bbit(b.indptr, b.indices, b.weights, k, bits, 31)
+        keys = torch_mod.empty((b.n_sets, k), dtype=torch_mod.int64, device="cuda")
+        words = dmx.dm_sketch_f64_bbit(ctx, *to_dev(torch_mod, b), k, bits, 31, out_keys=keys)
+        assert dmx.dm_sync_status(ctx, raise_on_error=False) == 1
+        assert np.array_equal(words.cpu().numpy().view(np.uint64), ew)
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), ek)
+    ctx.close()
+
+
 @pytest.mark.parametrize("weights,code", [([0.5, float("nan")], 1), ([0.5, -1.0], 1), ([float("inf"), 1.0], 1),
                                           ([0.5, 2.0 ** 960], 5), ([2.0 ** -991, 1e-310], 5),
                                           ([2.0 ** 961, float("nan")], 1)])

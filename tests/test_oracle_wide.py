@@ -196,3 +196,22 @@ def test_errors_and_sentinels():
     # the largest in-range weights (ranks near 2^-990 stay normal)
     st, out = wide.sketch_one([5, 6], [2.0 ** 959, 2.0 ** 958], 8, 1, T_)
     assert st == 0 and wide.EMPTY not in out
+
+
+def test_one_bit_collisions_match_weighted_jaccard():
+    """Section 1.1: a b-bit value agrees with probability J + (1 - J) 2^-b; 1-bit at 2^64."""
+    rng = np.random.default_rng(77)
+    k, b, pairs = 64, 2 * 0.5 / 1.5, 60
+    xs, ys = [], []
+    for _ in range(pairs):
+        ix, wx, iy, wy = workloads.wide_pair(rng, 6, b, 2.0 ** 64)
+        xs.append((ix, wx))
+        ys.append((iy, wy))
+    bx, by = workloads.wide_csr(xs), workloads.wide_csr(ys)
+    wx_, _, sx = wide.sketch_bbit(bx.indptr, bx.indices, bx.weights, k, 1, 5)
+    wy_, _, sy = wide.sketch_bbit(by.indptr, by.indices, by.weights, k, 1, 5)
+    assert not sx.any() and not sy.any()
+    agree = sum(k - bin(int(a) ^ int(c)).count("1") for a, c in zip(wx_[:, 0], wy_[:, 0]))
+    J, n = b / (2 - b), pairs * k
+    p = J + (1 - J) / 2
+    assert abs(agree - n * p) <= 4 * np.sqrt(n * p * (1 - p))
