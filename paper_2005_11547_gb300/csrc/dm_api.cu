@@ -12,6 +12,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dm_device.cuh"
 #include "dm_internal.h"
 
@@ -91,6 +93,16 @@ struct dm_ctx {
 };
 
 namespace {
+
+// NVTX range around a library call, for timelines (a no-op unless a tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
+const char *kind_name(int kind) {
+    return kind == dm::kLsh ? "dm_lsh" : (kind == dm::kBottomK ? "dm_bottomk" : "dm_sketch");
+}
 
 // t = ceil(k ln k) + k.  The product k ln k is irrational for k >= 2; double precision decides
 // the ceiling whenever k ln k is farther than 1e-6 from an integer, which holds for every
@@ -397,6 +409,7 @@ int run_sets(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const 
              uint64_t *out_keys, uint32_t *out_lsh, cudaStream_t st, void *queue = nullptr,
              const Choice *force = nullptr, const int32_t *scale = nullptr) {
     if (!ctx) return DM_EINVAL;
+    Range range(kind_name(kind));
     const Choice ch = force ? *force : choose(ctx, kind, k, K, b);
     Plan pl;
     int rc = plan_call(ctx, indptr, indices, weights, n_sets, kind, k, K, b, seed, out_words, out_keys, out_lsh,
@@ -560,6 +573,7 @@ int dm_sketch_f64_bbit(dm_ctx *ctx, const int64_t *indptr, const uint64_t *indic
     if (n_sets == 0) return DM_OK;
     if (!indptr || !indices || !weights || (b == 0 && !out_keys) || (b > 0 && !out_words)) return DM_EINVAL;
     uint64_t *out = out_keys;
+    Range range("dm_sketch_f64");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e);
     dm::WideParams wp;
@@ -640,6 +654,7 @@ int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
         if ((e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming)) != cudaSuccess)
             return cuda_fail(e);
     }
+    Range range("dm_sketch_host");
     // the staged work starts after everything already queued on the caller's stream
     if ((e = cudaEventRecord(ctx->ev_start, st)) != cudaSuccess) return cuda_fail(e);
     for (int i = 0; i < 2; ++i)

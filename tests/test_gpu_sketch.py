@@ -361,3 +361,49 @@ def test_w2_full_size_sampled(dmx, torch_mod, ctx, oracle_mod):
     sub = b.rows(sel)
     exp = oracle_mod.sketch(sub.indptr, sub.indices, sub.weights, 1024, 1, threads=THREADS)
     assert_same(out[torch.from_numpy(sel).cuda()].cpu().numpy().view(np.uint64), exp, "W2")
+
+
+def test_row_range_shards_on_streams_match_whole_batch(dmx, torch_mod, ctx):
+    """What N ranks do (each sketches its own contiguous rows): three row-range shards, each
+    on its own context and stream, launched together, give the bits of one whole-batch call."""
+    torch = torch_mod
+    b = workloads.random_sets(3000, 0, 300, 1 << 24, seed=91)
+    ip, ix, w = to_dev(torch, b)
+    whole = dmx.dm_sketch(ctx, ip, ix, w, 256, 5)
+    assert dmx.dm_sync_status(ctx, raise_on_error=False) == 0
+    cuts = [0, 700, 2100, 3000]
+    outs, ctxs, streams = [], [], []
+    for i in range(3):
+        lo, hi = cuts[i], cuts[i + 1]
+        sub = b.rows(range(lo, hi))
+        c = dmx.dm_create(0)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            sip, six, sw = to_dev(torch, sub)
+            outs.append(dmx.dm_sketch(c, sip, six, sw, 256, 5, stream=s))
+        ctxs.append(c)
+        streams.append(s)
+    for c, s in zip(ctxs, streams):
+        assert dmx.dm_sync_status(c, stream=s, raise_on_error=False) == 0
+        c.close()
+    torch.cuda.synchronize()
+    assert torch.equal(torch.cat(outs), whole)
+
+
+def test_ten_repeats_are_bit_identical(dmx, torch_mod):
+    """Concurrent atomicMin in any order gives one minimum: ten runs of each launch form and
+    of the LSH and bottom-k sinks repeat their bits exactly."""
+    torch = torch_mod
+    b = workloads.random_sets(600, 0, 400, 1 << 24, seed=17, scale_lo=1e-3, scale_hi=1e3)
+    ip, ix, w = to_dev(torch, b)
+    for form in (0, 1, 2):
+        c = dmx.dm_create(0)
+        dmx.dm_set_option(c, dmx.OPT_FORM, form)
+        dmx.dm_set_option(c, dmx.OPT_LARGE_NNZ, 200)
+        runs = [dmx.dm_sketch(c, ip, ix, w, 128, 3) for _ in range(10)]
+        runs += [dmx.dm_lsh(c, ip, ix, w, 16, 4, 3) for _ in range(10)]
+        runs += [dmx.dm_bottomk(c, ip, ix, w, 64, 3) for _ in range(10)]
+        assert dmx.dm_sync_status(c, raise_on_error=False) == 0
+        for i in (0, 10, 20):
+            assert all(torch.equal(runs[i], r) for r in runs[i + 1:i + 10])
+        c.close()
