@@ -288,6 +288,14 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
                 int64_t n_sets, int32_t lsh, int32_t k, int32_t K_or_b, uint64_t seed, int64_t max_sets,
                 dm_tuning *result, void *stream);
 
+/* Stores launch settings for later calls with the same (kind, k, K, b), exactly as dm_autotune
+ * stores its choice (lsh, k and K_or_b as there), so that settings saved from an earlier
+ * dm_autotune on this GPU model can be reinstalled without timing again.  Reads form,
+ * warps_per_block (0 = automatic), phi0_1024, large_nnz and large_work; the other fields are
+ * ignored.  Results never depend on the settings.  DM_EINVAL for values outside the options'
+ * ranges. */
+int dm_set_tuning(dm_ctx *ctx, int32_t lsh, int32_t k, int32_t K_or_b, const dm_tuning *tuning);
+
 /* t = ceil(k ln k) + k as the library computes it (Theorem 1's proof); 0 for k < 1. */
 int64_t dm_t_of_k(int32_t k);
 

@@ -74,6 +74,7 @@ def load(path: str | None = None):
             "dm_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "dm_set_option": ([P, ctypes.c_int, i64], ctypes.c_int),
             "dm_t_of_k": ([i32], i64),
+            "dm_set_tuning": ([P, i32, i32, i32, P], ctypes.c_int),
             "dm_poisson_thresholds": ([P], None),
             "dm_sketch_noalloc": ([P, P, P, i64, i32, u64, P, P], ctypes.c_int),
             "dm_autotune": ([P, P, P, P, i64, i32, i32, i32, u64, i64, P, P], ctypes.c_int),
@@ -421,6 +422,42 @@ def dm_autotune(ctx: Context, indptr, indices, weights, k: int, seed: int, b: in
                               int(seed) & (2**64 - 1), int(max_sets), ctypes.cast(ctypes.byref(res), ctypes.c_void_p),
                               _stream(stream)), "dm_autotune")
     return res.as_dict()
+
+
+def dm_set_tuning(ctx: Context, k: int, tuning: dict, b: int = 0, lsh_K: int = 0, bottomk: bool = False) -> None:
+    """Reinstall settings (a dict as dm_autotune returns) for later calls of that kind."""
+    t = Tuning()
+    for f in ("form", "warps_per_block", "phi0_1024", "large_nnz", "large_work"):
+        setattr(t, f, int(tuning[f]))
+    lsh = 2 if bottomk else (1 if lsh_K > 0 else 0)
+    _check(load().dm_set_tuning(ctx.handle, lsh, int(k), int(lsh_K if lsh else b),
+                                ctypes.cast(ctypes.byref(t), ctypes.c_void_p)), "dm_set_tuning")
+
+
+def save_tunings(path: str, entries) -> None:
+    """Write dm_autotune results to a JSON file, keyed by the GPU model: entries is a list of
+    {"k", "b", "lsh_K", "bottomk", "tuning"} dicts."""
+    import json
+    import torch
+    data = {}
+    if os.path.exists(path):
+        data = json.load(open(path))
+    data[torch.cuda.get_device_name()] = list(entries)
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1)
+
+
+def load_tunings(ctx: Context, path: str) -> int:
+    """Install the saved settings of this GPU model into a context; returns how many."""
+    import json
+    import torch
+    if not os.path.exists(path):
+        return 0
+    entries = json.load(open(path)).get(torch.cuda.get_device_name(), [])
+    for e in entries:
+        dm_set_tuning(ctx, e["k"], e["tuning"], b=e.get("b", 0), lsh_K=e.get("lsh_K", 0),
+                      bottomk=e.get("bottomk", False))
+    return len(entries)
 
 
 def dm_sync_status(ctx: Context, stream=None, raise_on_error: bool = True) -> int:

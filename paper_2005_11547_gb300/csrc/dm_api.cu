@@ -896,6 +896,23 @@ int dm_set_option(dm_ctx *ctx, int option, int64_t value) {
     }
 }
 
+int dm_set_tuning(dm_ctx *ctx, int32_t lsh, int32_t k, int32_t K_or_b, const dm_tuning *tuning) {
+    if (!ctx || !tuning || lsh < 0 || lsh > 2 || k < 1) return DM_EINVAL;
+    const dm_tuning &t = *tuning;
+    if (t.form < 0 || t.form > 2 || t.warps_per_block < 0 || t.warps_per_block > 8 || t.phi0_1024 < 1 ||
+        t.phi0_1024 > 1024 * 1024 || t.large_nnz < 0 || t.large_work < 0)
+        return DM_EINVAL;
+    const int kind = lsh, K = kind == dm::kLsh ? K_or_b : 0, b = kind == dm::kSketch ? K_or_b : 0;
+    const Choice c{t.form, t.warps_per_block, (float)t.phi0_1024 / 1024.0f, t.large_nnz, (float)t.large_work};
+    for (auto &e : ctx->tuned)
+        if (e.kind == kind && e.k == k && e.K == K && e.b == b) {
+            e.c = c;
+            return DM_OK;
+        }
+    ctx->tuned.push_back(TunedEntry{kind, k, K, b, c});
+    return DM_OK;
+}
+
 int64_t dm_t_of_k(int32_t k) { return t_of_k(k); }
 
 void dm_poisson_thresholds(uint32_t *out) {

@@ -172,3 +172,25 @@ def test_autotune_rejects_bad_arguments(dmx, torch_mod):
     with pytest.raises(dmx.DartMinHashError):
         dmx.dm_autotune(ctx, ip[:1], ix, w, 64, 1)          # no rows
     ctx.close()
+
+
+def test_saved_tunings_reinstall(dmx, torch_mod, tmp_path):
+    """Settings chosen by dm_autotune, saved to JSON and installed into a fresh context, are
+    the ones its calls use (the same launch-form plan as the tuned context) and change no bit."""
+    torch = torch_mod
+    b = workloads.random_sets(3000, 1, 300, 1 << 24, seed=23)
+    ip, ix, w = to_dev(torch, b)
+    c1 = dmx.dm_create(0)
+    t = dmx.dm_autotune(c1, ip, ix, w, 256, 9, max_sets=3000)
+    ref = dmx.dm_sketch(c1, ip, ix, w, 256, 9)
+    path = str(tmp_path / "tunings.json")
+    dmx.save_tunings(path, [{"k": 256, "b": 0, "tuning": t}])
+    c2 = dmx.dm_create(0)
+    assert dmx.load_tunings(c2, path) == 1
+    assert torch.equal(dmx.dm_sketch(c2, ip, ix, w, 256, 9), ref)
+    bad = dict(t, form=7)
+    with pytest.raises(dmx.DartMinHashError):
+        dmx.dm_set_tuning(c2, 256, bad)
+    assert dmx.dm_sync_status(c2, raise_on_error=False) == 0
+    c1.close()
+    c2.close()
