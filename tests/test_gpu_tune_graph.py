@@ -175,8 +175,8 @@ def test_autotune_rejects_bad_arguments(dmx, torch_mod):
 
 
 def test_saved_tunings_reinstall(dmx, torch_mod, tmp_path):
-    """Settings chosen by dm_autotune, saved to JSON and installed into a fresh context, are
-    the ones its calls use (the same launch-form plan as the tuned context) and change no bit."""
+    """Settings chosen by dm_autotune, saved to JSON and installed into a fresh context, change no
+    bit of its calls; settings outside the options' ranges are rejected."""
     torch = torch_mod
     b = workloads.random_sets(3000, 1, 300, 1 << 24, seed=23)
     ip, ix, w = to_dev(torch, b)
