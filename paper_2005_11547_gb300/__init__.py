@@ -152,6 +152,12 @@ def dm_destroy(ctx: Context) -> None:
     ctx.close()
 
 
+def _need(t, numel: int, what: str):
+    """A caller-provided output must hold exactly the values the call writes."""
+    if t is not None and t.numel() != numel:
+        raise ValueError(f"{what} must hold {numel} values (got {t.numel()})")
+
+
 def _csr_ptrs(indptr, indices, weights):
     n = indptr.numel() - 1
     return (n, _dev_ptr(indptr, "int64", "indptr"), _dev_ptr(indices, "uint32", "indices"),
@@ -200,6 +206,8 @@ def dm_sketch_f64_bbit(ctx: Context, indptr, indices, weights, k: int, b: int, s
     words = (k * b + 63) // 64
     if out_words is None:
         out_words = torch.empty((n, words), dtype=torch.int64, device=indptr.device)
+    _need(out_words, n * words, "out_words")
+    _need(out_keys, n * k, "out_keys")
     kp = _dev_ptr(out_keys, "uint64", "out_keys") if out_keys is not None else None
     _check(load().dm_sketch_f64_bbit(ctx.handle, ip, ix, w, n, int(k), int(b), int(seed) & (2**64 - 1),
                                      _dev_ptr(out_words, "uint64", "out_words"), kp, _stream(stream)),
@@ -213,6 +221,7 @@ def dm_mix64_burn(blocks: int, iters: int, seed: int = 1, out=None, stream=None)
     import torch
     if out is None:
         out = torch.empty(blocks * 256, dtype=torch.int64, device="cuda")
+    _need(out, blocks * 256, "out")
     _check(load().dm_mix64_burn(int(blocks), int(iters), int(seed) & (2**64 - 1), _dev_ptr(out, "uint64", "out"),
                                 _stream(stream)), "dm_mix64_burn")
     return out
@@ -227,6 +236,8 @@ def dm_sketch_bbit(ctx: Context, indptr, indices, weights, k: int, b: int, seed:
     words = (k * b + 63) // 64
     if out_words is None:
         out_words = torch.empty((n, words), dtype=torch.int64, device=indptr.device)
+    _need(out_words, n * words, "out_words")
+    _need(out_keys, n * k, "out_keys")
     kp = _dev_ptr(out_keys, "uint64", "out_keys") if out_keys is not None else None
     _check(load().dm_sketch_bbit(ctx.handle, ip, ix, w, n, int(k), int(b), int(seed) & (2**64 - 1),
                                  _dev_ptr(out_words, "uint64", "out_words"), kp, _stream(stream)),
@@ -240,6 +251,7 @@ def dm_lsh(ctx: Context, indptr, indices, weights, L: int, K: int, seed: int, ou
     n, ip, ix, w = _csr_ptrs(indptr, indices, weights)
     if out is None:
         out = torch.empty((n, L), dtype=torch.int32, device=indptr.device)
+    _need(out, n * L, "out")
     _check(load().dm_lsh(ctx.handle, ip, ix, w, n, int(L), int(K), int(seed) & (2**64 - 1),
                          _dev_ptr(out, "uint32", "out"), _stream(stream)), "dm_lsh")
     return out
@@ -254,6 +266,7 @@ def dm_lsh_scaled(ctx: Context, indptr, indices, weights, L: int, K: int, seed: 
         out = torch.empty((n, L), dtype=torch.int32, device=indptr.device)
     if scale_exp.numel() != n:
         raise ValueError("one scale per set")
+    _need(out, n * L, "out")
     _check(load().dm_lsh_scaled(ctx.handle, ip, ix, w, n, int(L), int(K), int(seed) & (2**64 - 1),
                                 _dev_ptr(scale_exp, "int32", "scale_exp"), _dev_ptr(out, "uint32", "out"),
                                 _stream(stream)), "dm_lsh_scaled")
@@ -270,6 +283,8 @@ class LshIndex:
 
     def insert(self, values, ids=None, stream=None):
         n = values.shape[0]
+        _need(values, n * self.L, "values")
+        _need(ids, n, "ids")
         _check(load().dm_lsh_index_insert(self.handle, _dev_ptr(values, "uint32", "values"),
                                           _dev_ptr(ids, "int64", "ids") if ids is not None else None, n,
                                           _stream(stream)), "dm_lsh_index_insert")
@@ -278,6 +293,7 @@ class LshIndex:
         """(counts int32[m], ids int64[m, max_candidates]) as CUDA tensors."""
         import torch
         m = values.shape[0]
+        _need(values, m * self.L, "values")
         counts = torch.empty(m, dtype=torch.int32, device=values.device)
         ids = torch.empty((m, max_candidates), dtype=torch.int64, device=values.device)
         _check(load().dm_lsh_index_query(self.handle, _dev_ptr(values, "uint32", "values"), m, int(max_candidates),
@@ -312,6 +328,8 @@ def dm_weight_classes(ctx: Context, indptr, weights, out=None, scale_out=None, n
     n = indptr.numel() - 1
     if out is None:
         out = torch.empty(n, dtype=torch.int32, device=indptr.device)
+    _need(out, n, "out")
+    _need(scale_out, n, "scale_out")
     _check(load().dm_weight_classes(ctx.handle, _dev_ptr(indptr, "int64", "indptr"),
                                     _dev_ptr(weights, "float32", "weights"), n, _dev_ptr(out, "int32", "out"),
                                     _dev_ptr(scale_out, "int32", "scale_out") if scale_out is not None else None,
@@ -341,8 +359,13 @@ def dm_compare(ctx: Context, a, c, k: int, bits: int = 0, cross: bool = False, o
     na, nc = a.shape[0], c.shape[0]
     if not cross and na != nc:
         raise ValueError("pairs need the same number of rows")
+    if k >= 1 and bits in (0, 1, 2, 4, 8, 16, 32):        # other values: the library rejects them
+        row = k if bits == 0 else (k * bits + 63) // 64
+        _need(a, na * row, "a")
+        _need(c, nc * row, "c")
     if out is None:
         out = torch.empty((na, nc) if cross else (na,), dtype=torch.int32, device=a.device)
+    _need(out, na * nc if cross else na, "out")
     _check(load().dm_compare(ctx.handle, _dev_ptr(a, "uint64", "a"), _dev_ptr(c, "uint64", "c"), na, nc, int(k),
                              int(bits), 1 if cross else 0, _dev_ptr(out, "uint32", "out"), _stream(stream)),
            "dm_compare")
