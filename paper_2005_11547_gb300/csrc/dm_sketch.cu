@@ -55,7 +55,7 @@ __host__ __device__ size_t sketch_sink_bytes(int k) { return ((size_t)k * 8 + 15
 
 // LSH buckets hold K + kLshSlack candidates between compactions: a small slack keeps a warp's
 // shared memory small (more resident warps), and compacting a few entries is cheap.
-constexpr uint32_t kLshSlack = 2;
+constexpr uint32_t kLshSlack = 1;
 
 size_t lsh_sink_bytes(int L, int K) {
     size_t B = (size_t)K + kLshSlack;
