@@ -328,6 +328,7 @@ struct BottomKSink {
 // limit gives u >= ulo for the sinks that must not see a dart twice.
 // ==========================================================================================
 constexpr int kSegTiles = 4, kSeg = 32 * kSegTiles;
+static_assert((kSeg & (kSeg - 1)) == 0, "WalkF::locate's binary search needs a power-of-two segment");
 
 constexpr int kKept = 64;            // kept-dart ring (LSH): drained 32 at a time
 
