@@ -439,6 +439,7 @@ def gpu_arm(args):
                 "peak_source": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int32 lanes x "
                                f"{sm_max:.0f} MHz (max SM clock)",
                 "peak_check": mix_ceiling(dmx, props, peak_ops, stream)}
+    roofline["peak_check"]["kernel_frac_of_ceiling"] = achieved / (roofline["peak_check"]["gop_per_s"] * 1e9)
 
     cpu_baseline = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and wl == "W1":
