@@ -14,6 +14,8 @@ Contents
     ``dm_oracle.c`` (Algorithm 1, Theorem 1, b-bit minhash, (L, K) LSH).
   * ``bruteforce`` -- an independent exact-Fraction enumeration of the hashed dart process
     over a bounding box, used to pin the C code.
+  * ``wide`` -- the wide-range variant (binary64 weights, 64-bit element ids, the norms of
+    Table 1) in pure Python integers, with its own box brute force.
 
 Parity of the hash bits themselves is unpinned by the paper (it prints no hash values and
 uses random tabulation tables); they are pinned only by the statistical tests in
