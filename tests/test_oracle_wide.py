@@ -215,3 +215,55 @@ def test_one_bit_collisions_match_weighted_jaccard():
     J, n = b / (2 - b), pairs * k
     p = J + (1 - J) / 2
     assert abs(agree - n * p) <= 4 * np.sqrt(n * p * (1 - p))
+
+
+@pytest.mark.parametrize("l1", [2.0 ** 512, 2.0 ** -512, 2.0 ** 64])
+def test_kept_dart_count_is_poisson_phi_t(l1):
+    """Lemma 1 at Table 1's norms: the darts of rank below theta = phi / ||x||_1 that hit x
+    number Poi(phi t) (here t = 331, phi = 1; theta's code truncation lowers phi by < 2^-20)."""
+    rng = np.random.default_rng(int(np.log2(l1)) % 1000 + 31)
+    t, counts = 331, []
+    for s in range(60):
+        ix, wx = workloads.wide_set(rng, 8, l1)
+        theta = wide.code_value(wide.first_limit_code(1.0, float(wx.sum())))
+        counts.append(sum(1 for i, x in zip(ix, wx)
+                          for _ in wide.element_darts(int(i), float(x), t, wide.seed_key(1000 + s), theta, table())))
+    c = np.array(counts, dtype=float)
+    assert abs(c.mean() - t) < 4 * np.sqrt(t / len(c))
+    assert 0.6 * t < c.var(ddof=1) < 1.5 * t
+
+
+def test_darts_per_area_and_uniforms():
+    """Algorithm 1's per-area draws under the wide keys: X ~ Poi(1) (chi-square over 0..4+) and
+    U, V uniform on [0, 1) (Kolmogorov-Smirnov), over the areas of sets at 2^{+-512}."""
+    from math import exp, factorial
+    rng = np.random.default_rng(5)
+    xs, us, vs = [], [], []
+    for l1 in (2.0 ** 512, 2.0 ** -512):
+        for s in range(3):
+            ix, wx = workloads.wide_set(rng, 8, l1)
+            theta = wide.code_value(wide.first_limit_code(1.0, float(wx.sum())))
+            areas = []
+            for i, x in zip(ix, wx):
+                list(wide.element_darts(int(i), float(x), 331, wide.seed_key(s), theta, table(), areas=areas))
+                e = wide.element_key(wide.seed_key(s), int(i))
+                for nu, rho, w, r in areas:
+                    a = wide.area_key(wide.region_key(e, nu, rho), w, r)
+                    n = wide.poisson_count(a >> 32, table())
+                    xs.append(n)
+                    for j in range(n):
+                        d = wide.dart_key(a, j)
+                        us.append((d >> 40) / 2 ** 24)
+                        vs.append(((d >> 16) & 0xFFFFFF) / 2 ** 24)
+                areas.clear()
+    xs = np.array(xs)
+    n = len(xs)
+    assert n > 20000
+    obs = [np.sum(xs == m) for m in range(4)] + [np.sum(xs >= 4)]
+    p = [exp(-1) / factorial(m) for m in range(4)]
+    p.append(1 - sum(p))
+    chi2 = sum((o - n * q) ** 2 / (n * q) for o, q in zip(obs, p))
+    assert chi2 < 18.5                                   # 4 degrees of freedom, p ~ 0.001
+    from scipy import stats
+    assert stats.kstest(us, "uniform").pvalue > 1e-3
+    assert stats.kstest(vs, "uniform").pvalue > 1e-3
