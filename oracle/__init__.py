@@ -284,20 +284,26 @@ def lsh_index_query(values, ids, queries, max_candidates: int):
 
 
 def weight_class(indptr, weights):
-    """Weight class of each set (Section 3): c = floor(log2 ||x||_1) with ||x||_1 summed in
-    double; sets with no positive weight get 0.  Normalising a class to ||x||_1 in [1, 2) means
-    scale = -c."""
+    """Weight class of each set (Section 3, "Bottom-k minhash and fast approximate near neighbor
+    search": the data is split into classes ||x||_1 in [2^c, 2^(c+1))): c = floor(log2 ||x||_1),
+    where ||x||_1 is the exact sum of the set's positive finite binary32 weights, added as
+    Fractions (zero, negative, NaN and infinite weights take no part); a set with no such weight
+    gets 0.  Normalising a class to ||x||_1 in [1, 2) means scale = -c."""
     indptr = np.asarray(indptr, dtype=np.int64)
-    w = np.asarray(weights, dtype=np.float64)
+    w = np.asarray(weights, dtype=np.float32)
     out = np.zeros(len(indptr) - 1, dtype=np.int32)
     for s in range(len(out)):
-        l1 = float(w[indptr[s]:indptr[s + 1]].sum())
+        l1 = Fraction(0)
+        for x in w[indptr[s]:indptr[s + 1]].tolist():
+            if x > 0 and math.isfinite(x):
+                l1 += Fraction(x)          # a binary32 value is exactly a Python float
         if l1 > 0:
-            out[s] = math.floor(math.log2(l1))
-            while 2.0 ** out[s] > l1:
-                out[s] -= 1
-            while 2.0 ** (out[s] + 1) <= l1:
-                out[s] += 1
+            c = l1.numerator.bit_length() - l1.denominator.bit_length()
+            while Fraction(2) ** c > l1:
+                c -= 1
+            while Fraction(2) ** (c + 1) <= l1:
+                c += 1
+            out[s] = c
     return out
 
 
