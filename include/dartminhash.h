@@ -104,10 +104,13 @@ int dm_lsh_scaled(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, c
                   int64_t n_sets, int32_t L, int32_t K, uint64_t seed, const int32_t *scale_exp, uint32_t *out,
                   void *stream);
 
-/* Weight class of each set: out[s] = floor(log2 ||x||_1) with ||x||_1 summed in fp32 by the GPU
- * (so a norm within rounding of a power of two may land in either neighbouring class); 0 for a
- * set without a positive weight.  Device int32 out[n_sets] (may be NULL); scale_out (may be
- * NULL) receives norm_exp - out[s], the scale for dm_lsh_scaled that puts the class's norms in
+/* Weight class of each set (Section 3, "Bottom-k minhash and fast approximate near neighbor
+ * search"): out[s] = floor(log2 ||x||_1), where ||x||_1 is the exact sum of the set's positive
+ * finite weights (an integer sum of their significands, so a norm next to a power of two always
+ * lands in the right class, whatever the element order); zero, negative, NaN and infinite weights
+ * take no part, and a set without a positive finite weight gets 0.  Classes run from -149 to
+ * 128 + log2(nnz); rows must have fewer than 2^32 elements.  Device int32 out[n_sets] (may be
+ * NULL); scale_out (may be NULL) receives norm_exp - out[s], the scale for dm_lsh_scaled that puts the class's norms in
  * [2^norm_exp, 2^(norm_exp+1)) (Section 3 normalises to [1, 2), norm_exp = 0; a larger range keeps
  * the first rank limit phi0 / ||x||_1 below 1, where the enumeration is cheapest). */
 int dm_weight_classes(dm_ctx *ctx, const int64_t *indptr, const float *weights, int64_t n_sets, int32_t *out,
@@ -207,15 +210,18 @@ int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
 /* dm_sketch without a context and without any device allocation.  (The paper has no
  * counterpart: this exists for host programs that do not allow a library to allocate, such as a
  * framework that hands all device memory to its own caching allocator, or a process that
- * reserved the whole device.)  Same arguments, outputs and bits as dm_sketch, with phi0 = 1 and
- * automatic launch shape, on the current CUDA device.  The library's scratch for this call
- * (work queue, counters, status) is a fixed device array of about 1 MiB that every GPU loading
- * the library holds until the process exits; n_sets above DM_NOALLOC_MAX_SETS is rejected with
- * DM_EINVAL before any GPU work.  All calls share that array, so calls whose work overlaps on a
- * GPU (other streams or host threads) race and may return wrong keys.  The first call on a
- * device performs a one-time set-up (finding the array's device address, loading the Poisson
- * table); make that first call before any stream capture.  The call waits for `stream` and
- * returns the first error the kernels recorded (DM_EINVAL for a bad weight, DM_ERANGE ...). */
+ * reserved the whole device.)  Same arguments, outputs and bits as dm_sketch, with the library's
+ * default phi0 (1.25) and automatic launch shape, on the current CUDA device; every pointer must
+ * be memory of that device.  The library's scratch for this call (work queue, counters, status)
+ * is a fixed device array of about 1 MiB that every GPU loading the library holds until the
+ * process exits; n_sets above DM_NOALLOC_MAX_SETS is rejected with DM_EINVAL before any GPU
+ * work.  All calls share that array, so calls whose work overlaps on a GPU (other streams or
+ * host threads) race and may return wrong keys.  The first call on a device performs a one-time
+ * set-up (finding the array's device address, loading the Poisson table, raising the kernels'
+ * shared-memory limit); a set-up that fails is tried again by the next call.  The call is
+ * synchronous: it waits for `stream` and returns the first error the kernels recorded
+ * (DM_EINVAL for a bad weight, DM_ERANGE ...).  It therefore cannot be recorded into a CUDA
+ * graph: on a stream that is being captured it returns DM_EINVAL without doing anything. */
 int dm_sketch_noalloc(const int64_t *indptr, const uint32_t *indices, const float *weights,
                       int64_t n_sets, int32_t k, uint64_t seed, uint64_t *out, void *stream);
 

@@ -411,12 +411,20 @@ def dm_sketch_host(ctx: Context, indptr, indices, weights, k: int, seed: int, ou
 def dm_sketch_noalloc(indptr, indices, weights, k: int, seed: int, out, stream=None):
     """dm_sketch for programs that forbid the library's own device allocations: no context, the
     scratch is a fixed array inside the library (at most DM_NOALLOC_MAX_SETS sets per call;
-    overlapping calls race).  `out` must be given.  Synchronous; raises on any error."""
+    overlapping calls race).  `out` must be given; all four tensors must be on one device, which
+    the call makes current.  Synchronous (so never on a stream under graph capture); raises on
+    any error."""
+    import torch
     n, ip, ix, w = _csr_ptrs(indptr, indices, weights)
     if out.numel() != n * k:
         raise ValueError("out must hold n_sets * k keys")
-    _check(load().dm_sketch_noalloc(ip, ix, w, n, int(k), int(seed) & (2**64 - 1),
-                                    _dev_ptr(out, "uint64", "out"), _stream(stream)), "dm_sketch_noalloc")
+    po = _dev_ptr(out, "uint64", "out")
+    dev = indptr.device
+    if any(t.device != dev for t in (indices, weights, out)):
+        raise ValueError("indptr, indices, weights and out must be on one device")
+    with torch.cuda.device(dev):                 # the library runs on the current device
+        _check(load().dm_sketch_noalloc(ip, ix, w, n, int(k), int(seed) & (2**64 - 1), po, _stream(stream)),
+               "dm_sketch_noalloc")
     return out
 
 

@@ -60,8 +60,7 @@ struct dm_ctx {
     int sm_count = 0;
     int *d_status = nullptr;
     int *h_status = nullptr;       // pinned
-    float phi0 = 1.25f;            // initial phi of the sketch loop (Theorem 1); 1.25 spares most
-                                   // retries at 25% more first-pass darts (measured faster on W1/W2)
+    float phi0 = dm::kDefaultPhi0; // initial phi of the sketch loop (Theorem 1)
     float phi0_lsh = 3.0f;         // initial phi of the LSH loop (every bucket needs K darts)
     unsigned long long *counters = nullptr;
     int form = 0;                  // 0 batched, 1 plain, 2 persistent in input order
@@ -485,6 +484,7 @@ int dm_create(dm_ctx **out, int device, size_t mem_budget_bytes) {
         (e = cudaMemset(c->d_status, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaMallocHost(&c->h_status, sizeof(int))) != cudaSuccess ||
         (e = dm::upload_poisson_table(T)) != cudaSuccess || (e = dm::upload_wide_table(T)) != cudaSuccess ||
+        (e = dm::allow_max_shared_memory(device)) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
         dm_destroy(c);
         return cuda_fail(e);

@@ -166,6 +166,22 @@ __device__ inline void warp_bitonic_sort(T *a, uint32_t n, int lane) {
     }
 }
 
+// Minimum of a 64-bit word in shared memory (saddr: its shared-space address).  A plain read
+// comes first, since most candidates lose against the current minimum; otherwise a
+// compare-and-swap retries until the word is at most v.  Each failed swap means another thread
+// lowered the word, so the loop ends after at most as many rounds as there are concurrent
+// writers.  Explicit shared-space instructions keep the address inside the block's window.
+__device__ __forceinline__ void shared_min_u64(uint32_t saddr, uint64_t v) {
+    uint64_t old;
+    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(old) : "r"(saddr) : "memory");
+    while (v < old) {
+        uint64_t prev;
+        asm volatile("atom.shared.cas.b64 %0, [%1], %2, %3;" : "=l"(prev) : "r"(saddr), "l"(old), "l"(v) : "memory");
+        if (prev == old) break;
+        old = prev;
+    }
+}
+
 __device__ __forceinline__ void set_status(int *status, int code) {
     if (status) atomicCAS(status, 0, code);
 }

@@ -11,8 +11,10 @@
 // The array is sized for DM_NOALLOC_MAX_SETS sets (about 1 MiB) and exists on every GPU that
 // loads the library until the process exits.  All calls share it: two calls whose work
 // overlaps on a GPU (different streams, or different host threads) race on it and may give
-// wrong results.  The first call on a device looks up the array's device address and loads the
-// Poisson table there; that first call does the set-up, so make it before any stream capture.
+// wrong results.  The first call on a device looks up the array's device address, loads the
+// Poisson table there and raises the kernels' shared-memory limit.  Every call ends with a
+// synchronisation on its stream, so no call can be captured into a CUDA graph: on a capturing
+// stream the call is refused before any work.
 #include <mutex>
 
 #include "dm_device.cuh"
@@ -56,10 +58,11 @@ int setup_device(int dev, DeviceSetup **out) {
             s.rc = DM_EINVAL;
         } else {
             if (e == cudaSuccess) e = dm::upload_poisson_table(T);
+            if (e == cudaSuccess) e = dm::allow_max_shared_memory(dev);
             s.rc = e == cudaSuccess ? DM_OK : DM_ECUDA;
         }
         s.scratch = (unsigned char *)ptr;
-        s.done = true;
+        s.done = s.rc == DM_OK;          // a failed set-up is tried again by the next call
     }
     *out = &s;
     return s.rc;
@@ -81,6 +84,9 @@ extern "C" int dm_sketch_noalloc(const int64_t *indptr, const uint32_t *indices,
     int rc = setup_device(dev, &ds);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return DM_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return DM_EINVAL;     // the call synchronises its stream
 
     // warps per block: as many as fit 96 KB of shared memory, at most 8
     const size_t wf = dm::warp_bytes(dm::kSketch, k, 0, 0), wg = dm::warp_bytes(dm::kSketch, k, 0, 1);
@@ -95,7 +101,7 @@ extern "C" int dm_sketch_noalloc(const int64_t *indptr, const uint32_t *indices,
     p.k = k;
     p.t = (uint32_t)t;
     p.sigma = dm::mix64(seed ^ dm::kSeedSalt);
-    p.phi0 = 1.0f;
+    p.phi0 = dm::kDefaultPhi0;
     p.out_keys = out;
     p.warps_per_block = wpb;
     p.warp_bytes = (int32_t)wg;

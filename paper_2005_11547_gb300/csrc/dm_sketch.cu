@@ -20,9 +20,13 @@
 //  * Elements are taken 32 at a time (a tile, one lane each).  Each lane computes its
 //    element's area count for the pass in closed form; a warp scan flattens the tile's areas
 //    and every lane walks a contiguous, equal share of them.
-//  * Each area costs one hash (its Poisson count X).  Darts are written to a 128-entry
-//    shared-memory queue of self-contained records and evaluated 64 at a time (two per lane),
-//    so the variable Poisson counts do not diverge the warp.
+//  * Each area costs one hash (its Poisson count X), each dart one (its U, V), each kept dart
+//    one (its bucket and fingerprint).  In the fast path every step of the warp runs one kind
+//    of hash on all lanes: area steps (with the first dart of each area), dart steps over a
+//    per-warp queue of areas with more darts, and bucket steps over a queue of kept darts, so
+//    the variable Poisson counts and keep decisions do not leave lanes idle.
+#include <mutex>
+
 #include "dm_device.cuh"
 #include "dm_internal.h"
 
@@ -33,11 +37,11 @@ __constant__ uint32_t c_pois[12];
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kMaxPasses = 21;     // phi0 * 2^20 at most (Theorem 1's loop limit)
 constexpr int kDefer = -1;         // a pass the fast kernel leaves to the general kernel
-constexpr int kRowTab = 40;        // fast path: rows of nu = 0..38 (+1 pad)
 constexpr int kOverflow = 64;      // LSH: appends past a full bucket within one batch
 // batched form: hist[0..96) bin counts, [96..192) bin cursors, [192..195) class totals
 constexpr int kClasses = 3, kBins = 32, kCursors = kClasses * kBins, kTotals = 2 * kClasses * kBins;
 constexpr size_t kHeaderBytes = 1024;   // queue count, 3 work counters, histogram, totals
+constexpr int kMaxDevices = 64;
 
 __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
 #pragma unroll
@@ -71,12 +75,13 @@ size_t lsh_sink_bytes(int L, int K) {
 struct SketchSink {
     uint64_t *slots;
     uint32_t k;
+    uint32_t sbase;                               // shared-space address of slots[0]
     static constexpr bool kLowerCut = false;      // min is idempotent: band overlap is harmless
-    static constexpr bool kRing = false;          // kept darts go straight to their bucket
 
     __device__ void bind(unsigned char *base, const SketchParams &p) {
         slots = reinterpret_cast<uint64_t *>(base);
         k = (uint32_t)p.k;
+        sbase = (uint32_t)__cvta_generic_to_shared(base);
     }
     __device__ void reset(int lane) {
         for (uint32_t j = lane; j < k; j += 32) slots[j] = ~0ull;
@@ -84,8 +89,7 @@ struct SketchSink {
     }
     __device__ __forceinline__ bool put(uint64_t qh, uint32_t code) {
         const uint32_t slot = fastrange32((uint32_t)(qh >> 32), k);
-        atomicMin(reinterpret_cast<unsigned long long *>(&slots[slot]),
-                  (unsigned long long)(((uint64_t)code << 32) | (uint32_t)qh));
+        shared_min_u64(sbase + 8u * slot, ((uint64_t)code << 32) | (uint32_t)qh);
         return false;
     }
     __device__ __forceinline__ void after_batch(int, bool) {}
@@ -142,7 +146,6 @@ struct LshSink {
     uint16_t *ovf_b;
     uint32_t L, K, B, S;                          // S = B + 1: stride between bucket arrays
     static constexpr bool kLowerCut = true;
-    static constexpr bool kRing = true;           // kept darts are buffered and put 32 at a time
 
     __device__ void bind(unsigned char *base, const SketchParams &p) {
         L = (uint32_t)p.k;
@@ -254,7 +257,6 @@ struct BottomKSink {
     uint32_t *cnt;
     uint32_t k, C;
     static constexpr bool kLowerCut = true;
-    static constexpr bool kRing = true;
 
     __device__ void bind(unsigned char *base, const SketchParams &p) {
         k = (uint32_t)p.k;
@@ -315,33 +317,42 @@ struct BottomKSink {
 // kt[nu] = gamma (1 + rlo[nu]) + ((21 nu mod 64) << 58) (gamma mod 64 = 21).  Tiles with an
 // element beyond nu_top = 31 send the set to the general kernel.
 //
-// The areas of a segment (up to kSegTiles tiles of 32 elements) are split into 32 contiguous
-// equal shares, one per lane.  The warp then runs steps: a lane with no dart left fetches its
-// next area (area hash, Poisson count), and every lane with a dart left evaluates one dart
-// (dart hash, weight and rank tests; a kept dart is hashed to its bucket).  A step thus costs
-// one area and one dart evaluation whichever lanes need them, with no queue in between.
+// Step loop.  The areas of a segment (kSegTiles tiles of 32 elements) are split into 32 equal
+// contiguous shares, one per lane, and the warp runs steps of three kinds.  Each kind is chosen
+// for the whole warp, so every lane with work runs the same hash at the same time:
+//  * area step (every lane on its next area): the area hash a gives the Poisson count X, and
+//    the first dart's hash M(a + gamma) is evaluated at once (weight and rank tests).  A kept
+//    dart goes to the kept queue; an area with X >= 2 goes to the dart queue with the counter
+//    of its second dart and the number of darts left.
+//  * dart step (32 queued areas): the next dart of each is hashed and tested; an area with
+//    darts left goes back to the dart queue.
+//  * bucket step (32 queued kept darts): the bucket/fingerprint hash, the rank code and the
+//    sink.
+// A queue is served as soon as it holds 32 entries, so neither exceeds 64; both carry over
+// from one segment to the next and are drained at the end of the pass.  Only the last steps
+// of a pass (the drain) and the shorter share of a segment's last lanes run on part of the warp.
 //
 // Rank test in integers: a dart of row r has rank (r 2^24 + u) 2^-S, S = nu + 24, and its code
 // (binary32, rounded toward zero) is below bits(theta) iff r 2^24 + u < ceil(theta 2^S) =
-// pthr[nu] (theta is a binary32 value, so rounding toward zero cannot cross it).  Per area this
-// becomes u < uthr = pthr[nu] - r 2^24 (clamped to [0, 2^25]); likewise the previous pass's
-// limit gives u >= ulo for the sinks that must not see a dart twice.
+// pthr[nu] (theta is a binary32 value, so rounding toward zero cannot cross it).  Every row of a
+// region but the last passes whatever u is (pthr > (rhi - 1) 2^24); the last row passes iff
+// u < lastthr[nu] = pthr[nu] - (rhi - 1) 2^24, which lies in (0, 2^24].  Likewise the previous
+// pass's limit cuts only the first row rlo, at u >= firstlo[nu] = ceil(theta_prev 2^S) - rlo 2^24,
+// for the sinks that must not see a dart twice.
 // ==========================================================================================
-constexpr int kSegTiles = 4, kSeg = 32 * kSegTiles;
+constexpr int kSegTiles = 2, kSeg = 32 * kSegTiles;
 static_assert((kSeg & (kSeg - 1)) == 0, "WalkF::locate's binary search needs a power-of-two segment");
+constexpr int kFastRegions = 32;      // weight regions nu = 0..31 of the fast path
+constexpr int kQ = 64;                // capacity of each step queue (served at 32)
 
-constexpr int kKept = 64;            // kept-dart ring (LSH): drained 32 at a time
-
-// Per-pass records of weight region nu, two 16-byte halves in separate arrays (lanes reading
-// different regions then collide in a shared-memory bank only for regions 8 apart): the area
-// counter offset kt and the integer rank threshold of this pass; the rows and the threshold of
-// the previous pass.
-struct RowA {
-    uint64_t kt, pthr;
+// Per-pass record of weight region nu: the area counter offset kt, the u limit of its last row
+// and the u floor of its first row (RegA); its first row and its row end (RegB).
+struct RegA {
+    uint64_t kt;
+    uint32_t lastthr, firstlo;
 };
-struct RowB {
+struct RegB {
     uint32_t rlo, rhi;
-    uint64_t plo;
 };
 // Per-element record of a segment (16 bytes, one load): element key, offset of its first area in
 // the segment, and vtop | nu_top << 24 (nu_top = -1: no areas).
@@ -351,25 +362,27 @@ struct ElRec {
 };
 
 struct FastMem {
-    RowA *ra;                           // [kRowTab]
-    RowB *rb;                           // [kRowTab]
+    RegA *ra;                           // [kFastRegions]
     ElRec *el;                          // [kSeg]
-    uint64_t *kd;                       // ring: kept darts' hashes [kKept] (sinks with kRing)
-    uint32_t *kc;                       // ring: their rank codes [kKept]
+    uint4 *kq;                          // kept queue [kQ]: dart hash (low, high word), row r, region nu
+    uint4 *xp;                          // dart queue [kQ]: uthr | darts left << 26, vmax | nu << 24, r, ulo
+    uint64_t *xo;                       // dart queue [kQ]: counter of the area's next dart
+    RegB *rb;                           // [kFastRegions]
 };
 
-constexpr size_t kFastPathBytes = (size_t)kRowTab * (sizeof(RowA) + sizeof(RowB)) + (size_t)kSeg * sizeof(ElRec);
-constexpr size_t kFastRingBytes = (size_t)kKept * 12;
-static_assert(sizeof(RowA) == 16 && sizeof(RowB) == 16 && sizeof(ElRec) == 16, "record layout");
-static_assert(kFastPathBytes % 16 == 0, "the ring after the fast-path tables must stay aligned");
+constexpr size_t kFastPathBytes = (size_t)kFastRegions * (sizeof(RegA) + sizeof(RegB)) +
+                                  (size_t)kSeg * sizeof(ElRec) + (size_t)kQ * (16 + 16 + 8);
+static_assert(sizeof(RegA) == 16 && sizeof(RegB) == 8 && sizeof(ElRec) == 16, "record layout");
+static_assert(kFastPathBytes % 16 == 0, "fast-path tables keep 16-byte alignment");
 
 __device__ __forceinline__ FastMem carve_fast(unsigned char *base) {
     FastMem m;
-    m.ra = reinterpret_cast<RowA *>(base);
-    m.rb = reinterpret_cast<RowB *>(m.ra + kRowTab);
-    m.el = reinterpret_cast<ElRec *>(m.rb + kRowTab);
-    m.kd = reinterpret_cast<uint64_t *>(base + kFastPathBytes);
-    m.kc = reinterpret_cast<uint32_t *>(m.kd + kKept);
+    m.ra = reinterpret_cast<RegA *>(base);
+    m.el = reinterpret_cast<ElRec *>(m.ra + kFastRegions);
+    m.kq = reinterpret_cast<uint4 *>(m.el + kSeg);
+    m.xp = m.kq + kQ;
+    m.xo = reinterpret_cast<uint64_t *>(m.xp + kQ);
+    m.rb = reinterpret_cast<RegB *>(m.xo + kQ);
     return m;
 }
 
@@ -384,25 +397,19 @@ __device__ __forceinline__ uint64_t ceil_scaled(uint32_t bits, int S) {
     return (m + (1ull << -sh) - 1) >> -sh;
 }
 
-// u threshold of the current area from its remaining rank room p = pthr - r 2^24.
-__device__ __forceinline__ uint32_t clamp_u(int64_t p) {
-    return p <= 0 ? 0u : (uint32_t)min(p, (int64_t)(1 << 25));
-}
-
 struct WalkF {
     int el, nu, nutop;
-    uint32_t r, rhi, vtop, vmax;
+    uint32_t r, rlo, rhi, vtop, vmax, lastthr, firstlo;
     uint64_t e, ctr;
-    int64_t pr, pl;           // pthr - r 2^24 and plo - r 2^24 of the current area
 
     __device__ __forceinline__ void region(const FastMem &m) {
-        const uint4 a = *reinterpret_cast<const uint4 *>(&m.ra[nu]);          // kt, pthr
-        const uint4 b = *reinterpret_cast<const uint4 *>(&m.rb[nu]);          // rlo, rhi, plo
-        r = b.x;
+        const uint4 a = *reinterpret_cast<const uint4 *>(&m.ra[nu]);          // kt, lastthr, firstlo
+        const uint2 b = *reinterpret_cast<const uint2 *>(&m.rb[nu]);          // rlo, rhi
+        r = rlo = b.x;
         rhi = b.y;
         ctr = e + (((uint64_t)a.y << 32) | a.x);
-        pr = (int64_t)(((uint64_t)a.w << 32) | a.z) - ((int64_t)r << 24);
-        pl = (int64_t)(((uint64_t)b.w << 32) | b.z) - ((int64_t)r << 24);
+        lastthr = a.z;
+        firstlo = a.w;
         vmax = nu == nutop ? vtop : kUMask;
     }
     __device__ __forceinline__ void load(const FastMem &m) {
@@ -428,16 +435,12 @@ struct WalkF {
         region(m);
         r += li;
         ctr += kGolden * (uint64_t)li;
-        pr -= (int64_t)li << 24;
-        pl -= (int64_t)li << 24;
     }
     // Next area.  Every region of a pass has at least one row (rlo = floor(g_prev 2^nu) <
     // ceil(g 2^nu) = rhi because g_prev < g), so one region step suffices.
     __device__ __forceinline__ void advance(int n_el, const FastMem &m) {
         ++r;
         ctr += kGolden;
-        pr -= 1ll << 24;
-        pl -= 1ll << 24;
         if (r == rhi) {
             if (++nu > nutop) {
                 nu = 0;
@@ -450,18 +453,6 @@ struct WalkF {
     }
 };
 
-// Hash n <= 32 kept darts of the ring from position h to their buckets (the whole warp).
-template <class Sink>
-__device__ __forceinline__ void fast_put(const FastMem &m, Sink &sink, uint32_t h, uint32_t n, int lane) {
-    bool need = false;
-    if ((uint32_t)lane < n) {
-        const uint32_t i = (h + (uint32_t)lane) & (kKept - 1);
-        need = sink.put(mix64(m.kd[i] ^ kSlotSalt), m.kc[i]);
-    }
-    __syncwarp();
-    sink.after_batch(lane, need);
-}
-
 // One rank-region-0 pass over tiles first, first + stride, ... of the row [.., end).  The areas
 // of each segment are split among nparts warps (this one is number part), 32 lanes each.
 // Returns 0, an error code, or kDefer.
@@ -471,18 +462,75 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
                          int part = 0, int nparts = 1) {
     constexpr bool LOWER = Sink::kLowerCut;
     __syncwarp();
-    for (int nu = lane; nu < kRowTab; nu += 32) {
-        const int n = nu > kMaxRegion ? kMaxRegion : nu;
-        const uint32_t lo = n ? (uint32_t)min(pc.gfl_lo >> (64 - n), (uint64_t)0xFFFFFFFFu) : 0u;
-        m.rb[nu].rlo = lo;
-        m.rb[nu].rhi = n ? (uint32_t)min((pc.gm1 >> (64 - n)) + 1, (uint64_t)0xFFFFFFFFu) : 1u;
-        m.rb[nu].plo = ceil_scaled(pc.cthr_lo, n + 24);
+    {   // per-pass region table, one region per lane
+        const int nu = lane;
+        const uint32_t lo = nu ? (uint32_t)(pc.gfl_lo >> (64 - nu)) : 0u;
+        const uint32_t hi = nu ? (uint32_t)((pc.gm1 >> (64 - nu)) + 1) : 1u;
+        const uint64_t pthr = ceil_scaled(pc.cthr, nu + 24), plo = ceil_scaled(pc.cthr_lo, nu + 24);
         m.ra[nu].kt = kGolden * (1ull + lo) + ((uint64_t)((21u * (uint32_t)nu) & 63u) << 58);
-        m.ra[nu].pthr = ceil_scaled(pc.cthr, n + 24);
+        m.ra[nu].lastthr = (uint32_t)(pthr - ((uint64_t)(hi - 1) << 24));
+        m.ra[nu].firstlo = (uint32_t)(plo - ((uint64_t)lo << 24));
+        m.rb[nu].rlo = lo;
+        m.rb[nu].rhi = hi;
     }
     const uint32_t g_hi = (uint32_t)(pc.gm1 >> 32), glo_hi = (uint32_t)(pc.gfl_lo >> 32);
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t kq = 0, kh = 0;            // kept-dart ring: tail and head
+    uint32_t kh = 0, kt = 0, xh = 0, xt = 0;     // kept and dart queues: heads and tails
+
+    auto push_kept = [&](bool keep, uint64_t d, uint32_t r, uint32_t nu) {
+        const unsigned km = __ballot_sync(kFull, keep);
+        if (keep) m.kq[(kt + __popc(km & lt)) & (kQ - 1)] = make_uint4((uint32_t)d, (uint32_t)(d >> 32), r, nu);
+        kt += __popc(km);
+        if (COUNT && keep) cnt[2]++;
+    };
+    auto push_darts = [&](bool more, uint64_t op, uint32_t w0, uint32_t w1, uint32_t r, uint32_t ulo) {
+        const unsigned xm = __ballot_sync(kFull, more);
+        if (more) {
+            const uint32_t i = (xt + __popc(xm & lt)) & (kQ - 1);
+            m.xo[i] = op;
+            m.xp[i] = make_uint4(w0, w1, r, ulo);
+        }
+        xt += __popc(xm);
+    };
+    // bucket step over the n (<= 32) oldest kept darts
+    auto kept_step = [&](uint32_t n) {
+        __syncwarp();
+        const bool v = (uint32_t)lane < n;
+        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+        if (v) q = m.kq[(kh + (uint32_t)lane) & (kQ - 1)];
+        kh += n;
+        const uint64_t d = ((uint64_t)q.y << 32) | q.x;
+        const uint64_t h = mix64(d ^ kSlotSalt);
+        // binary32 code of rank = P 2^-S rounded toward zero: exact u64 -> f32 conversion in
+        // round-toward-zero mode, then the exponent lowered by S
+        const uint64_t P = ((uint64_t)q.z << 24) | (uint32_t)(d >> 40);
+        const uint32_t code = P ? __float_as_uint(__ull2float_rz(P)) - ((q.w + 24u) << 23) : 0u;
+        bool need = false;
+        if (v) need = sink.put(h, code);
+        __syncwarp();
+        sink.after_batch(lane, need);
+    };
+    // dart step over the n (<= 32) oldest queued areas
+    auto dart_step = [&](uint32_t n) {
+        __syncwarp();
+        const bool v = (uint32_t)lane < n;
+        uint64_t op = 0;
+        uint4 x = make_uint4(0u, 0u, 0u, 0u);
+        if (v) {
+            const uint32_t i = (xh + (uint32_t)lane) & (kQ - 1);
+            op = m.xo[i];
+            x = m.xp[i];
+        }
+        xh += n;
+        __syncwarp();                             // every lane has read its entry before any push
+        const uint64_t d = mix64(op);
+        const uint32_t u = (uint32_t)(d >> 40), vv = (uint32_t)(d >> 16) & kUMask;
+        bool keep = v && u < (x.x & 0x3FFFFFFu) && vv <= (x.y & kUMask);
+        if constexpr (LOWER) keep = keep && u >= x.w;
+        push_kept(keep, d, x.z, x.y >> 24);
+        push_darts(v && (x.x >> 26) > 1u, op + kGolden, x.x - (1u << 26), x.y, x.z, x.w);
+    };
+
     for (int64_t tile = first; tile < end;) {
         // segment tables: geometry, element hash and area offsets of up to kSegTiles tiles
         __syncwarp();
@@ -520,70 +568,40 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         const uint32_t share = (total + lanes - 1) / lanes;
         const uint32_t lo = share * (32u * (uint32_t)part + (uint32_t)lane);
         uint32_t left = lo < total ? min(share, total - lo) : 0u;
-        WalkF s;
+        // area steps of this warp: lane 0 has the largest share
+        const uint32_t lo0 = share * 32u * (uint32_t)part;
+        const uint32_t steps = lo0 < total ? min(share, total - lo0) : 0u;
+        WalkF s{};
         if (left) s.locate(lo, n_el, m);
-        bool fresh = true;              // the walk sits on the next area to fetch
-        uint32_t nx = 0, uthr = 0, ulo = 0;
-        uint64_t c = 0;
-        while (__any_sync(kFull, left | nx)) {
-            if (nx == 0 && left) {
-                if (!fresh) s.advance(n_el, m);
-                fresh = false;
-                --left;
-                c = mix64(s.ctr);
-                nx = (uint32_t)poisson1((uint32_t)(c >> 32), c_pois);
-                uthr = clamp_u(s.pr);
-                if (LOWER) ulo = clamp_u(s.pl);
-                if (COUNT) { cnt[0]++; cnt[1] += nx; }
+        for (uint32_t st = 0; st < steps; ++st) {
+            for (;;) {                            // serve full queues (each below 32 afterwards)
+                if (kt - kh >= 32u) kept_step(32u);
+                else if (xt - xh >= 32u) dart_step(32u);
+                else break;
             }
-            bool keep = false;
-            uint64_t d = 0;
-            uint32_t u = 0;
-            if (nx) {
-                --nx;
-                c += kGolden;
-                d = mix64(c);
-                u = (uint32_t)(d >> 40);
-                const uint32_t v = (uint32_t)(d >> 16) & kUMask;
-                keep = u < uthr && v <= s.vmax;
-                if (LOWER) keep = keep && u >= ulo;
-            }
-            if (!Sink::kRing) {
-                // bucket minimum at once (a shared-memory atomic is cheap)
-                if (keep) {
-                    const uint64_t P = ((uint64_t)s.r << 24) | u;
-                    const uint32_t code =
-                        P ? __float_as_uint(__ull2float_rz(P)) - ((uint32_t)(s.nu + 24) << 23) : 0u;
-                    sink.put(mix64(d ^ kSlotSalt), code);
-                    if (COUNT) cnt[2]++;
-                }
-                continue;
-            }
-            // kept darts go to the ring; 32 of them at a time are hashed to their buckets
-            const unsigned km = __ballot_sync(kFull, keep);
-            if (km) {
-                if (keep) {
-                    const uint64_t P = ((uint64_t)s.r << 24) | u;
-                    // binary32 code of rank = P 2^-S rounded toward zero: exact u64 -> f32
-                    // conversion in round-toward-zero mode, then the exponent lowered by S
-                    const uint32_t i = (kq + __popc(km & lt)) & (kKept - 1);
-                    m.kd[i] = d;
-                    m.kc[i] = P ? __float_as_uint(__ull2float_rz(P)) - ((uint32_t)(s.nu + 24) << 23) : 0u;
-                    if (COUNT) cnt[2]++;
-                }
-                kq += __popc(km);
-                if (kq - kh >= 32) {
-                    __syncwarp();
-                    fast_put<Sink>(m, sink, kh, 32, lane);
-                    kh += 32;
-                }
-            }
+            // area step
+            const bool act = left != 0;
+            const uint64_t a = mix64(s.ctr);
+            const uint32_t X = act ? (uint32_t)poisson1((uint32_t)(a >> 32), c_pois) : 0u;
+            const uint32_t uthr = s.r + 1 == s.rhi ? s.lastthr : (1u << 25);
+            const uint32_t ulo = LOWER && s.r == s.rlo ? s.firstlo : 0u;
+            const uint64_t d = mix64(a + kGolden);
+            const uint32_t u = (uint32_t)(d >> 40), vv = (uint32_t)(d >> 16) & kUMask;
+            bool keep = X != 0 && u < uthr && vv <= s.vmax;
+            if constexpr (LOWER) keep = keep && u >= ulo;
+            if (COUNT) { cnt[0] += act; cnt[1] += X; }
+            push_kept(keep, d, s.r, (uint32_t)s.nu);
+            push_darts(X >= 2, a + 2 * kGolden, uthr | ((X - 1) << 26), s.vmax | ((uint32_t)s.nu << 24), s.r, ulo);
+            if (act && --left) s.advance(n_el, m);
         }
     }
-    if (kq != kh) {
-        __syncwarp();
-        fast_put<Sink>(m, sink, kh, kq - kh, lane);
+    for (;;) {                                    // drain both queues
+        if (kt - kh >= 32u) kept_step(32u);
+        else if (xt != xh) dart_step(min(xt - xh, 32u));
+        else if (kt != kh) kept_step(kt - kh);
+        else break;
     }
+    __syncwarp();
     return 0;
 }
 
@@ -943,25 +961,57 @@ __global__ void __launch_bounds__(256) classify_kernel(const SketchParams p) {
 }
 
 // Weight class c = floor(log2 |x|_1) per set (Section 3's split of the data into classes
-// |x|_1 in [2^c, 2^(c+1))); the norm is the warp's fp32 sum.
-__global__ void __launch_bounds__(256) weight_class_kernel(const int64_t *indptr, const float *weights,
-                                                           int64_t n_sets, int32_t *out, int32_t *scale_out,
-                                                           int32_t norm_exp) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n_sets; s += nw) {
-        float l1 = 0.f;
-        for (int64_t i = indptr[s] + lane; i < indptr[s + 1]; i += 32) {
-            const float x = weights[i];
-            if (x > 0.f && x < 3.0e38f) l1 += x;
-        }
+// |x|_1 in [2^c, 2^(c+1))), where |x|_1 is the exact sum of the set's positive finite binary32
+// weights (zero, negative, NaN and infinite weights take no part).  A weight is M 2^(s - 149) with
+// M < 2^24 and s = max(exponent field, 1) - 1 in [0, 253], so N = |x|_1 2^149 = sum M 2^s is an
+// integer.  Each lane adds its elements' M 2^s into nine base-2^32 digits, each held in a 64-bit
+// word of a shared-memory column of its own (the upper halves collect carries); the warp then
+// sums the columns digit by digit, propagates the carries and takes the class from the highest
+// set bit, c = bitlen(N) - 1 - 149.  Every step is integer addition, so the result does not
+// depend on the order of the elements.  Rows must have fewer than 2^32 elements.
+constexpr int kClassDigits = 9;         // digits of the per-lane sums: bits 0 .. 287
+constexpr int kClassWarps = 8;
+
+__global__ void __launch_bounds__(32 * kClassWarps) weight_class_kernel(const int64_t *indptr, const float *weights,
+                                                                        int64_t n_sets, int32_t *out,
+                                                                        int32_t *scale_out, int32_t norm_exp) {
+    __shared__ uint64_t acc[kClassWarps][kClassDigits][32];      // [warp][digit][lane]
+    __shared__ uint64_t tot[kClassWarps][kClassDigits];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * kClassWarps;
+    for (int64_t s = (int64_t)blockIdx.x * kClassWarps + wid; s < n_sets; s += nw) {
 #pragma unroll
-        for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(kFull, l1, o);
+        for (int d = 0; d < kClassDigits; ++d) acc[wid][d][lane] = 0;
+        for (int64_t i = indptr[s] + lane; i < indptr[s + 1]; i += 32) {
+            const uint32_t xb = __float_as_uint(weights[i]), ex = xb >> 23;
+            if (xb == 0 || ex >= 255u) continue;          // zero, negative (sign bit set), NaN or infinite
+            const uint32_t M = ex ? (xb & 0x7FFFFFu) | 0x800000u : xb;
+            const uint32_t sh = (ex ? ex : 1u) - 1u;
+            const uint64_t v = (uint64_t)M << (sh & 31u);   // below 2^55: digits sh / 32 and sh / 32 + 1
+            const uint32_t d = sh >> 5;
+            acc[wid][d][lane] += (uint32_t)v;
+            acc[wid][d + 1][lane] += v >> 32;
+        }
+        __syncwarp();
+        if (lane < kClassDigits) {                       // digit sums over the 32 columns
+            uint64_t t = 0;
+            for (int j = 0; j < 32; ++j) t += acc[wid][lane][j];
+            tot[wid][lane] = t;
+        }
+        __syncwarp();
         if (lane == 0) {
-            const int c = (l1 > 0.f && l1 < 3.0e38f) ? ilogbf(l1) : 0;
+            uint64_t carry = 0;
+            int c = 0;
+            for (int d = 0; d <= kClassDigits; ++d) {   // one more digit for the last carry
+                const uint64_t word = (d < kClassDigits ? tot[wid][d] : 0ull) + carry;
+                const uint32_t digit = (uint32_t)word;
+                carry = word >> 32;
+                if (digit) c = 32 * d + (31 - __clz(digit)) - 149;
+            }
             if (out) out[s] = c;
             if (scale_out) scale_out[s] = norm_exp - c;
         }
+        __syncwarp();
     }
 }
 
@@ -990,8 +1040,8 @@ __global__ void __launch_bounds__(256) scatter_kernel(const SketchParams p) {
 }
 
 // Large sets: a block per set.  The block's warps share the set's k bucket minima in shared
-// memory (atomicMin works across warps).  A set of at least two tiles per warp has its tiles
-// dealt round-robin to the warps; a smaller one (few elements, much work) has every tile's
+// memory (the shared-memory minimum works across warps).  A set of at least two tiles per warp
+// has its tiles dealt round-robin to the warps; a smaller one (few elements, much work) has every tile's
 // areas split among all the warps.  Passes are separated by block barriers.  A pass runs the
 // fast walk when the limit is below 1 and every tile allows it, else the general walk over all
 // tiles (a dart seen twice does not change a minimum).
@@ -1095,18 +1145,12 @@ __global__ void __launch_bounds__(256, 2) large_kernel(const SketchParams p) {
 template <bool BBIT, bool COUNT>
 static cudaError_t launch_large(const SketchParams &p, int grid, cudaStream_t st) {
     const size_t smem = large_block_bytes(p.k, p.large_warps);
-    auto fn = large_kernel<BBIT, COUNT>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    fn<<<grid, 32 * p.large_warps, smem, st>>>(p);
+    large_kernel<BBIT, COUNT><<<grid, 32 * p.large_warps, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 int large_blocks_per_sm(bool bbit, int warps, size_t smem) {
     const void *fn = bbit ? (const void *)large_kernel<true, false> : (const void *)large_kernel<false, false>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * warps, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
@@ -1115,8 +1159,8 @@ int large_blocks_per_sm(bool bbit, int warps, size_t smem) {
 cudaError_t launch_weight_classes(const int64_t *indptr, const float *weights, int64_t n_sets, int32_t *out,
                                   int32_t *scale_out, int32_t norm_exp, int sm_count, cudaStream_t st) {
     const int64_t blocks = (n_sets + 7) / 8, cap = 16LL * (sm_count > 0 ? sm_count : 1);
-    weight_class_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(indptr, weights, n_sets, out, scale_out,
-                                                                             norm_exp);
+    weight_class_kernel<<<(int)(blocks < cap ? blocks : cap), 32 * kClassWarps, 0, st>>>(indptr, weights, n_sets, out,
+                                                                                          scale_out, norm_exp);
     return cudaGetLastError();
 }
 
@@ -1147,13 +1191,8 @@ static const void *kernel_fn() {
 
 template <class Sink, bool BBIT, bool COUNT, int MODE>
 static cudaError_t launch_t(const SketchParams &p, int grid, cudaStream_t st) {
-    size_t smem = (size_t)(MODE == 0 ? p.warp_bytes_fast : p.warp_bytes) * p.warps_per_block;
-    auto fn = set_kernel<Sink, BBIT, COUNT, MODE>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    fn<<<grid, 32 * p.warps_per_block, smem, st>>>(p);
+    const size_t smem = (size_t)(MODE == 0 ? p.warp_bytes_fast : p.warp_bytes) * p.warps_per_block;
+    set_kernel<Sink, BBIT, COUNT, MODE><<<grid, 32 * p.warps_per_block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -1238,7 +1277,49 @@ size_t sink_bytes(int kind, int k, int K) {
 
 size_t warp_bytes(int kind, int k, int K, int mode) {
     const size_t sink = (sink_bytes(kind, k, K) + 15) & ~(size_t)15;
-    return sink + (mode == 0 ? kFastPathBytes + (kind != kSketch ? kFastRingBytes : 0) : kGenPathBytes);
+    return sink + (mode == 0 ? kFastPathBytes : kGenPathBytes);
+}
+
+// Shared memory limit of every kernel in this file.  The dynamic shared memory a launch may
+// request above 48 KB is a per-function attribute of the device, so it is raised once per device,
+// to the device's opt-in maximum, before the first launch (at context creation), and never
+// changed afterwards: launches from several host threads with different shared-memory sizes then
+// cannot race on it.  The attribute only bounds what a launch may request; each launch still
+// gets exactly the bytes it asks for.
+template <class Sink, bool BBIT, bool COUNT>
+static cudaError_t allow_smem_sink(int bytes) {
+    cudaError_t e = cudaFuncSetAttribute(set_kernel<Sink, BBIT, COUNT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(set_kernel<Sink, BBIT, COUNT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+template <class Sink>
+static cudaError_t allow_smem_all(int bytes) {
+    cudaError_t e = allow_smem_sink<Sink, false, false>(bytes);
+    if (e == cudaSuccess) e = allow_smem_sink<Sink, false, true>(bytes);
+    if (e == cudaSuccess) e = allow_smem_sink<Sink, true, false>(bytes);
+    if (e == cudaSuccess) e = allow_smem_sink<Sink, true, true>(bytes);
+    return e;
+}
+
+cudaError_t allow_max_shared_memory(int device) {
+    static std::mutex mu;
+    static bool done[kMaxDevices] = {};
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[device]) return cudaSuccess;
+    int bytes = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e == cudaSuccess) e = allow_smem_all<SketchSink>(bytes);
+    if (e == cudaSuccess) e = allow_smem_all<LshSink>(bytes);
+    if (e == cudaSuccess) e = allow_smem_all<BottomKSink>(bytes);
+    const void *large[4] = {(const void *)large_kernel<false, false>, (const void *)large_kernel<false, true>,
+                            (const void *)large_kernel<true, false>, (const void *)large_kernel<true, true>};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        e = cudaFuncSetAttribute(large[i], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done[device] = true;
+    return e;
 }
 
 int blocks_per_sm(int kind, int mode, bool bbit, int warps_per_block, size_t smem) {
@@ -1248,7 +1329,6 @@ int blocks_per_sm(int kind, int mode, bool bbit, int warps_per_block, size_t sme
         fn = mode == 0 ? kernel_fn<BottomKSink, false, false, 0>() : kernel_fn<BottomKSink, false, false, 1>();
     else if (mode == 0) fn = bbit ? kernel_fn<SketchSink, true, false, 0>() : kernel_fn<SketchSink, false, false, 0>();
     else fn = bbit ? kernel_fn<SketchSink, true, false, 1>() : kernel_fn<SketchSink, false, false, 1>();
-    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * warps_per_block, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;

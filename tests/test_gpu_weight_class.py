@@ -1,7 +1,6 @@
 """GPU parity of the weight-class normalised LSH (Section 3): dm_lsh_scaled equals the oracle's
 exactly scaled LSH for every set and scale, scale 0 equals dm_lsh, and dm_weight_classes gives
-floor(log2 ||x||_1) (the oracle's class wherever the norm is not within fp32 rounding of a power
-of two)."""
+floor(log2 ||x||_1) of the exact norm, equal to the oracle's class for every set."""
 import numpy as np
 import pytest
 
@@ -60,8 +59,24 @@ def test_scaled_lsh_matches_oracle(dmx, torch_mod, oracle_mod, form):
 
 
 def test_weight_classes(dmx, torch_mod, oracle_mod):
+    """Every set's class equals the oracle's exact class bit for bit: random sets over 16 decades,
+    the closed-form edge sets (norms at, one unit below and, in binary64, rounding across a power
+    of two; subnormals; sums beyond the binary32 range; weights that take no part), large rows,
+    and the edge sets again with their elements reversed."""
+    import test_oracle_weight_class as pins
     torch = torch_mod
-    b = workloads.random_sets(2000, 0, 100, 1 << 22, seed=62, scale_lo=1e-8, scale_hi=1e8)
+    rand = workloads.random_sets(2000, 0, 100, 1 << 22, seed=62, scale_lo=1e-8, scale_hi=1e8)
+    rows = [(rand.indices[rand.indptr[s]:rand.indptr[s + 1]], rand.weights[rand.indptr[s]:rand.indptr[s + 1]])
+            for s in range(rand.n_sets)]
+    edges = pins.edge_sets()
+    for w, _ in edges:
+        rows.append((np.arange(len(w), dtype=np.uint32), np.array(w, dtype=np.float32)))
+        rows.append((np.arange(len(w), dtype=np.uint32), np.array(w[::-1], dtype=np.float32)))
+    rng = np.random.default_rng(63)
+    for nnz in (1000, 5000, 40000):                  # many elements per lane and digit
+        w = np.float32(2.0) ** rng.integers(-149, 100, size=nnz).astype(np.float32)
+        rows.append((np.arange(nnz, dtype=np.uint32), w.astype(np.float32)))
+    b = workloads.csr_of(rows)
     ctx = dmx.dm_create(0)
     ip, ix, w = to_dev(torch, b)
     got = dmx.dm_weight_classes(ctx, ip, w).cpu().numpy()
@@ -70,9 +85,6 @@ def test_weight_classes(dmx, torch_mod, oracle_mod):
     assert np.array_equal(sc.cpu().numpy(), 2 - got)
     ctx.close()
     exp = oracle_mod.weight_class(b.indptr, b.weights)
-    l1 = np.array([b.weights[b.indptr[s]:b.indptr[s + 1]].astype(np.float64).sum() for s in range(b.n_sets)])
-    frac = np.where(l1 > 0, np.log2(np.maximum(l1, 1e-300)) - exp, 0.5)
-    clear = (frac > 1e-5) & (frac < 1 - 1e-5)           # not within fp32 rounding of a power of two
-    assert clear.sum() > 1900
-    assert np.array_equal(got[clear], exp[clear])
-    assert np.all(np.abs(got - exp) <= 1)
+    assert np.array_equal(got, exp)
+    e0 = rand.n_sets
+    assert got[e0:e0 + 2 * len(edges):2].tolist() == [c for _, c in edges]
