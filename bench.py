@@ -4,7 +4,9 @@
 One step = one dm_sketch_bbit call over workload W1 (1,000,000 weighted sets, 256 distinct
 elements each over d = 2^20, Exp(1) weights): k = 256 uint64 minhash keys plus the 1-bit
 packed sketch (4 words) per set, inputs and outputs resident in HBM (2 GB in, 2 GB out: far
-larger than the 129 MB L2, so no flush between steps).  Prints one JSON line (rank 0).
+larger than the 129 MB L2, so no flush between steps).  Prints one JSON line (rank 0).  The same
+run then times the heavy-tailed W2 batch (200,000 sets, k = 1024) in the batched and the plain
+per-set forms and reports it under "w2" in that line (--no-w2 skips it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dm|reference] [--sets N]
 
@@ -56,7 +58,7 @@ def parse():
                          "IDX: LSH-table index build and query over the W3 values; "
                          "T1: Table 1's sets (1,024 elements, 64-bit ids, binary64 weights, k=256) at "
                          "||x||_1 = 1, 2^64, 2^-64, 2^512, 2^-512 through dm_sketch_f64")
-    ap.add_argument("--duration", type=float, default=20.0, help="W4: seconds of 50,000/s arrivals to replay")
+    ap.add_argument("--duration", type=float, default=60.0, help="W4: seconds of 50,000/s arrivals to replay")
     ap.add_argument("--norm-exp", type=int, default=2,
                     help="W3S: normalise each weight class to ||x||_1 in [2^e, 2^(e+1)) (2: first limit below 1)")
     ap.add_argument("--form", choices=["batched", "plain", "persistent"], default="batched",
@@ -70,6 +72,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-set form measured beside")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-w2", action="store_true", help="W1: skip the heavy-tailed batch timed beside it")
     return ap.parse_args()
 
 
@@ -178,16 +181,6 @@ def kernel_fingerprint() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_set():
-    path = os.path.join(ROOT, "profiles", "sketch_w1_traffic.json")
-    if not os.path.exists(path):
-        return None
-    d = json.load(open(path))
-    if d.get("kernel_fingerprint") != kernel_fingerprint():
-        return None
-    return d.get("dram_bytes_per_set")
-
-
 def mix_ceiling(dmx, props, peak_ops, stream):
     """What pure hashing reaches: SplitMix64 chains alone (dm_mix64_burn, full occupancy), in the
     same op count per mix as the roofline's work model, against the same peak."""
@@ -208,6 +201,20 @@ def mix_ceiling(dmx, props, peak_ops, stream):
 # ------------------------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline leg and the reference arm)
 # ------------------------------------------------------------------------------------------
+def traffic_per_set(wl: str):
+    """DRAM bytes per set of the workload's dominant kernel, from its committed ncu capture
+    (profiles/traffic_<workload>.json: read + write bytes of one launch over a prefix of the batch,
+    divided by the sets it processed).  None when the workload has no capture or the kernel source
+    changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{wl.lower()}.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("workload") != wl or d.get("kernel_fingerprint") != kernel_fingerprint():
+        return None
+    return d.get("dram_bytes_per_set")
+
+
 def time_oracle(batch, n_sample: int, cores: int):
     import oracle
     sub = batch.rows(range(min(n_sample, batch.n_sets)))
@@ -216,6 +223,16 @@ def time_oracle(batch, n_sample: int, cores: int):
     oracle.sketch_bbit(sub.indptr, sub.indices, sub.weights, K_SLOTS, B_BITS, SEED, keys=True, threads=cores)
     dt = time.perf_counter() - t0
     return sub.n_sets / dt, sub.n_sets, dt
+
+
+WL_DESC = {
+    "W1": "W1: 1,000,000 sets x 256 distinct elements (d=2^20), Exp(1) fp32 weights; k=256 uint64 keys + 1-bit words",
+    "W2": "W2: 200,000 heavy-tailed sets (nnz log-normal median 100, sigma 1.5, clipped to [1, 1e5]; ||x||_1 "
+          "log-uniform 1e-3..1e3), d=2^24; k=1024 uint64 keys",
+    "W3": "W3: 1,000,000 tf-idf-like sets (Zipf(1.1) tokens, nnz U{200..2000}), d=2^20; (L, K) = (64, 8) LSH uint32 "
+          "values",
+    "W1B": "W1 sets (1,000,000 x 256 elements, Exp(1) weights); bottom-k sketches, k=256 sorted uint64 keys",
+}
 
 
 def reference_arm(args):
@@ -254,21 +271,18 @@ def reference_arm(args):
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
-def gpu_arm(args):
+def measure(args, wl, local, dist, props, full):
+    """Time one batch workload (W1, W2, W3, W1B, W3S) on this rank's GPU: autotune, graph replay,
+    W warm-up steps, K steps between barriers with CUDA events on the launching stream (max over
+    ranks), the unit counts of one launch, the plain per-set form beside it.  full: also the
+    end-to-end leg through the host-buffer entry (W1), the hash ceiling and the CPU oracle."""
     import numpy as np
     import torch
 
     import paper_2005_11547_gb300 as dmx
     import workloads
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = dist_init(world, True)
-    dmx.build()
-    dmx.load()
-    props = torch.cuda.get_device_properties(local)
-
-    wl = args.workload
+    rank, world, _ = dist_env()
     if wl in ("W1", "W1B"):
         b = workloads.workload1(args.sets or 1_000_000)
     elif wl == "W2":
@@ -291,6 +305,7 @@ def gpu_arm(args):
     cls = torch.empty(n, dtype=torch.int32, device="cuda")
     scl = torch.empty(n, dtype=torch.int32, device="cuda")
     form_id = {"batched": dmx.FORM_BATCHED, "plain": dmx.FORM_PLAIN, "persistent": dmx.FORM_PERSISTENT}[args.form]
+
     def manual_settings(c):
         dmx.dm_set_option(c, dmx.OPT_FORM, form_id)
         if args.large_nnz is not None:
@@ -327,15 +342,10 @@ def gpu_arm(args):
             tuning = dmx.dm_autotune(ctx, ip, ix, w, 1024, SEED, max_sets=n, stream=stream)
         elif wl == "W1B":
             tuning = dmx.dm_autotune(ctx, ip, ix, w, K_SLOTS, SEED, bottomk=True, stream=stream)
-        elif wl == "W3S":
-            tuning = None                             # the tuner does not model the scaled calls
-        else:
+        elif wl == "W3":
             tuning = dmx.dm_autotune(ctx, ip, ix, w, 64, SEED, lsh_K=8, stream=stream)
     if not args.no_graph:
         dmx.dm_set_option(ctx, dmx.OPT_GRAPH, 1)
-
-    def step():
-        launch(ctx)
 
     # work units of one launch (untimed counting launch with the same settings; counters never
     # change output bits)
@@ -355,9 +365,8 @@ def gpu_arm(args):
     cctx.close()
 
     for _ in range(max(3, args.warmup)):
-        step()
+        launch(ctx)
     dmx.dm_sync_status(ctx)
-
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sampler = ClockSampler(local)
@@ -366,7 +375,7 @@ def gpu_arm(args):
     t_wall = time.perf_counter()
     for i in range(args.steps):
         starts[i].record(stream)
-        step()
+        launch(ctx)
         ends[i].record(stream)
     barrier(dist, True)
     t_wall = time.perf_counter() - t_wall
@@ -384,7 +393,7 @@ def gpu_arm(args):
         pctx = dmx.dm_create(local)
         dmx.dm_set_option(pctx, dmx.OPT_FORM, dmx.FORM_PLAIN)
         launch(pctx)
-        pe = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        pe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         barrier(dist, True)
         pe[0].record(stream)
         for _ in range(3):
@@ -393,14 +402,13 @@ def gpu_arm(args):
         barrier(dist, True)
         dmx.dm_sync_status(pctx)
         pctx.close()
-        p_ms = pe[0].elapsed_time(pe[1]) / 3
-        p_max = max_over_ranks(dist, p_ms / 1e3, True)
+        p_max = max_over_ranks(dist, pe[0].elapsed_time(pe[1]) / 3 / 1e3, True)
         plain = {"ms_per_step": p_max * 1e3, "value": all_sets / args.steps / p_max, "unit": "sets/s",
                  "batched_over_plain": value / (all_sets / args.steps / p_max)}
 
     # end to end through the host-buffer C-ABI entry (copies inside the timed region)
     e2e = None
-    if not args.no_e2e and wl == "W1":
+    if full and not args.no_e2e and wl == "W1":
         hip = torch.from_numpy(b.indptr).pin_memory()
         hix = torch.from_numpy(b.indices.view(np.int32)).pin_memory()
         hw = torch.from_numpy(b.weights).pin_memory()
@@ -419,64 +427,99 @@ def gpu_arm(args):
         h2d = b.indptr.nbytes + b.indices.nbytes + b.weights.nbytes
         d2h = hk.numel() * 8 + hwd.numel() * 8
         e2e = {"value": world * n * e2e_steps / te, "unit": "sets/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+               "d2h_bytes_per_step": int(d2h), "copies_declared": True}
         del hip, hix, hw, hk, hwd
 
-    # roofline of the dominant (only) kernel of the step
+    # roofline of the dominant kernel of the step (integer issue; see the work model above)
     mean_launch_s = sum(per_launch_ms) / len(per_launch_ms) / 1e3
     ops = areas * OPS_PER_AREA + darts * OPS_PER_DART + kept * OPS_PER_KEPT
     out_bytes = keys.numel() * keys.element_size() + (outw.numel() * 8 if outw is not None else 0)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak_ops = props.multi_processor_count * INT_LANES_PER_SM * sm_max * 1e6
     achieved = ops / mean_launch_s
-    tps = ncu_traffic_per_set()
+    tps = traffic_per_set(wl) if args.sets is None else None
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
                 "frac": achieved / peak_ops, "traffic": (tps * n if tps is not None else None),
+                "traffic_source": (f"profiles/traffic_{wl.lower()}.json" if tps is not None else
+                                   "none for the current kernel source"),
                 "ops_per_launch": ops, "units_per_launch": {"areas": areas, "darts": darts, "kept": kept,
                                                             "passes": passes},
                 "hbm_gbs_algorithmic": (b.indptr.nbytes + b.indices.nbytes + b.weights.nbytes
                                         + out_bytes) / mean_launch_s / 1e9,
                 "peak_source": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int32 lanes x "
-                               f"{sm_max:.0f} MHz (max SM clock)",
-                "peak_check": mix_ceiling(dmx, props, peak_ops, stream)}
-    roofline["peak_check"]["kernel_frac_of_ceiling"] = achieved / (roofline["peak_check"]["gop_per_s"] * 1e9)
+                               f"{sm_max:.0f} MHz (max SM clock)"}
+    if full:
+        roofline["peak_check"] = mix_ceiling(dmx, props, peak_ops, stream)
+        roofline["peak_check"]["kernel_frac_of_ceiling"] = achieved / (roofline["peak_check"]["gop_per_s"] * 1e9)
 
     cpu_baseline = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl == "W1":
+    if full and rank == 0 and world == 1 and not args.no_cpu_baseline and wl == "W1":
         cores = os.cpu_count() or 1
         v, ns, dt = time_oracle(b, 16000 * cores // 4, cores)
+        v1, ns1, dt1 = time_oracle(b, 4000, 1)
         cpu_baseline = {"value": v, "unit": "sets/s", "cores": cores, "kind": "oracle",
-                        "sample": f"first {ns} sets of W1 ({dt:.1f} s wall on {cores} threads)"}
+                        "sample": f"first {ns} sets of W1 ({dt:.1f} s wall on {cores} threads)",
+                        "single_thread": {"value": v1, "unit": "sets/s", "cores": 1,
+                                          "sample": f"first {ns1} sets of W1 ({dt1:.1f} s wall on 1 thread)"}}
+    # kernels per step: fast + general; the batched form adds classify, scan, scatter and, for
+    # sketches with a large-set threshold, the block-per-set kernel; W3S adds the class kernel
+    eff = tuning or {"form": form_id, "large_nnz": 2048 if args.large_nnz is None else args.large_nnz,
+                     "large_work": 0}
+    large_on = wl in ("W1", "W2") and (eff["large_nnz"] > 0 or eff["large_work"] > 0)
+    launches_per_step = (2 if eff["form"] != dmx.FORM_BATCHED else 5 + (1 if large_on else 0)) \
+        + (1 if wl == "W3S" else 0)
+    ctx.close()
+    return {"value": value, "t_max": t_max, "n": n, "kk": kk, "roofline": roofline, "plain_form": plain,
+            "e2e": e2e, "cpu_baseline": cpu_baseline, "clocks": clocks, "tuning": tuning,
+            "gpu_launches": launches_per_step * args.steps, "wall_s_timed": t_wall}
 
-    desc = {"W1": "W1: 1,000,000 sets x 256 distinct elements (d=2^20), Exp(1) fp32 weights; "
-                  "k=256 uint64 keys + 1-bit words",
-            "W2": "W2: 200,000 heavy-tailed sets (nnz log-normal median 100, sigma 1.5; ||x||_1 log-uniform "
-                  "1e-3..1e3), d=2^24; k=1024 uint64 keys",
-            "W3": "W3: 1,000,000 tf-idf-like sets (Zipf(1.1) tokens, nnz U{200..2000}), d=2^20; (L, K) = (64, 8) "
-                  "LSH uint32 values",
-            "W1B": "W1 sets (1,000,000 x 256 elements, Exp(1) weights); bottom-k sketches, k=256 sorted uint64 keys",
-            "W3S": f"W3 sets with each set's weight class normalised to ||x||_1 in [2^{args.norm_exp}, "
-                   f"2^{args.norm_exp + 1}) (Section 3); (L, K) = (64, 8) LSH uint32 values"}[wl]
+
+def gpu_arm(args):
+    import torch
+
+    import paper_2005_11547_gb300 as dmx
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, True)
+    dmx.build()
+    dmx.load()
+    props = torch.cuda.get_device_properties(local)
+    wl = args.workload
+    r = measure(args, wl, local, dist, props, full=True)
+    # the heavy-tailed batch (k = 1024) is part of the default run: its batched (autotuned,
+    # graph) and plain forms are timed on the same GPU after the headline workload
+    w2 = None
+    if wl == "W1" and args.sets is None and not args.no_w2:
+        import gc
+        gc.collect()
+        torch.cuda.empty_cache()
+        r2 = measure(args, "W2", local, dist, props, full=False)
+        w2 = {"workload": WL_DESC["W2"], "value": r2["value"], "unit": "sets/s",
+              "ms_per_step": r2["t_max"] * 1e3 / args.steps, "minhashes_per_s": r2["value"] * 1024,
+              "plain_form": r2["plain_form"], "roofline": r2["roofline"], "tuning": r2["tuning"],
+              "clocks": r2["clocks"], "gpu_launches": r2["gpu_launches"]}
+    desc = dict(WL_DESC)
+    desc["W3S"] = (f"W3 sets with each set's weight class normalised to ||x||_1 in [2^{args.norm_exp}, "
+                   f"2^{args.norm_exp + 1}) (Section 3); (L, K) = (64, 8) LSH uint32 values")
     if rank == 0:
         line = {
             "metric": METRIC if wl == "W1" else f"weighted sets/s ({wl})",
-            "value": value, "unit": "sets/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "value": r["value"], "unit": "sets/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["t_max"] * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "minhashes_per_s": value * kk,
-            "config": {"workload": desc if args.sets is None else f"{wl} prefix of {n} sets",
-                       "n_sets": n, "k": kk, "b": B_BITS if wl == "W1" else None, "seed": SEED,
+            "minhashes_per_s": r["value"] * r["kk"],
+            "config": {"workload": desc[wl] if args.sets is None else f"{wl} prefix of {r['n']} sets",
+                       "n_sets": r["n"], "k": r["kk"], "b": B_BITS if wl == "W1" else None, "seed": SEED,
                        "form": args.form + ("" if args.no_graph else " + CUDA graph")
-                               + (" + autotuned" if tuning else ""),
-                       "l2": "inputs 2 GB and outputs 2 GB per step, > 129 MB L2: no flush needed"},
-            "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
-            "plain_form": plain, "tuning": tuning,
-            "gpu_launches": (2 if (tuning["form"] if tuning else form_id) != dmx.FORM_BATCHED
-                             else (5 if wl in ("W3", "W1B") else (6 if wl == "W3S" else 6))) * args.steps,
-            "wall_s_timed": t_wall,
+                               + (" + autotuned" if r["tuning"] else ""),
+                       "l2": "inputs and outputs of a step are GBs, > 129 MB L2: no flush needed"},
+            "roofline": r["roofline"], "cpu_baseline": r["cpu_baseline"], "e2e": r["e2e"], "clocks": r["clocks"],
+            "plain_form": r["plain_form"], "tuning": r["tuning"],
+            "gpu_launches": r["gpu_launches"] + (w2["gpu_launches"] if w2 else 0),
+            "wall_s_timed": r["wall_s_timed"], "w2": w2,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 

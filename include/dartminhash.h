@@ -160,6 +160,13 @@ int dm_lsh_index_destroy(dm_lsh_index *ix);
 int dm_compare(dm_ctx *ctx, const uint64_t *a, const uint64_t *c, int64_t n_a, int64_t n_c, int32_t k,
                int32_t bits, int32_t mode, uint32_t *out, void *stream);
 
+/* Weighted Jaccard estimates from the counts of dm_compare (Section 1.1, "Similarity
+ * estimation"): out[i] = m[i] / k for keys (bits = 0; Eq. 1 makes it unbiased), and
+ * (m[i] / k - 2^-b) / (1 - 2^-b) for b-bit fields (bits = b), each step a correctly rounded
+ * binary64 operation in that order.  matches: device uint32[n]; out: device double[n].  Needs no
+ * context; runs on the current device, asynchronously on `stream`. */
+int dm_estimate_jaccard(const uint32_t *matches, int64_t n, int32_t k, int32_t bits, double *out, void *stream);
+
 /* Wide-range minhash keys: 64-bit element ids and binary64 weights, for the norms the binary32
  * entry points cannot reach (Section 4, "Synthetic data", hashes 64-bit ids with double weights;
  * Table 1 runs ||x||_1 = 2^{+-64} and 2^{+-512}).  Same dart process as dm_sketch (Section 2,

@@ -354,6 +354,17 @@ def compare(a, c, k: int, bits: int = 0, mode: str = "pairs"):
     return np.stack([(va[i][None, :] == vc).sum(axis=1) for i in range(len(va))]).astype(np.uint32)
 
 
+def estimate_jaccard(matches, k: int, bits: int = 0):
+    """Weighted Jaccard estimates from agreeing-slot counts m (Section 1.1, "Similarity estimation"):
+    m / k for keys, since E[m] = k J (Eq. 1); for b-bit fields E[m] = k (J + (1 - J) 2^-b), which
+    solved for J gives (m / k - 2^-b) / (1 - 2^-b).  binary64, one rounding per operation."""
+    p = np.asarray(matches, dtype=np.float64) / np.float64(k)
+    if bits == 0:
+        return p
+    r = np.float64(2.0) ** -bits
+    return (p - r) / (np.float64(1.0) - r)
+
+
 DART_DTYPE = np.dtype({
     "names": ["pos", "i", "nu", "rho", "w", "r", "j", "u", "v", "code", "q"],
     "formats": [np.int64, np.uint32, np.int32, np.int32, np.uint64, np.uint64, np.int32,

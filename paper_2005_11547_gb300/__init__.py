@@ -58,6 +58,7 @@ def load(path: str | None = None):
             "dm_lsh": ([P, P, P, P, i64, i32, i32, u64, P, P], ctypes.c_int),
             "dm_bottomk": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
             "dm_compare": ([P, P, P, i64, i64, i32, i32, i32, P, P], ctypes.c_int),
+            "dm_estimate_jaccard": ([P, i64, i32, i32, P, P], ctypes.c_int),
             "dm_lsh_scaled": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_lsh_index_create": ([ctypes.POINTER(P), ctypes.c_int, i32, i64], ctypes.c_int),
             "dm_lsh_index_insert": ([P, P, P, i64, P], ctypes.c_int),
@@ -372,13 +373,18 @@ def dm_compare(ctx: Context, a, c, k: int, bits: int = 0, cross: bool = False, o
     return out
 
 
-def estimate_jaccard(matches, k: int, bits: int = 0):
-    """J estimate from agreeing-slot counts: m / k for keys, (m / k - 2^-b) / (1 - 2^-b) for b bits."""
-    p = matches / float(k)
-    if bits == 0:
-        return p
-    r = 2.0 ** -bits
-    return (p - r) / (1.0 - r)
+def estimate_jaccard(matches, k: int, bits: int = 0, out=None, stream=None):
+    """Weighted Jaccard estimates (float64 tensor) from dm_compare's agreeing-slot counts, computed
+    by the library (dm_estimate_jaccard): m / k for keys, (m / k - 2^-b) / (1 - 2^-b) for b-bit
+    fields.  matches: uint32 counts (int32 CUDA tensor), as dm_compare returns them."""
+    import torch
+    n = matches.numel()
+    if out is None:
+        out = torch.empty(matches.shape, dtype=torch.float64, device=matches.device)
+    _need(out, n, "out")
+    _check(load().dm_estimate_jaccard(_dev_ptr(matches, "uint32", "matches"), n, int(k), int(bits),
+                                      _dev_ptr(out, "float64", "out"), _stream(stream)), "dm_estimate_jaccard")
+    return out
 
 
 def dm_sketch_host(ctx: Context, indptr, indices, weights, k: int, seed: int, out_keys=None, b: int = 0,

@@ -119,7 +119,34 @@ __global__ void __launch_bounds__(128) cross_words(const uint64_t *a, const uint
     }
 }
 
+// Weighted Jaccard estimates from agreeing-slot counts (Section 1.1): p = m / k estimates J for
+// keys (Eq. 1); for b-bit fields E[m] / k = J + (1 - J) 2^-b, so J is estimated by
+// (p - 2^-b) / (1 - 2^-b).  binary64, IEEE-rounded division and subtraction in that order.
+__global__ void __launch_bounds__(256) estimate_kernel(const uint32_t *m, int64_t n, double k, double r,
+                                                       int bbit, double *out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double p = __ddiv_rn((double)m[i], k);
+        out[i] = bbit ? __ddiv_rn(__dsub_rn(p, r), __dsub_rn(1.0, r)) : p;
+    }
+}
+
 }  // namespace
+
+extern "C" int dm_estimate_jaccard(const uint32_t *matches, int64_t n, int32_t k, int32_t bits, double *out,
+                                   void *stream) {
+    if (n < 0 || k < 1 || k > 8192) return DM_EINVAL;
+    if (!(bits == 0 || bits == 1 || bits == 2 || bits == 4 || bits == 8 || bits == 16 || bits == 32)) return DM_EINVAL;
+    if (n == 0) return DM_OK;
+    if (!matches || !out) return DM_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DM_ECUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t blocks = (n + 255) / 256, cap = 8LL * (sms > 0 ? sms : 1);
+    estimate_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, (cudaStream_t)stream>>>(
+        matches, n, (double)k, bits ? 1.0 / (double)(1ull << bits) : 0.0, bits != 0, out);
+    return cudaGetLastError() == cudaSuccess ? DM_OK : DM_ECUDA;
+}
 
 extern "C" int dm_compare(dm_ctx *ctx, const uint64_t *a, const uint64_t *c, int64_t n_a, int64_t n_c, int32_t k,
                           int32_t bits, int32_t mode, uint32_t *out, void *stream) {

@@ -323,9 +323,9 @@ struct BottomKSink {
 //  * area step (every lane on its next area): the area hash a gives the Poisson count X, and
 //    the first dart's hash M(a + gamma) is evaluated at once (weight and rank tests).  A kept
 //    dart goes to the kept queue; an area with X >= 2 goes to the dart queue with the counter
-//    of its second dart and the number of darts left.
-//  * dart step (32 queued areas): the next dart of each is hashed and tested; an area with
-//    darts left goes back to the dart queue.
+//    of its second dart (j = 1) and the area's Poisson uniform.
+//  * dart step (32 queued areas): dart j of each is hashed and tested; the area goes back to
+//    the dart queue when dart j + 1 exists (X > j + 1: the uniform reaches T[j + 1]).
 //  * bucket step (32 queued kept darts): the bucket/fingerprint hash, the rank code and the
 //    sink.
 // A queue is served as soon as it holds 32 entries, so neither exceeds 64; both carry over
@@ -365,13 +365,14 @@ struct FastMem {
     RegA *ra;                           // [kFastRegions]
     ElRec *el;                          // [kSeg]
     uint4 *kq;                          // kept queue [kQ]: dart hash (low, high word), row r, region nu
-    uint4 *xp;                          // dart queue [kQ]: uthr | darts left << 26, vmax | nu << 24, r, ulo
-    uint64_t *xo;                       // dart queue [kQ]: counter of the area's next dart
+    uint4 *xp;                          // dart queue [kQ]: uthr | j << 26, vmax | nu << 24, r, Poisson uniform
+    uint64_t *xo;                       // dart queue [kQ]: counter of the area's dart j
+    uint32_t *xl;                       // dart queue [kQ]: u floor of the area (sinks with a lower cut)
     RegB *rb;                           // [kFastRegions]
 };
 
 constexpr size_t kFastPathBytes = (size_t)kFastRegions * (sizeof(RegA) + sizeof(RegB)) +
-                                  (size_t)kSeg * sizeof(ElRec) + (size_t)kQ * (16 + 16 + 8);
+                                  (size_t)kSeg * sizeof(ElRec) + (size_t)kQ * (16 + 16 + 8 + 4);
 static_assert(sizeof(RegA) == 16 && sizeof(RegB) == 8 && sizeof(ElRec) == 16, "record layout");
 static_assert(kFastPathBytes % 16 == 0, "fast-path tables keep 16-byte alignment");
 
@@ -382,7 +383,8 @@ __device__ __forceinline__ FastMem carve_fast(unsigned char *base) {
     m.kq = reinterpret_cast<uint4 *>(m.el + kSeg);
     m.xp = m.kq + kQ;
     m.xo = reinterpret_cast<uint64_t *>(m.xp + kQ);
-    m.rb = reinterpret_cast<RegB *>(m.xo + kQ);
+    m.xl = reinterpret_cast<uint32_t *>(m.xo + kQ);
+    m.rb = reinterpret_cast<RegB *>(m.xl + kQ);
     return m;
 }
 
@@ -483,12 +485,13 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         kt += __popc(km);
         if (COUNT && keep) cnt[2]++;
     };
-    auto push_darts = [&](bool more, uint64_t op, uint32_t w0, uint32_t w1, uint32_t r, uint32_t ulo) {
+    auto push_darts = [&](bool more, uint64_t op, uint32_t w0, uint32_t w1, uint32_t r, uint32_t up, uint32_t ulo) {
         const unsigned xm = __ballot_sync(kFull, more);
         if (more) {
             const uint32_t i = (xt + __popc(xm & lt)) & (kQ - 1);
             m.xo[i] = op;
-            m.xp[i] = make_uint4(w0, w1, r, ulo);
+            m.xp[i] = make_uint4(w0, w1, r, up);
+            if constexpr (LOWER) m.xl[i] = ulo;
         }
         xt += __popc(xm);
     };
@@ -516,19 +519,24 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         const bool v = (uint32_t)lane < n;
         uint64_t op = 0;
         uint4 x = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t lo = 0;
         if (v) {
             const uint32_t i = (xh + (uint32_t)lane) & (kQ - 1);
             op = m.xo[i];
             x = m.xp[i];
+            if constexpr (LOWER) lo = m.xl[i];
         }
         xh += n;
         __syncwarp();                             // every lane has read its entry before any push
         const uint64_t d = mix64(op);
         const uint32_t u = (uint32_t)(d >> 40), vv = (uint32_t)(d >> 16) & kUMask;
         bool keep = v && u < (x.x & 0x3FFFFFFu) && vv <= (x.y & kUMask);
-        if constexpr (LOWER) keep = keep && u >= x.w;
+        if constexpr (LOWER) keep = keep && u >= lo;
         push_kept(keep, d, x.z, x.y >> 24);
-        push_darts(v && (x.x >> 26) > 1u, op + kGolden, x.x - (1u << 26), x.y, x.z, x.w);
+        // dart j + 1 exists iff X > j + 1, i.e. the area's Poisson uniform reaches T[j + 1]
+        const uint32_t jn = (x.x >> 26) + 1u;
+        const bool more = v && jn < 12u && x.w >= c_pois[jn < 12u ? jn : 11u];
+        push_darts(more, op + kGolden, x.x + (1u << 26), x.y, x.z, x.w, lo);
     };
 
     for (int64_t tile = first; tile < end;) {
@@ -574,24 +582,28 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         WalkF s{};
         if (left) s.locate(lo, n_el, m);
         for (uint32_t st = 0; st < steps; ++st) {
-            for (;;) {                            // serve full queues (each below 32 afterwards)
-                if (kt - kh >= 32u) kept_step(32u);
-                else if (xt - xh >= 32u) dart_step(32u);
-                else break;
+            if (max(kt - kh, xt - xh) >= 32u) {
+                for (;;) {                        // serve full queues (each below 32 afterwards)
+                    if (kt - kh >= 32u) kept_step(32u);
+                    else if (xt - xh >= 32u) dart_step(32u);
+                    else break;
+                }
             }
-            // area step
+            // area step: X >= 1 and X >= 2 decide the first dart and the dart queue; the count
+            // itself is resolved dart by dart from the Poisson uniform ua
             const bool act = left != 0;
             const uint64_t a = mix64(s.ctr);
-            const uint32_t X = act ? (uint32_t)poisson1((uint32_t)(a >> 32), c_pois) : 0u;
+            const uint32_t ua = (uint32_t)(a >> 32);
+            const bool x1 = act && ua >= c_pois[0], x2 = act && ua >= c_pois[1];
             const uint32_t uthr = s.r + 1 == s.rhi ? s.lastthr : (1u << 25);
             const uint32_t ulo = LOWER && s.r == s.rlo ? s.firstlo : 0u;
             const uint64_t d = mix64(a + kGolden);
             const uint32_t u = (uint32_t)(d >> 40), vv = (uint32_t)(d >> 16) & kUMask;
-            bool keep = X != 0 && u < uthr && vv <= s.vmax;
+            bool keep = x1 && u < uthr && vv <= s.vmax;
             if constexpr (LOWER) keep = keep && u >= ulo;
-            if (COUNT) { cnt[0] += act; cnt[1] += X; }
+            if (COUNT) { cnt[0] += act; cnt[1] += act ? (uint32_t)poisson1(ua, c_pois) : 0u; }
             push_kept(keep, d, s.r, (uint32_t)s.nu);
-            push_darts(X >= 2, a + 2 * kGolden, uthr | ((X - 1) << 26), s.vmax | ((uint32_t)s.nu << 24), s.r, ulo);
+            push_darts(x2, a + 2 * kGolden, uthr | (1u << 26), s.vmax | ((uint32_t)s.nu << 24), s.r, ua, ulo);
             if (act && --left) s.advance(n_el, m);
         }
     }

@@ -90,11 +90,19 @@ def test_library_sketches_estimate_jaccard(dmx, torch_mod, ctx, oracle_mod):
     ox = oracle_mod.sketch(xs.indptr, xs.indices, xs.weights, k, 3, threads=16)
     oy = oracle_mod.sketch(ys.indptr, ys.indices, ys.weights, k, 3, threads=16)
     assert np.array_equal(m, oracle_mod.compare(ox, oy, k))
-    assert abs(dmx.estimate_jaccard(m, k).mean() - 0.5) < 0.01
+    est = dmx.estimate_jaccard(dmx.dm_compare(ctx, sx, sy, k), k).cpu().numpy()
+    assert np.array_equal(est, oracle_mod.estimate_jaccard(m, k))          # the same binary64 steps
+    assert abs(est.mean() - 0.5) < 0.01
     wx = dmx.dm_sketch_bbit(ctx, *to_dev(xs), k, 1, 3)
     wy = dmx.dm_sketch_bbit(ctx, *to_dev(ys), k, 1, 3)
     m1 = dmx.dm_compare(ctx, wx, wy, k, bits=1).cpu().numpy().view(np.uint32)
-    assert abs(dmx.estimate_jaccard(m1, k, bits=1).mean() - 0.5) < 0.02
+    est1 = dmx.estimate_jaccard(dmx.dm_compare(ctx, wx, wy, k, bits=1), k, bits=1).cpu().numpy()
+    assert np.array_equal(est1, oracle_mod.estimate_jaccard(m1, k, bits=1))
+    assert abs(est1.mean() - 0.5) < 0.02
+    for b in (2, 4, 8, 16, 32):                         # every b-bit correction, on all counts 0..k
+        mm = np.arange(k + 1, dtype=np.uint32)
+        got = dmx.estimate_jaccard(torch.from_numpy(mm.view(np.int32)).cuda(), k, bits=b).cpu().numpy()
+        assert np.array_equal(got, oracle_mod.estimate_jaccard(mm, k, bits=b))
     cross = dmx.dm_compare(ctx, sx[:50], sy[:60], k, cross=True).cpu().numpy().view(np.uint32)
     assert np.array_equal(np.diag(cross[:50, :50]), m[:50])
 

@@ -23,17 +23,21 @@ def dmx():
     return dmx
 
 
-def trace(n, seed, max_nnz=5000):
-    """W4-like requests: nnz = min(max_nnz, floor(Pareto(1.2) + 1)), weights U(0, 5], k uniform
-    over {64, 256, 1024}, seeds 1 or 2, arrivals at 50,000/s."""
+def trace(n, seed, max_nnz=100_000):
+    """W4-like requests (the serving workload's sizes): nnz = min(max_nnz, floor(Pareto(1.2) + 1)),
+    weights U(0, 5], k uniform over {64, 256, 1024}, seeds 1 or 2, arrivals at 50,000/s.  The
+    first request and one in the middle have the largest nnz the workload allows (100,000) with
+    k = 1024, so they run alone at the start and in the mix later."""
     rng = np.random.default_rng(seed)
     lens = np.minimum(max_nnz, np.floor(rng.pareto(1.2, size=n) + 1.0)).astype(np.int64)
-    lens[:3] = [max_nnz, 3000, 2100]           # sets for the block-per-set path
+    lens[:3] = [100_000, 3000, 2100]           # sets for the block-per-set path
+    lens[n // 2] = 100_000
     ip = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(lens, out=ip[1:])
     idx = workloads._ragged_distinct(rng, lens, 1 << 24)
     w = (5.0 * (1.0 - rng.random(int(ip[-1])))).astype(np.float32)
     ks = rng.choice(np.array([64, 256, 1024], dtype=np.int32), size=n)
+    ks[0] = ks[n // 2] = 1024
     seeds = rng.integers(1, 3, size=n).astype(np.uint64)
     arr = np.cumsum(rng.exponential(1.0 / 50_000, size=n) * 1e9).astype(np.int64)
     return ip, idx, w, ks, seeds, arr
@@ -79,7 +83,7 @@ def test_replay_matches_oracle(dmx, oracle_mod, mode):
 def test_tickets_from_threads_match_dm_sketch(dmx, oracle_mod):
     """Submissions from several host threads; each result equals the oracle's for its row."""
     import threading
-    ip, idx, w, ks, seeds, _ = trace(600, 5, max_nnz=3000)
+    ip, idx, w, ks, seeds, _ = trace(600, 5)
     srv = dmx.Server(0, lanes=3)
     outs = [None] * 600
     errors = []

@@ -67,3 +67,22 @@ def test_compare_follows_the_collision_laws(oracle_mod, bits):
     m = oracle_mod.compare(a, c, k, bits=bits).astype(np.float64)
     p = J + (1 - J) * (2.0 ** -bits if bits else 0.0)
     assert abs(m.sum() - k * p.sum()) / math.sqrt(k * (p * (1 - p)).sum()) < 4
+
+
+def test_estimator_is_unbiased_and_fixes_its_end_points(oracle_mod):
+    """Section 1.1: with m ~ Bin(k, J + (1 - J) 2^-b) agreeing b-bit fields (p = J for keys), the
+    estimate has expectation exactly J (summed over the binomial pmf in rationals); all slots
+    agreeing gives 1, and the chance level k 2^-b gives 0."""
+    from fractions import Fraction
+    from math import comb
+    k = 64
+    for bits in (0, 1, 2, 4, 8):
+        m = np.arange(k + 1, dtype=np.uint32)
+        est = oracle_mod.estimate_jaccard(m, k, bits=bits)
+        assert est[k] == 1.0
+        if bits and (k >> bits) << bits == k:
+            assert est[k >> bits] == 0.0
+        for J in (Fraction(1, 5), Fraction(1, 2), Fraction(7, 8)):
+            p = J if bits == 0 else J + (1 - J) / 2 ** bits
+            mean = sum(comb(k, i) * p ** i * (1 - p) ** (k - i) * Fraction(float(est[i])) for i in range(k + 1))
+            assert abs(float(mean - J)) < 1e-12, (bits, J)
