@@ -619,17 +619,23 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
 
 // ==========================================================================================
 // General path: every region (nu, rho), columns w and rows r, in 64-bit arithmetic, with the
-// same step loop as the fast path (a lane with no dart left fetches its next area; every lane
-// with a dart left evaluates one).  A dart of the current area has rank (pb + (u << sh)) 2^-S
-// with the area's rank base pb (a multiple of 2^24), sh = 38 - nu and S = 62 - rho, and hits x
-// iff v <= vmax.
+// same three kinds of warp-wide steps as the fast path (area steps with the area's first dart,
+// dart steps over queued areas, bucket steps over queued kept darts).  A dart of an area has
+// rank (pb + (u << sh)) 2^-S with the area's rank base pb (a multiple of 2^24), sh = 38 - nu and
+// S = 62 - rho, and hits x iff v <= vmax; pv = pb + vmax holds both.  A dart is kept iff its
+// binary32 rank code lies in [bits(theta_{p-1}), bits(theta_p)) (the lower bound only for the
+// sinks that must not see a dart twice).
 // ==========================================================================================
 struct GenMem {
     uint64_t *te, *tF, *toff;
     int *tnu;
+    uint4 *kq;                          // kept queue [kQ]: dart hash (low, high word), rank code, unused
+    uint4 *xa;                          // dart queue [kQ]: counter of the area's dart j (low, high), pv (low, high)
+    uint2 *xb;                          // dart queue [kQ]: j | nu << 4 | rho << 10, the area's Poisson uniform
 };
 
-constexpr size_t kGenPathBytes = 3 * 32 * 8 + 32 * 4;
+constexpr size_t kGenPathBytes = 3 * 32 * 8 + 32 * 4 + (size_t)kQ * (16 + 16 + 8);
+static_assert((3 * 32 * 8 + 32 * 4) % 16 == 0, "general-path queues keep 16-byte alignment");
 
 __device__ __forceinline__ GenMem carve_gen(unsigned char *base) {
     GenMem m;
@@ -637,6 +643,9 @@ __device__ __forceinline__ GenMem carve_gen(unsigned char *base) {
     m.tF = m.te + 32;
     m.toff = m.tF + 32;
     m.tnu = reinterpret_cast<int *>(m.toff + 32);
+    m.kq = reinterpret_cast<uint4 *>(m.tnu + 32);
+    m.xa = m.kq + kQ;
+    m.xb = reinterpret_cast<uint2 *>(m.xa + kQ);
     return m;
 }
 
@@ -760,6 +769,71 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
                         const GenMem &m, Sink &sink, int lane, unsigned long long *cnt, int escale = 0,
                         int part = 0, int nparts = 1) {
     constexpr bool LOWER = Sink::kLowerCut;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t kh = 0, kt = 0, xh = 0, xt = 0;     // kept and dart queues: heads and tails
+
+    // binary32 code of rank = P 2^-S rounded toward zero: exact u64 -> f32 conversion in
+    // round-toward-zero mode, then the exponent lowered by S; kept iff in the pass's code range
+    auto rank_code = [](uint64_t P, uint32_t S) -> uint32_t {
+        return P ? __float_as_uint(__ull2float_rz(P)) - (S << 23) : 0u;
+    };
+    auto in_band = [&](uint32_t code) -> bool {
+        if constexpr (LOWER) return code < pc.cthr && code >= pc.cthr_lo;
+        return code < pc.cthr;
+    };
+    auto push_kept = [&](bool keep, uint64_t d, uint32_t code) {
+        const unsigned km = __ballot_sync(kFull, keep);
+        if (keep) m.kq[(kt + __popc(km & lt)) & (kQ - 1)] = make_uint4((uint32_t)d, (uint32_t)(d >> 32), code, 0u);
+        kt += __popc(km);
+        if (COUNT && keep) cnt[2]++;
+    };
+    auto push_darts = [&](bool more, uint64_t op, uint64_t pv, uint32_t w, uint32_t ua) {
+        const unsigned xm = __ballot_sync(kFull, more);
+        if (more) {
+            const uint32_t i = (xt + __popc(xm & lt)) & (kQ - 1);
+            m.xa[i] = make_uint4((uint32_t)op, (uint32_t)(op >> 32), (uint32_t)pv, (uint32_t)(pv >> 32));
+            m.xb[i] = make_uint2(w, ua);
+        }
+        xt += __popc(xm);
+    };
+    // bucket step over the n (<= 32) oldest kept darts
+    auto kept_step = [&](uint32_t n) {
+        __syncwarp();
+        const bool v = (uint32_t)lane < n;
+        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+        if (v) q = m.kq[(kh + (uint32_t)lane) & (kQ - 1)];
+        kh += n;
+        const uint64_t h = mix64((((uint64_t)q.y << 32) | q.x) ^ kSlotSalt);
+        bool need = false;
+        if (v) need = sink.put(h, q.z);
+        __syncwarp();
+        sink.after_batch(lane, need);
+    };
+    // dart step over the n (<= 32) oldest queued areas: dart j of each; the area goes back to
+    // the queue when dart j + 1 exists (its Poisson uniform reaches T[j + 1])
+    auto dart_step = [&](uint32_t n) {
+        __syncwarp();
+        const bool v = (uint32_t)lane < n;
+        uint4 xa = make_uint4(0u, 0u, 0u, 0u);
+        uint2 xb = make_uint2(0u, 0u);
+        if (v) {
+            const uint32_t i = (xh + (uint32_t)lane) & (kQ - 1);
+            xa = m.xa[i];
+            xb = m.xb[i];
+        }
+        xh += n;
+        __syncwarp();                             // every lane has read its entry before any push
+        const uint64_t op = ((uint64_t)xa.y << 32) | xa.x, pv = ((uint64_t)xa.w << 32) | xa.z;
+        const uint64_t d = mix64(op);
+        const uint32_t u = (uint32_t)(d >> 40), vv = (uint32_t)(d >> 16) & kUMask;
+        const uint32_t nu = (xb.x >> 4) & 63u, rho = (xb.x >> 10) & 63u;
+        const uint32_t code = rank_code((pv & ~(uint64_t)kUMask) + ((uint64_t)u << (38u - nu)), 62u - rho);
+        push_kept(v && vv <= ((uint32_t)pv & kUMask) && in_band(code), d, code);
+        const uint32_t jn = (xb.x & 15u) + 1u;
+        const bool more = v && jn < 12u && xb.y >= c_pois[jn < 12u ? jn : 11u];
+        push_darts(more, op + kGolden, pv, xb.x + 1u, xb.y);
+    };
+
     for (int64_t tile = first; tile < end; tile += stride) {
         const int64_t pos = tile + lane;
         int nutop = -1;
@@ -783,46 +857,41 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
         const uint64_t share = (total + lanes - 1) / lanes;
         const uint64_t lo = share * (32ull * (uint64_t)part + (uint64_t)lane);
         uint64_t left = lo < total ? min(share, total - lo) : 0;   // areas of this lane
-        WalkG s;
+        const uint64_t lo0 = share * 32ull * (uint64_t)part;        // lane 0 has the largest share
+        const uint64_t steps = lo0 < total ? min(share, total - lo0) : 0;
+        WalkG s{};
         if (left) s.locate(lo, m, pc);
-        bool fresh = true;              // the walk sits on the next area to fetch
-        uint32_t nx = 0, vmax = 0, sh = 0, S = 0;
-        uint64_t c = 0, pb = 0;
-        while (__any_sync(kFull, left != 0 || nx != 0)) {
-            bool need = false;
-            if (nx == 0 && left) {
-                if (!fresh) s.advance(m, pc);
-                fresh = false;
-                --left;
-                c = mix64(s.ctr);
-                nx = (uint32_t)poisson1((uint32_t)(c >> 32), c_pois);
-                const uint64_t pv = s.pv();
-                pb = pv & ~(uint64_t)kUMask;
-                vmax = (uint32_t)pv & kUMask;
-                sh = 38 - (uint32_t)s.nu;
-                S = 62 - (uint32_t)s.rho;
-                if (COUNT) { cnt[0]++; cnt[1] += nx; }
-            }
-            if (nx) {
-                --nx;
-                c += kGolden;
-                const uint64_t d = mix64(c);
-                const uint32_t u = (uint32_t)(d >> 40), v = (uint32_t)(d >> 16) & kUMask;
-                const uint64_t P = pb + ((uint64_t)u << sh);
-                // binary32 code of rank = P 2^-S rounded toward zero (exact u64 -> f32
-                // conversion in round-toward-zero mode, then the exponent lowered by S)
-                const uint32_t code = P ? __float_as_uint(__ull2float_rz(P)) - (S << 23) : 0u;
-                bool keep = v <= vmax && code < pc.cthr;
-                if (LOWER) keep = keep && code >= pc.cthr_lo;
-                if (keep) {
-                    need = sink.put(mix64(d ^ kSlotSalt), code);
-                    if (COUNT) cnt[2]++;
+        for (uint64_t st = 0; st < steps; ++st) {
+            if (max(kt - kh, xt - xh) >= 32u) {
+                for (;;) {                        // serve full queues (each below 32 afterwards)
+                    if (kt - kh >= 32u) kept_step(32u);
+                    else if (xt - xh >= 32u) dart_step(32u);
+                    else break;
                 }
             }
-            __syncwarp();
-            sink.after_batch(lane, need);
+            // area step: X >= 1 and X >= 2 from the Poisson uniform ua; the first dart at once
+            const bool act = left != 0;
+            const uint64_t a = mix64(s.ctr);
+            const uint32_t ua = (uint32_t)(a >> 32);
+            const bool x1 = act && ua >= c_pois[0], x2 = act && ua >= c_pois[1];
+            const uint64_t pv = s.pv();
+            const uint64_t d = mix64(a + kGolden);
+            const uint32_t u = (uint32_t)(d >> 40), vv = (uint32_t)(d >> 16) & kUMask;
+            const uint32_t code = rank_code((pv & ~(uint64_t)kUMask) + ((uint64_t)u << (38 - s.nu)),
+                                            62u - (uint32_t)s.rho);
+            if (COUNT) { cnt[0] += act; cnt[1] += act ? (uint32_t)poisson1(ua, c_pois) : 0u; }
+            push_kept(x1 && vv <= ((uint32_t)pv & kUMask) && in_band(code), d, code);
+            push_darts(x2, a + 2 * kGolden, pv, 1u | ((uint32_t)s.nu << 4) | ((uint32_t)s.rho << 10), ua);
+            if (act && --left) s.advance(m, pc);
         }
     }
+    for (;;) {                                    // drain both queues
+        if (kt - kh >= 32u) kept_step(32u);
+        else if (xt != xh) dart_step(min(xt - xh, 32u));
+        else if (kt != kh) kept_step(kt - kh);
+        else break;
+    }
+    __syncwarp();
     return 0;
 }
 
