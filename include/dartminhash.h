@@ -201,12 +201,15 @@ int dm_sketch_f64_bbit(dm_ctx *ctx, const int64_t *indptr, const uint64_t *indic
 int dm_mix64_burn(int64_t blocks, int32_t iters, uint64_t seed, uint64_t *out, void *stream);
 
 /* dm_sketch / dm_sketch_bbit with HOST arrays: indptr, indices, weights, out_keys and
- * out_words are host pointers (page-locked memory gives full copy speed).  b = 0 computes keys
+ * out_words are host pointers (page-locked memory gives full speed).  b = 0 computes keys
  * only (out_keys required, out_words ignored); b in {1, 2, 4, 8, 16, 32} also writes the b-bit
- * words (out_keys may then be NULL).  The library copies the batch to context-owned device
- * buffers on `stream` in chunks, overlapping the copies of one chunk with the kernel of the
- * previous one, and returns after every output is back in host memory (synchronous).
- * Returns DM_ENOMEM if the staging buffers would exceed the context's memory budget. */
+ * words (out_keys may then be NULL).  Two ways to move the data (DM_OPT_HOST_MODE): in place,
+ * where the kernels read the page-locked, mapped host arrays and write the outputs there
+ * directly (no device copy of the batch is made); or staged, where the library copies the batch
+ * to context-owned device buffers on `stream` in chunks, overlapping the copies of one chunk with
+ * the kernel of the previous one.  Either way the call returns after every output is in host
+ * memory (synchronous).  Returns DM_ENOMEM if the staging buffers would exceed the context's
+ * memory budget. */
 int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
                    int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_keys,
                    uint64_t *out_words, void *stream);
@@ -269,9 +272,15 @@ enum dm_option {
                                    inspects (phi0 t + sum_i (log2(1 + t x_i) + 1) +
                                    nnz log2(1 + phi0/|x|_1)) reaches this value also gets a block of
                                    8 warps (default 0 = never; dm_lsh never does) */
-    DM_OPT_HOST_CHUNKS = 10     /* dm_sketch_host: number of chunks (1..256, default 8) a batch is
+    DM_OPT_HOST_CHUNKS = 10,    /* dm_sketch_host: number of chunks (1..256, default 8) a batch is
                                    split into, so that one chunk's copies overlap another's kernels
                                    (chunks hold at least 4,096 sets) */
+    DM_OPT_HOST_MODE = 11       /* dm_sketch_host: 0 = staged (chunked copies to device buffers);
+                                   1 = in place (the kernels read the input arrays and write the
+                                   outputs through the device's mapping of page-locked host memory,
+                                   so the transfers ride on the kernels' own loads and stores; the
+                                   call fails with DM_EINVAL if an array is not mapped); 2 (default)
+                                   = in place when every array is page-locked and mapped, else staged */
 };
 int dm_set_option(dm_ctx *ctx, int option, int64_t value);
 

@@ -21,11 +21,12 @@ from .build import LIB, build
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
            "dm_sketch_host", "dm_bottomk", "dm_compare", "dm_lsh_scaled", "dm_weight_classes", "LshIndex", "estimate_jaccard", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
            "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
-           "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "OPT_LARGE_WORK", "OPT_HOST_CHUNKS", "FORM_BATCHED",
+           "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "OPT_LARGE_WORK", "OPT_HOST_CHUNKS", "OPT_HOST_MODE", "HOST_STAGED", "HOST_IN_PLACE", "HOST_AUTO", "FORM_BATCHED",
            "FORM_PLAIN", "FORM_PERSISTENT", "dm_autotune", "Tuning", "Server", "EAGAIN"]
 
 OPT_PHI0, OPT_COUNTERS, OPT_FORM, OPT_WARPS_PER_BLOCK, OPT_LSH_PHI0, OPT_LARGE_NNZ = 1, 2, 3, 4, 5, 6
-OPT_GRAPH, OPT_TUNED, OPT_LARGE_WORK, OPT_HOST_CHUNKS = 7, 8, 9, 10
+OPT_GRAPH, OPT_TUNED, OPT_LARGE_WORK, OPT_HOST_CHUNKS, OPT_HOST_MODE = 7, 8, 9, 10, 11
+HOST_STAGED, HOST_IN_PLACE, HOST_AUTO = 0, 1, 2
 EAGAIN, ETIMEOUT = 7, 4
 FORM_BATCHED, FORM_PLAIN, FORM_PERSISTENT = 0, 1, 2
 _lock = threading.Lock()

@@ -68,6 +68,7 @@ struct dm_ctx {
     int large_nnz = 2048;          // batched form: sets with this many elements get a block
     float large_work = 0.f;        // batched form: sets with this work estimate get a block
     int host_chunks = 8;           // host-buffer entry: chunks a batch is split into
+    int host_mode = 2;             // host-buffer entry: 0 staged, 1 in place, 2 in place when possible
     // staging for the host-buffer entry points
     void *d_stage = nullptr;
     size_t d_stage_bytes = 0;
@@ -594,6 +595,17 @@ int dm_sketch_f64_bbit(dm_ctx *ctx, const int64_t *indptr, const uint64_t *indic
     return cuda_fail(dm::launch_wide(wp, ctx->counters != nullptr, ctx->sm_count, (cudaStream_t)stream));
 }
 
+// The device address of a page-locked, mapped host array (null when it is not one).
+const void *mapped_view(const void *h) {
+    if (!h) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();                       // an unregistered pointer is not an error here
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
                    int64_t n_sets, int32_t k, int32_t b, uint64_t seed, uint64_t *out_keys,
                    uint64_t *out_words, void *stream) {
@@ -607,6 +619,21 @@ int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e);
     if (indptr[0] != 0 || indptr[n_sets] < 0) return DM_EINVAL;
+    if (ctx->host_mode != 0) {
+        // in place: the kernels address the host arrays through their device mapping
+        const void *dip = mapped_view(indptr), *dix = mapped_view(indices), *dw = mapped_view(weights);
+        void *dk = out_keys ? const_cast<void *>(mapped_view(out_keys)) : nullptr;
+        void *dwd = b > 0 ? const_cast<void *>(mapped_view(out_words)) : nullptr;
+        const bool ok = dip && dix && dw && (!out_keys || dk) && (b == 0 || dwd);
+        if (ok) {
+            Range range("dm_sketch_host");
+            rc = run_sketch(ctx, (const int64_t *)dip, (const uint32_t *)dix, (const float *)dw, n_sets, k, b, seed,
+                            (uint64_t *)dwd, (uint64_t *)dk, st);
+            if (rc) return rc;
+            return cuda_fail(cudaStreamSynchronize(st));
+        }
+        if (ctx->host_mode == 1) return DM_EINVAL;
+    }
     const int64_t words = b > 0 ? ((int64_t)k * b + 63) / 64 : 0;
     // chunks of about 1/host_chunks of the batch (at least 4,096 sets), two buffer sets in flight;
     // the first two and the last two chunks are a quarter and a half of that, so that the copy
@@ -869,6 +896,10 @@ int dm_set_option(dm_ctx *ctx, int option, int64_t value) {
         case DM_OPT_HOST_CHUNKS:
             if (value < 1 || value > 256) return DM_EINVAL;
             ctx->host_chunks = (int)value;
+            return DM_OK;
+        case DM_OPT_HOST_MODE:
+            if (value < 0 || value > 2) return DM_EINVAL;
+            ctx->host_mode = (int)value;
             return DM_OK;
         case DM_OPT_LSH_PHI0:
             if (value < 1 || value > 1024 * 1024) return DM_EINVAL;

@@ -299,27 +299,46 @@ def test_counters_and_streams(dmx, torch_mod, ctx, oracle_mod):
     assert kept >= wk[:, 2].sum() * 0.5
 
 
-def test_host_entry_matches_device(dmx, torch_mod, ctx):
+@pytest.mark.parametrize("mode", ["staged", "in_place", "auto"])
+def test_host_entry_matches_device(dmx, torch_mod, oracle_mod, mode):
+    """dm_sketch_host in each way of moving the data (staged chunked copies; kernels reading and
+    writing the page-locked host arrays in place; the automatic choice): keys and 1-bit words
+    equal the device entry's and the oracle's."""
     torch = torch_mod
+    ctx = dmx.dm_create(0)
+    dmx.dm_set_option(ctx, dmx.OPT_HOST_MODE, {"staged": dmx.HOST_STAGED, "in_place": dmx.HOST_IN_PLACE,
+                                               "auto": dmx.HOST_AUTO}[mode])
     b = workloads.random_sets(500, 1, 100, 1 << 20, seed=8)
     ref, _ = gpu_sketch(dmx, torch, ctx, b, 128, 4)
+    assert_same(ref, oracle_mod.sketch(b.indptr, b.indices, b.weights, 128, 4, threads=THREADS), "device entry")
     ip = torch.from_numpy(b.indptr.astype(np.int64)).pin_memory()
     ix = torch.from_numpy(b.indices.view(np.int32)).pin_memory()
     w = torch.from_numpy(b.weights).pin_memory()
     out = torch.empty((b.n_sets, 128), dtype=torch.int64).pin_memory()
     dmx.dm_sketch_host(ctx, ip, ix, w, 128, 4, out)
     assert_same(out.numpy().view(np.uint64), ref, "host entry")
-    # keys and 1-bit words together, batch split into several chunks
+    # keys and 1-bit words together, batch split into several chunks when staged
     big = workloads.random_sets(40_000, 1, 64, 1 << 20, seed=9)
     ref2, _ = gpu_sketch(dmx, torch, ctx, big, 64, 6)
     ipb = torch.from_numpy(big.indptr.astype(np.int64)).pin_memory()
     ixb = torch.from_numpy(big.indices.view(np.int32)).pin_memory()
     wb = torch.from_numpy(big.weights).pin_memory()
-    kh, wh = dmx.dm_sketch_host(ctx, ipb, ixb, wb, 64, 6, out_keys=torch.empty((big.n_sets, 64), dtype=torch.int64),
-                                b=1)
-    assert_same(kh.numpy().view(np.uint64), ref2, "host entry chunked keys")
+    kh, wh = dmx.dm_sketch_host(ctx, ipb, ixb, wb, 64, 6,
+                                out_keys=torch.empty((big.n_sets, 64), dtype=torch.int64).pin_memory(),
+                                out_words=torch.empty((big.n_sets, 1), dtype=torch.int64).pin_memory(), b=1)
+    assert_same(kh.numpy().view(np.uint64), ref2, "host entry keys")
     dev_words = dmx.dm_sketch_bbit(ctx, *to_dev(torch, big), 64, 1, 6)
     assert_same(wh.numpy().view(np.uint64), dev_words.cpu().numpy().view(np.uint64), "host entry words")
+    # an output in ordinary (not page-locked) memory: staged and automatic modes copy, in place refuses
+    plain = torch.empty((b.n_sets, 128), dtype=torch.int64)
+    if mode == "in_place":
+        with pytest.raises(dmx.DartMinHashError) as e:
+            dmx.dm_sketch_host(ctx, ip, ix, w, 128, 4, plain)
+        assert e.value.code == 1
+    else:
+        dmx.dm_sketch_host(ctx, ip, ix, w, 128, 4, plain)
+        assert_same(plain.numpy().view(np.uint64), ref, "host entry, pageable output")
+    ctx.close()
 
 
 @pytest.fixture(scope="module")
