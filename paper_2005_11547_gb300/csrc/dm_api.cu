@@ -69,6 +69,7 @@ struct dm_ctx {
     float large_work = 0.f;        // batched form: sets with this work estimate get a block
     int host_chunks = 8;           // host-buffer entry: chunks a batch is split into
     int host_mode = 2;             // host-buffer entry: 0 staged, 1 in place, 2 in place when possible
+    bool host_out = false;         // the current call writes host memory in place: no key-row layout
     // staging for the host-buffer entry points
     void *d_stage = nullptr;
     size_t d_stage_bytes = 0;
@@ -167,8 +168,8 @@ int cuda_fail(cudaError_t e) {
 
 // Warps per block: as many as fit 96 KB of shared memory (so two or more blocks are resident),
 // at most 8.
-int auto_warps(int kind, int k, int K) {
-    size_t a = dm::warp_bytes(kind, k, K, 0), b = dm::warp_bytes(kind, k, K, 1);
+int auto_warps(int kind, int k, int K, bool key_row = false) {
+    size_t a = dm::warp_bytes(kind, k, K, 0, key_row), b = dm::warp_bytes(kind, k, K, 1, key_row);
     size_t per = a > b ? a : b;
     int w = (int)((96 * 1024) / per);
     if (w > 8) w = 8;
@@ -198,14 +199,15 @@ int ensure_queue(dm_ctx *ctx, int64_t n_sets) {
     return DM_OK;
 }
 
-// Blocks of a kernel resident per SM, cached per context (the query sets a kernel attribute
-// and costs a few microseconds).  which: 0 fast, 1 general, 2 large.
-int occupancy(dm_ctx *ctx, int which, int kind, bool bbit, int wpb, size_t smem) {
+// Blocks of a kernel resident per SM, cached per context (the query costs a few microseconds).
+// which: 0 fast, 1 general, 2 large.
+int occupancy(dm_ctx *ctx, int which, int kind, bool bbit, int wpb, size_t smem, bool key_row) {
     const uint64_t key = ((uint64_t)which) | ((uint64_t)kind << 2) | ((uint64_t)bbit << 4) |
-                         ((uint64_t)wpb << 5) | ((uint64_t)smem << 12);
+                         ((uint64_t)key_row << 5) | ((uint64_t)wpb << 6) | ((uint64_t)smem << 12);
     for (auto &e : ctx->occupancy)
         if (e.first == key) return e.second;
-    int nb = which == 2 ? dm::large_blocks_per_sm(bbit, wpb, smem) : dm::blocks_per_sm(kind, which, bbit, wpb, smem);
+    int nb = which == 2 ? dm::large_blocks_per_sm(bbit, wpb, smem, key_row)
+                        : dm::blocks_per_sm(kind, which, bbit, wpb, smem, key_row);
     ctx->occupancy.emplace_back(key, nb);
     return nb;
 }
@@ -250,8 +252,11 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
     if (bbit && !out_words) return DM_EINVAL;
     if (n_sets == 0) return DM_OK;
     if (n_sets > 0x7FFFFFFF) return DM_EINVAL;
-    const int wpb = ch.wpb > 0 ? ch.wpb : auto_warps(kind, k, K);
-    const size_t smem_fast = dm::warp_bytes(kind, k, K, 0) * wpb, smem = dm::warp_bytes(kind, k, K, 1) * wpb;
+    // large sketches with keys: codes in shared memory, minima in the output row
+    const bool key_row = kind == dm::kSketch && out_keys && k >= dm::kKeyRowMinK && !ctx->host_out;
+    const int wpb = ch.wpb > 0 ? ch.wpb : auto_warps(kind, k, K, key_row);
+    const size_t smem_fast = dm::warp_bytes(kind, k, K, 0, key_row) * wpb,
+                 smem = dm::warp_bytes(kind, k, K, 1, key_row) * wpb;
     if (smem > 227 * 1024 || smem_fast > 227 * 1024) return DM_EINVAL;     // L and K too large for LSH
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -278,9 +283,10 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
     p.status = ctx->d_status;
     p.counters = ctx->counters;
     p.warps_per_block = wpb;
-    p.warp_bytes = (int32_t)dm::warp_bytes(kind, k, K, 1);
-    p.warp_bytes_fast = (int32_t)dm::warp_bytes(kind, k, K, 0);
-    p.sink_bytes = (int32_t)((dm::sink_bytes(kind, k, K) + 15) & ~(size_t)15);
+    p.warp_bytes = (int32_t)dm::warp_bytes(kind, k, K, 1, key_row);
+    p.warp_bytes_fast = (int32_t)dm::warp_bytes(kind, k, K, 0, key_row);
+    p.sink_bytes = (int32_t)((dm::sink_bytes(kind, k, K, key_row) + 15) & ~(size_t)15);
+    p.key_row = key_row;
     dm::carve_call_scratch(queue, n_sets, p);
     pl.kind = kind;
     pl.bbit = bbit;
@@ -294,8 +300,8 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
         return DM_OK;
     }
     // persistent grids: as many blocks as can be resident, never more than there are sets
-    const int64_t cap0 = (int64_t)ctx->sm_count * occupancy(ctx, 0, kind, bbit, wpb, smem_fast);
-    const int64_t cap1 = (int64_t)ctx->sm_count * occupancy(ctx, 1, kind, bbit, wpb, smem);
+    const int64_t cap0 = (int64_t)ctx->sm_count * occupancy(ctx, 0, kind, bbit, wpb, smem_fast, key_row);
+    const int64_t cap1 = (int64_t)ctx->sm_count * occupancy(ctx, 1, kind, bbit, wpb, smem, key_row);
     pl.grid_fast = (int)(blocks < cap0 ? blocks : cap0);
     pl.grid_general = (int)(blocks < cap1 ? blocks : cap1);
     if (ch.form == 2) return DM_OK;
@@ -304,8 +310,8 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
     p.large_nnz = kind != dm::kSketch ? 0 : ch.large_nnz;
     p.large_work = kind != dm::kSketch ? 0.f : ch.large_work;
     if (p.large_nnz > 0 || p.large_work > 0.f) {
-        const size_t lb = dm::large_block_bytes(k, p.large_warps);
-        if (lb <= 227 * 1024) pl.grid_large = ctx->sm_count * occupancy(ctx, 2, false, bbit, p.large_warps, lb);
+        const size_t lb = dm::large_block_bytes(k, p.large_warps, key_row);
+        if (lb <= 227 * 1024) pl.grid_large = ctx->sm_count * occupancy(ctx, 2, dm::kSketch, bbit, p.large_warps, lb, key_row);
         else p.large_nnz = 0;
     }
     return DM_OK;
@@ -627,8 +633,10 @@ int dm_sketch_host(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
         const bool ok = dip && dix && dw && (!out_keys || dk) && (b == 0 || dwd);
         if (ok) {
             Range range("dm_sketch_host");
+            ctx->host_out = true;                 // bucket minima stay in shared memory
             rc = run_sketch(ctx, (const int64_t *)dip, (const uint32_t *)dix, (const float *)dw, n_sets, k, b, seed,
                             (uint64_t *)dwd, (uint64_t *)dk, st);
+            ctx->host_out = false;
             if (rc) return rc;
             return cuda_fail(cudaStreamSynchronize(st));
         }
@@ -830,7 +838,8 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
     if (!found) ctx->tuned.push_back(TunedEntry{kind, k, K, b, best});
     if (result) {
         result->form = best.form;
-        result->warps_per_block = best.wpb > 0 ? best.wpb : auto_warps(kind, k, K);
+        result->warps_per_block =
+            best.wpb > 0 ? best.wpb : auto_warps(kind, k, K, kind == dm::kSketch && b == 0 && k >= dm::kKeyRowMinK);
         result->phi0_1024 = (int32_t)(best.phi0 * 1024.0f + 0.5f);
         result->large_nnz = best.large_nnz;
         result->large_work = (int32_t)best.large_work;

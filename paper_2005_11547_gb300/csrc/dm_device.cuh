@@ -182,6 +182,14 @@ __device__ __forceinline__ void shared_min_u64(uint32_t saddr, uint64_t v) {
     }
 }
 
+// Atomic minimum of a 32-bit word in shared memory (saddr: its shared-space address); returns the
+// previous value.
+__device__ __forceinline__ uint32_t shared_min_u32(uint32_t saddr, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.shared.min.u32 %0, [%1], %2;" : "=r"(old) : "r"(saddr), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ void set_status(int *status, int code) {
     if (status) atomicCAS(status, 0, code);
 }

@@ -49,15 +49,20 @@ struct SketchParams {
     int32_t large_nnz;          // sets with at least this many elements go to the block kernel
     float large_work;           // so do sets whose Lemma 2 work estimate reaches this (0: off)
     int32_t large_warps;        // warps per block of the large-set kernel
+    int32_t key_row;            // sketches: bucket minima in out_keys, shared memory holds codes only
 };
 
 // Shared memory per warp of the fast (mode 0) or general (mode 1) kernel, and of its sink
 // (k buckets of minima, or L buckets of bottom-K candidates for LSH).
-size_t warp_bytes(int kind, int k, int K, int mode);
-size_t sink_bytes(int kind, int k, int K);
+size_t warp_bytes(int kind, int k, int K, int mode, bool key_row = false);
+size_t sink_bytes(int kind, int k, int K, bool key_row = false);
+
+// Sketches with at least this many buckets keep only rank codes in shared memory and their 64-bit
+// minima in the output row (key-row layout), when the call writes keys.
+constexpr int kKeyRowMinK = 512;
 
 // Resident blocks per SM of a kernel.
-int blocks_per_sm(int kind, int mode, bool bbit, int warps_per_block, size_t smem);
+int blocks_per_sm(int kind, int mode, bool bbit, int warps_per_block, size_t smem, bool key_row = false);
 
 cudaError_t upload_poisson_table(const uint32_t *T);
 
@@ -89,8 +94,8 @@ cudaError_t launch_weight_classes(const int64_t *indptr, const float *weights, i
                                   int32_t *scale_out, int32_t norm_exp, int sm_count, cudaStream_t st);
 
 // Shared memory of the large-set kernel's blocks.
-size_t large_block_bytes(int k, int warps);
-int large_blocks_per_sm(bool bbit, int warps, size_t smem);
+size_t large_block_bytes(int k, int warps, bool key_row);
+int large_blocks_per_sm(bool bbit, int warps, size_t smem, bool key_row = false);
 
 // Scratch of one call: queue, order, classes and the small header (counters, histogram).
 size_t call_scratch_bytes(int64_t n_sets);

@@ -89,7 +89,8 @@ extern "C" int dm_sketch_noalloc(const int64_t *indptr, const uint32_t *indices,
     if (cap != cudaStreamCaptureStatusNone) return DM_EINVAL;     // the call synchronises its stream
 
     // warps per block: as many as fit 96 KB of shared memory, at most 8
-    const size_t wf = dm::warp_bytes(dm::kSketch, k, 0, 0), wg = dm::warp_bytes(dm::kSketch, k, 0, 1);
+    const bool key_row = k >= dm::kKeyRowMinK;    // out is always given
+    const size_t wf = dm::warp_bytes(dm::kSketch, k, 0, 0, key_row), wg = dm::warp_bytes(dm::kSketch, k, 0, 1, key_row);
     int wpb = (int)((96 * 1024) / (wf > wg ? wf : wg));
     wpb = wpb > 8 ? 8 : (wpb < 1 ? 1 : wpb);
 
@@ -106,15 +107,16 @@ extern "C" int dm_sketch_noalloc(const int64_t *indptr, const uint32_t *indices,
     p.warps_per_block = wpb;
     p.warp_bytes = (int32_t)wg;
     p.warp_bytes_fast = (int32_t)wf;
-    p.sink_bytes = (int32_t)dm::sink_bytes(dm::kSketch, k, 0);
+    p.sink_bytes = (int32_t)dm::sink_bytes(dm::kSketch, k, 0, key_row);
+    p.key_row = key_row;
     p.queue = (int32_t *)ds->scratch;
     p.queue_count = (unsigned int *)(ds->scratch + kQueueBytes);     // count, then the work counters
     p.work_next = p.queue_count + 1;
     p.status = (int *)(ds->scratch + kQueueBytes + 16);
 
     const int64_t blocks = (n_sets + wpb - 1) / wpb;
-    const int64_t cap0 = (int64_t)ds->sm_count * dm::blocks_per_sm(dm::kSketch, 0, false, wpb, wf * wpb);
-    const int64_t cap1 = (int64_t)ds->sm_count * dm::blocks_per_sm(dm::kSketch, 1, false, wpb, wg * wpb);
+    const int64_t cap0 = (int64_t)ds->sm_count * dm::blocks_per_sm(dm::kSketch, 0, false, wpb, wf * wpb, key_row);
+    const int64_t cap1 = (int64_t)ds->sm_count * dm::blocks_per_sm(dm::kSketch, 1, false, wpb, wg * wpb, key_row);
     // the status word keeps the previous call's value: clear it (launch_sets clears the counters)
     cudaError_t e = cudaMemsetAsync(p.status, 0, sizeof(int), st);
     if (e == cudaSuccess)

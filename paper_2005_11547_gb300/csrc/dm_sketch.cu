@@ -55,7 +55,6 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
 // ==========================================================================================
 // Sinks
 // ==========================================================================================
-__host__ __device__ size_t sketch_sink_bytes(int k) { return ((size_t)k * 8 + 15) & ~(size_t)15; }
 
 // LSH buckets hold K + kLshSlack candidates between compactions: a small slack keeps a warp's
 // shared memory small (more resident warps), and compacting a few entries is cheap.
@@ -71,40 +70,84 @@ size_t lsh_sink_bytes(int L, int K) {
     return (b + 15) & ~(size_t)15;
 }
 
-// k buckets, each the minimum key of the darts hashed to it (Theorem 1).
-struct SketchSink {
-    uint64_t *slots;
+// k buckets, each the minimum key of the darts hashed to it (Theorem 1).  Two layouts, with the
+// same bits:
+//  * shared: the k 64-bit minima live in shared memory (8 k bytes per warp);
+//  * key row (p.key_row, for large k): shared memory holds only each bucket's smallest rank code
+//    (4 k bytes) and the 64-bit minimum goes straight to the set's output row in global memory
+//    (L2-resident while the set runs).  A candidate whose code exceeds the bucket's code cannot
+//    be its minimum: a dart with a smaller code was put before it, and that dart's key reached
+//    the row.  Ties in the code reach the row, whose 64-bit minimum decides them.
+// 0xFFFFFFFF marks an empty bucket's code: a kept dart's code is below bits(theta) < 0x7F800000.
+__host__ __device__ size_t sketch_sink_bytes(int k, bool key_row) {
+    return ((size_t)k * (key_row ? 4 : 8) + 15) & ~(size_t)15;
+}
+
+template <bool KEYROW>
+struct SketchSinkT {
+    uint64_t *slots;                              // shared layout: the k minima
+    uint32_t *codes;                              // key-row layout: the k smallest codes
+    uint64_t *row;                                // key-row layout: the set's output row
     uint32_t k;
-    uint32_t sbase;                               // shared-space address of slots[0]
+    uint32_t sbase;                               // shared-space address of the bucket array
     static constexpr bool kLowerCut = false;      // min is idempotent: band overlap is harmless
 
     __device__ void bind(unsigned char *base, const SketchParams &p) {
         slots = reinterpret_cast<uint64_t *>(base);
+        codes = reinterpret_cast<uint32_t *>(base);
         k = (uint32_t)p.k;
         sbase = (uint32_t)__cvta_generic_to_shared(base);
+        row = nullptr;
+    }
+    __device__ void set_row(const SketchParams &p, int64_t set) {
+        if constexpr (KEYROW) row = p.out_keys + set * (int64_t)k;
     }
     __device__ void reset(int lane) {
-        for (uint32_t j = lane; j < k; j += 32) slots[j] = ~0ull;
+        if constexpr (KEYROW)
+            for (uint32_t j = lane; j < k; j += 32) {
+                codes[j] = 0xFFFFFFFFu;
+                row[j] = ~0ull;
+            }
+        else
+            for (uint32_t j = lane; j < k; j += 32) slots[j] = ~0ull;
         __syncwarp();
     }
     __device__ __forceinline__ bool put(uint64_t qh, uint32_t code) {
         const uint32_t slot = fastrange32((uint32_t)(qh >> 32), k);
-        shared_min_u64(sbase + 8u * slot, ((uint64_t)code << 32) | (uint32_t)qh);
+        const uint64_t key = ((uint64_t)code << 32) | (uint32_t)qh;
+        if constexpr (KEYROW) {
+            if (code <= codes[slot] && code <= shared_min_u32(sbase + 4u * slot, code))
+                atomicMin(reinterpret_cast<unsigned long long *>(&row[slot]), (unsigned long long)key);
+        } else {
+            shared_min_u64(sbase + 8u * slot, key);
+        }
         return false;
     }
     __device__ __forceinline__ void after_batch(int, bool) {}
+    __device__ bool empty_bucket(uint32_t j) const {
+        if constexpr (KEYROW) return codes[j] == 0xFFFFFFFFu;
+        return slots[j] == ~0ull;
+    }
     __device__ bool filled(int lane) {
         bool empty = false;
-        for (uint32_t j = lane; j < k; j += 32) empty |= (slots[j] == ~0ull);
+        for (uint32_t j = lane; j < k; j += 32) empty |= empty_bucket(j);
         return !__any_sync(kFull, empty);
     }
     __device__ void clear_to_error(int lane) {
-        for (uint32_t j = lane; j < k; j += 32) slots[j] = ~0ull;
+        for (uint32_t j = lane; j < k; j += 32) {
+            if constexpr (KEYROW) row[j] = ~0ull;
+            else slots[j] = ~0ull;
+        }
         __syncwarp();
+    }
+    // the final key of bucket j (the row is read from L2: the global minima were updated there)
+    __device__ __forceinline__ uint64_t key(uint32_t j) const {
+        if constexpr (KEYROW) return __ldcg(reinterpret_cast<const unsigned long long *>(&row[j]));
+        return slots[j];
     }
     template <bool BBIT>
     __device__ void finish(const SketchParams &p, int64_t set, bool err, int lane) {
-        if (p.out_keys)
+        if (!KEYROW && p.out_keys)
             for (uint32_t j = lane; j < k; j += 32) p.out_keys[set * (int64_t)k + j] = slots[j];
         if (!BBIT) return;
         const int b = p.b;
@@ -115,8 +158,8 @@ struct SketchSink {
         } else if (b == 1) {
             for (uint32_t j0 = 0; j0 < k; j0 += 64) {
                 uint32_t j1 = j0 + lane, j2 = j0 + 32 + lane;
-                bool b1 = j1 < k && (mix64(slots[j1] ^ kBbitSalt) & 1);
-                bool b2 = j2 < k && (mix64(slots[j2] ^ kBbitSalt) & 1);
+                bool b1 = j1 < k && (mix64(key(j1) ^ kBbitSalt) & 1);
+                bool b2 = j2 < k && (mix64(key(j2) ^ kBbitSalt) & 1);
                 unsigned lo = __ballot_sync(kFull, b1), hi = __ballot_sync(kFull, b2);
                 if (lane == 0) ow[j0 >> 6] = (uint64_t)lo | ((uint64_t)hi << 32);
             }
@@ -125,13 +168,15 @@ struct SketchSink {
             for (uint32_t j0 = 0; j0 < k; j0 += 32) {
                 uint32_t j = j0 + lane;
                 uint64_t v = 0;
-                if (j < k) v = (mix64(slots[j] ^ kBbitSalt) & bmask) << ((j * (uint32_t)b) & 63);
+                if (j < k) v = (mix64(key(j) ^ kBbitSalt) & bmask) << ((j * (uint32_t)b) & 63);
                 for (int o = 1; o < g; o <<= 1) v |= __shfl_xor_sync(kFull, v, o);
                 if ((lane & (g - 1)) == 0 && j < k) ow[(j * (uint32_t)b) >> 6] = v;
             }
         }
     }
 };
+using SketchSink = SketchSinkT<false>;   // bucket minima in shared memory
+using RowSink = SketchSinkT<true>;       // codes in shared memory, minima in the output row
 
 // L buckets, each the K smallest keys of the darts hashed to it ((L, K) LSH).  A bucket keeps
 // up to B = K + kLshSlack candidates and a threshold tau (its K-th smallest key after the last
@@ -159,6 +204,7 @@ struct LshSink {
         ovf_n = cnt + L;
         ovf_b = reinterpret_cast<uint16_t *>(ovf_n + 4);
     }
+    __device__ void set_row(const SketchParams &, int64_t) {}
     __device__ void reset(int lane) {
         for (uint32_t b = lane; b < L; b += 32) {
             cnt[b] = 0;
@@ -265,6 +311,7 @@ struct BottomKSink {
         tau = buf + C;
         cnt = reinterpret_cast<uint32_t *>(tau + 1);
     }
+    __device__ void set_row(const SketchParams &, int64_t) {}
     __device__ void reset(int lane) {
         if (lane == 0) {
             *cnt = 0;
@@ -938,6 +985,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) set_kernel(const Sketc
 #pragma unroll
         for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(kFull, l1, o);
         int err = __any_sync(kFull, bad) ? DM_EINVAL : 0;
+        sink.set_row(p, set);
         sink.reset(lane);
         unsigned long long cnt[3] = {0, 0, 0};
         unsigned long long passes = 0;
@@ -1126,22 +1174,22 @@ __global__ void __launch_bounds__(256) scatter_kernel(const SketchParams p) {
 // areas split among all the warps.  Passes are separated by block barriers.  A pass runs the
 // fast walk when the limit is below 1 and every tile allows it, else the general walk over all
 // tiles (a dart seen twice does not change a minimum).
-size_t large_block_bytes(int k, int warps) {
+size_t large_block_bytes(int k, int warps, bool key_row) {
     const size_t per = kFastPathBytes > kGenPathBytes ? kFastPathBytes : kGenPathBytes;
-    return sketch_sink_bytes(k) + (size_t)warps * per + 64;
+    return sketch_sink_bytes(k, key_row) + (size_t)warps * per + 64;
 }
 
-template <bool BBIT, bool COUNT>
+template <class Sink, bool BBIT, bool COUNT>
 __global__ void __launch_bounds__(256, 2) large_kernel(const SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const size_t per = kFastPathBytes > kGenPathBytes ? kFastPathBytes : kGenPathBytes;
-    SketchSink sink;
+    Sink sink;
     sink.bind(smem, p);
-    unsigned char *wbase = smem + sketch_sink_bytes(p.k) + (size_t)wid * per;
+    unsigned char *wbase = smem + sketch_sink_bytes(p.k, p.key_row != 0) + (size_t)wid * per;
     const FastMem fm = carve_fast(wbase);
     const GenMem gm = carve_gen(wbase);
-    int *flags = reinterpret_cast<int *>(smem + sketch_sink_bytes(p.k) + (size_t)nwarps * per);
+    int *flags = reinterpret_cast<int *>(smem + sketch_sink_bytes(p.k, p.key_row != 0) + (size_t)nwarps * per);
     float *wsum = reinterpret_cast<float *>(flags + 4);
     const int64_t n_work = p.hist[kTotals + 2], base = p.hist[kTotals];
     for (;;) {
@@ -1162,6 +1210,7 @@ __global__ void __launch_bounds__(256, 2) large_kernel(const SketchParams p) {
 #pragma unroll
         for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(kFull, l1, o);
         if (lane == 0) wsum[wid] = l1;
+        sink.set_row(p, set);
         if (wid == 0) sink.reset(lane);
         int err = __syncthreads_or(bad) ? DM_EINVAL : 0;
         l1 = 0.f;
@@ -1184,16 +1233,16 @@ __global__ void __launch_bounds__(256, 2) large_kernel(const SketchParams p) {
                 pc.cthr = th;
                 int e = kDefer;
                 if (pc.rho_top == 0)
-                    e = split ? fast_pass<SketchSink, COUNT>(p, beg, 32, end, pc, fm, sink, lane, cnt, sc, wid, nwarps)
-                              : fast_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, fm, sink, lane, cnt, sc);
+                    e = split ? fast_pass<Sink, COUNT>(p, beg, 32, end, pc, fm, sink, lane, cnt, sc, wid, nwarps)
+                              : fast_pass<Sink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, fm, sink, lane, cnt, sc);
                 const int any_defer = __syncthreads_or(e == kDefer);
                 if (any_defer)
-                    e = split ? gen_pass<SketchSink, COUNT>(p, beg, 32, end, pc, gm, sink, lane, cnt, sc, wid, nwarps)
-                              : gen_pass<SketchSink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, gm, sink, lane, cnt, sc);
+                    e = split ? gen_pass<Sink, COUNT>(p, beg, 32, end, pc, gm, sink, lane, cnt, sc, wid, nwarps)
+                              : gen_pass<Sink, COUNT>(p, beg + 32 * wid, 32 * nwarps, end, pc, gm, sink, lane, cnt, sc);
                 ++passes;
                 if (__syncthreads_or(e == DM_ERANGE)) { err = DM_ERANGE; break; }
                 int empty = 0;
-                for (uint32_t j = threadIdx.x; j < (uint32_t)p.k; j += blockDim.x) empty |= (sink.slots[j] == ~0ull);
+                for (uint32_t j = threadIdx.x; j < (uint32_t)p.k; j += blockDim.x) empty |= sink.empty_bucket(j);
                 if (!__syncthreads_or(empty)) break;
                 pc.rho_lo = rc.g_one ? rc.rho_top + 1 : rc.rho_top;
                 pc.gfl_lo = rc.g_one ? 0 : rc.gfl;
@@ -1225,13 +1274,17 @@ __global__ void __launch_bounds__(256, 2) large_kernel(const SketchParams p) {
 
 template <bool BBIT, bool COUNT>
 static cudaError_t launch_large(const SketchParams &p, int grid, cudaStream_t st) {
-    const size_t smem = large_block_bytes(p.k, p.large_warps);
-    large_kernel<BBIT, COUNT><<<grid, 32 * p.large_warps, smem, st>>>(p);
+    const size_t smem = large_block_bytes(p.k, p.large_warps, p.key_row != 0);
+    if (p.key_row) large_kernel<RowSink, BBIT, COUNT><<<grid, 32 * p.large_warps, smem, st>>>(p);
+    else large_kernel<SketchSink, BBIT, COUNT><<<grid, 32 * p.large_warps, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-int large_blocks_per_sm(bool bbit, int warps, size_t smem) {
-    const void *fn = bbit ? (const void *)large_kernel<true, false> : (const void *)large_kernel<false, false>;
+int large_blocks_per_sm(bool bbit, int warps, size_t smem, bool key_row) {
+    const void *fn = key_row ? (bbit ? (const void *)large_kernel<RowSink, true, false>
+                                     : (const void *)large_kernel<RowSink, false, false>)
+                             : (bbit ? (const void *)large_kernel<SketchSink, true, false>
+                                     : (const void *)large_kernel<SketchSink, false, false>);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * warps, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
@@ -1296,6 +1349,10 @@ cudaError_t launch_sets(const SketchParams &p, int kind, bool bbit, bool count, 
         if ((e = launch_mode<BottomKSink, 0>(p, false, count, grid_fast, st)) != cudaSuccess) return e;
         return launch_mode<BottomKSink, 1>(p, false, count, grid_general, st);
     }
+    if (p.key_row) {
+        if ((e = launch_mode<RowSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
+        return launch_mode<RowSink, 1>(p, bbit, count, grid_general, st);
+    }
     if ((e = launch_mode<SketchSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
     return launch_mode<SketchSink, 1>(p, bbit, count, grid_general, st);
 }
@@ -1342,8 +1399,13 @@ cudaError_t launch_batched(const SketchParams &p0, int kind, bool bbit, bool cou
         if ((e = launch_mode<BottomKSink, 0>(p, false, count, grid_fast, st)) != cudaSuccess) return e;
         return launch_mode<BottomKSink, 1>(p, false, count, grid_general, st);
     }
-    if ((e = launch_mode<SketchSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
-    if ((e = launch_mode<SketchSink, 1>(p, bbit, count, grid_general, st)) != cudaSuccess) return e;
+    if (p.key_row) {
+        if ((e = launch_mode<RowSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
+        if ((e = launch_mode<RowSink, 1>(p, bbit, count, grid_general, st)) != cudaSuccess) return e;
+    } else {
+        if ((e = launch_mode<SketchSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
+        if ((e = launch_mode<SketchSink, 1>(p, bbit, count, grid_general, st)) != cudaSuccess) return e;
+    }
     if (large && side) {
         if ((e = cudaEventRecord(side->join, side->st)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess)
@@ -1352,12 +1414,13 @@ cudaError_t launch_batched(const SketchParams &p0, int kind, bool bbit, bool cou
     return cudaSuccess;
 }
 
-size_t sink_bytes(int kind, int k, int K) {
-    return kind == kLsh ? lsh_sink_bytes(k, K) : (kind == kBottomK ? bottomk_sink_bytes(k) : sketch_sink_bytes(k));
+size_t sink_bytes(int kind, int k, int K, bool key_row) {
+    return kind == kLsh ? lsh_sink_bytes(k, K)
+                        : (kind == kBottomK ? bottomk_sink_bytes(k) : sketch_sink_bytes(k, key_row));
 }
 
-size_t warp_bytes(int kind, int k, int K, int mode) {
-    const size_t sink = (sink_bytes(kind, k, K) + 15) & ~(size_t)15;
+size_t warp_bytes(int kind, int k, int K, int mode, bool key_row) {
+    const size_t sink = (sink_bytes(kind, k, K, key_row) + 15) & ~(size_t)15;
     return sink + (mode == 0 ? kFastPathBytes : kGenPathBytes);
 }
 
@@ -1393,22 +1456,32 @@ cudaError_t allow_max_shared_memory(int device) {
     int bytes = 0;
     cudaError_t e = cudaDeviceGetAttribute(&bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e == cudaSuccess) e = allow_smem_all<SketchSink>(bytes);
+    if (e == cudaSuccess) e = allow_smem_all<RowSink>(bytes);
     if (e == cudaSuccess) e = allow_smem_all<LshSink>(bytes);
     if (e == cudaSuccess) e = allow_smem_all<BottomKSink>(bytes);
-    const void *large[4] = {(const void *)large_kernel<false, false>, (const void *)large_kernel<false, true>,
-                            (const void *)large_kernel<true, false>, (const void *)large_kernel<true, true>};
-    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+    const void *large[8] = {(const void *)large_kernel<SketchSink, false, false>,
+                            (const void *)large_kernel<SketchSink, false, true>,
+                            (const void *)large_kernel<SketchSink, true, false>,
+                            (const void *)large_kernel<SketchSink, true, true>,
+                            (const void *)large_kernel<RowSink, false, false>,
+                            (const void *)large_kernel<RowSink, false, true>,
+                            (const void *)large_kernel<RowSink, true, false>,
+                            (const void *)large_kernel<RowSink, true, true>};
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i)
         e = cudaFuncSetAttribute(large[i], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) done[device] = true;
     return e;
 }
 
-int blocks_per_sm(int kind, int mode, bool bbit, int warps_per_block, size_t smem) {
+int blocks_per_sm(int kind, int mode, bool bbit, int warps_per_block, size_t smem, bool key_row) {
     const void *fn;
     if (kind == kLsh) fn = mode == 0 ? kernel_fn<LshSink, false, false, 0>() : kernel_fn<LshSink, false, false, 1>();
     else if (kind == kBottomK)
         fn = mode == 0 ? kernel_fn<BottomKSink, false, false, 0>() : kernel_fn<BottomKSink, false, false, 1>();
-    else if (mode == 0) fn = bbit ? kernel_fn<SketchSink, true, false, 0>() : kernel_fn<SketchSink, false, false, 0>();
+    else if (key_row) {
+        if (mode == 0) fn = bbit ? kernel_fn<RowSink, true, false, 0>() : kernel_fn<RowSink, false, false, 0>();
+        else fn = bbit ? kernel_fn<RowSink, true, false, 1>() : kernel_fn<RowSink, false, false, 1>();
+    } else if (mode == 0) fn = bbit ? kernel_fn<SketchSink, true, false, 0>() : kernel_fn<SketchSink, false, false, 0>();
     else fn = bbit ? kernel_fn<SketchSink, true, false, 1>() : kernel_fn<SketchSink, false, false, 1>();
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * warps_per_block, smem) != cudaSuccess) return 1;
