@@ -388,24 +388,24 @@ struct BottomKSink {
 // for the sinks that must not see a dart twice.
 // ==========================================================================================
 constexpr int kSegTiles = 2, kSeg = 32 * kSegTiles;
-static_assert((kSeg & (kSeg - 1)) == 0, "WalkF::locate's binary search needs a power-of-two segment");
 constexpr int kFastRegions = 32;      // weight regions nu = 0..31 of the fast path
+static_assert(kFastRegions == 32, "one region per lane; WalkF::locate searches 32 regions");
 constexpr int kQ = 64;                // capacity of each step queue (served at 32)
 
 // Per-pass record of weight region nu: the area counter offset kt, the u limit of its last row
-// and the u floor of its first row (RegA); its first row and its row end (RegB).
+// and the u floor of its first row (RegA); its first row and row end, and per segment the number
+// of its elements and the offset of its first area in the segment (RegB).
 struct RegA {
     uint64_t kt;
     uint32_t lastthr, firstlo;
 };
 struct RegB {
-    uint32_t rlo, rhi;
+    uint32_t rlo, rhi, cnt, C;
 };
-// Per-element record of a segment (16 bytes, one load): element key, offset of its first area in
-// the segment, and vtop | nu_top << 24 (nu_top = -1: no areas).
+// Per-element record of a segment (16 bytes, one load): element key and vtop | nu_top << 24.
 struct ElRec {
     uint64_t e;
-    uint32_t off, vn;
+    uint32_t pad, vn;
 };
 
 struct FastMem {
@@ -420,7 +420,7 @@ struct FastMem {
 
 constexpr size_t kFastPathBytes = (size_t)kFastRegions * (sizeof(RegA) + sizeof(RegB)) +
                                   (size_t)kSeg * sizeof(ElRec) + (size_t)kQ * (16 + 16 + 8 + 4);
-static_assert(sizeof(RegA) == 16 && sizeof(RegB) == 8 && sizeof(ElRec) == 16, "record layout");
+static_assert(sizeof(RegA) == 16 && sizeof(RegB) == 16 && sizeof(ElRec) == 16, "record layout");
 static_assert(kFastPathBytes % 16 == 0, "fast-path tables keep 16-byte alignment");
 
 __device__ __forceinline__ FastMem carve_fast(unsigned char *base) {
@@ -446,58 +446,56 @@ __device__ __forceinline__ uint64_t ceil_scaled(uint32_t bits, int S) {
     return (m + (1ull << -sh) - 1) >> -sh;
 }
 
+// The walk over a segment's areas in region-major order: weight region nu, then the region's
+// elements (sorted by nu_top, descending, so region nu's elements are the first cnt(nu)), then
+// rows.  Every element of a region has the same rows, so a one-row region costs one element
+// step per area, and a lane's share rarely crosses a region.
 struct WalkF {
-    int el, nu, nutop;
-    uint32_t r, rlo, rhi, vtop, vmax, lastthr, firstlo;
-    uint64_t e, ctr;
+    int nu, q, qend;
+    uint32_t r, rlo, rhi, vmax, lastthr, firstlo;
+    uint64_t kt, ctr;
 
     __device__ __forceinline__ void region(const FastMem &m) {
         const uint4 a = *reinterpret_cast<const uint4 *>(&m.ra[nu]);          // kt, lastthr, firstlo
-        const uint2 b = *reinterpret_cast<const uint2 *>(&m.rb[nu]);          // rlo, rhi
-        r = rlo = b.x;
-        rhi = b.y;
-        ctr = e + (((uint64_t)a.y << 32) | a.x);
+        const uint4 b = *reinterpret_cast<const uint4 *>(&m.rb[nu]);          // rlo, rhi, cnt, C
+        kt = ((uint64_t)a.y << 32) | a.x;
         lastthr = a.z;
         firstlo = a.w;
-        vmax = nu == nutop ? vtop : kUMask;
+        rlo = b.x;
+        rhi = b.y;
+        qend = (int)b.z;
     }
-    __device__ __forceinline__ void load(const FastMem &m) {
-        const uint4 q = *reinterpret_cast<const uint4 *>(&m.el[el]);
-        e = ((uint64_t)q.y << 32) | q.x;
-        vtop = q.w & kUMask;
-        nutop = (int)(signed char)(q.w >> 24);
+    // element q of region nu at row r: counter e + kt + gamma (r - rlo); the v limit of the
+    // element's last region
+    __device__ __forceinline__ void element(const FastMem &m) {
+        const uint4 e = *reinterpret_cast<const uint4 *>(&m.el[q]);
+        ctr = (((uint64_t)e.y << 32) | e.x) + kt + kGolden * (uint64_t)(r - rlo);
+        vmax = (int)(signed char)(e.w >> 24) == nu ? (e.w & kUMask) : kUMask;
     }
     // position the walk on area idx of the segment (idx < its total)
-    __device__ void locate(uint32_t idx, int n_el, const FastMem &m) {
-        el = 0;                                   // last element whose offset is <= idx
-        for (int step = kSeg / 2; step; step >>= 1) {
-            const int c = el + step;
-            if (c < n_el && m.el[c].off <= idx) el = c;
-        }
-        load(m);
-        uint32_t li = idx - m.el[el].off;
-        for (nu = 0;; ++nu) {
-            const uint32_t rows = m.rb[nu].rhi - m.rb[nu].rlo;
-            if (li < rows) break;
-            li -= rows;
-        }
+    __device__ void locate(uint32_t idx, const FastMem &m) {
+        nu = 0;                                   // last region whose first area is <= idx
+        for (int step = kFastRegions / 2; step; step >>= 1)
+            if (m.rb[nu + step].C <= idx) nu += step;
         region(m);
-        r += li;
-        ctr += kGolden * (uint64_t)li;
+        const uint32_t off = idx - m.rb[nu].C, rows = rhi - rlo;
+        q = (int)(off / rows);
+        r = rlo + (off - (uint32_t)q * rows);
+        element(m);
     }
     // Next area.  Every region of a pass has at least one row (rlo = floor(g_prev 2^nu) <
-    // ceil(g 2^nu) = rhi because g_prev < g), so one region step suffices.
-    __device__ __forceinline__ void advance(int n_el, const FastMem &m) {
+    // ceil(g 2^nu) = rhi because g_prev < g).
+    __device__ __forceinline__ void advance(const FastMem &m) {
         ++r;
         ctr += kGolden;
         if (r == rhi) {
-            if (++nu > nutop) {
-                nu = 0;
-                do { ++el; } while (el < n_el && (signed char)(m.el[el].vn >> 24) < 0);
-                if (el >= n_el) return;
-                load(m);
+            if (++q == qend) {
+                ++nu;
+                q = 0;
+                region(m);
             }
-            region(m);
+            r = rlo;
+            element(m);
         }
     }
 };
@@ -511,6 +509,7 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
                          int part = 0, int nparts = 1) {
     constexpr bool LOWER = Sink::kLowerCut;
     __syncwarp();
+    uint32_t myrows;                             // rows of region nu = lane in this pass
     {   // per-pass region table, one region per lane
         const int nu = lane;
         const uint32_t lo = nu ? (uint32_t)(pc.gfl_lo >> (64 - nu)) : 0u;
@@ -521,8 +520,8 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         m.ra[nu].firstlo = (uint32_t)(plo - ((uint64_t)lo << 24));
         m.rb[nu].rlo = lo;
         m.rb[nu].rhi = hi;
+        myrows = hi - lo;
     }
-    const uint32_t g_hi = (uint32_t)(pc.gm1 >> 32), glo_hi = (uint32_t)(pc.gfl_lo >> 32);
     const unsigned lt = (1u << lane) - 1u;
     uint32_t kh = 0, kt = 0, xh = 0, xt = 0;     // kept and dart queues: heads and tails
 
@@ -587,38 +586,64 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
     };
 
     for (int64_t tile = first; tile < end;) {
-        // segment tables: geometry, element hash and area offsets of up to kSegTiles tiles
+        // segment: geometry and key of up to kSegTiles tiles; elements sorted by nu_top (descending)
         __syncwarp();
-        uint64_t base = 0;
-        int nt = 0;
-        for (; nt < kSegTiles && tile < end; ++nt, tile += stride) {
-            const int64_t pos = tile + lane;
-            int nutop = -1;
-            uint64_t F = 0, e = 0;
-            if (pos < end) {
-                nutop = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F, escale);
-                if (nutop >= 0) e = mix64(p.sigma + kGolden * ((uint64_t)p.indices[pos] + 1));
-            }
-            if (__any_sync(kFull, nutop == -2)) return DM_ERANGE;
-            if (!__all_sync(kFull, nutop <= 31)) return kDefer;
-            uint64_t n_el = 0;
-            if (nutop >= 0) {
-                n_el = 1 + (uint64_t)nutop;
-                if (nutop > 0) {
-                    const uint32_t H = g_hi >> (32 - nutop), Hl = glo_hi >> (32 - nutop);
-                    n_el += (2 * (uint64_t)H - __popc(H)) - (2 * (uint64_t)Hl - __popc(Hl));
+        int nut[kSegTiles];
+        uint64_t et[kSegTiles];
+        uint32_t vt[kSegTiles], rank[kSegTiles];
+#pragma unroll
+        for (int t = 0; t < kSegTiles; ++t) {
+            nut[t] = -1;
+            et[t] = 0;
+            vt[t] = 0;
+            rank[t] = 0;
+            if (tile < end) {
+                const int64_t pos = tile + lane;
+                uint64_t F = 0;
+                if (pos < end) {
+                    nut[t] = weight_geometry(__float_as_uint(p.weights[pos]), p.t, F, escale);
+                    if (nut[t] >= 0) et[t] = mix64(p.sigma + kGolden * ((uint64_t)p.indices[pos] + 1));
                 }
+                if (__any_sync(kFull, nut[t] == -2)) return DM_ERANGE;
+                if (!__all_sync(kFull, nut[t] <= 31)) return kDefer;
+                vt[t] = (uint32_t)(F >> 40);
+                tile += stride;
             }
-            const uint64_t incl = warp_incl_scan(n_el, lane);
-            const uint32_t off = (uint32_t)min(base + incl - n_el, (uint64_t)0xFFFFFFFFu);
-            const uint32_t vn = (uint32_t)(F >> 40) | ((uint32_t)(uint8_t)(signed char)(n_el ? nutop : -1) << 24);
-            *reinterpret_cast<uint4 *>(&m.el[nt * 32 + lane]) = make_uint4((uint32_t)e, (uint32_t)(e >> 32), off, vn);
-            base += __shfl_sync(kFull, incl, 31);
         }
+        int nhi = -1, nlo = 32;
+#pragma unroll
+        for (int t = 0; t < kSegTiles; ++t) {
+            nhi = max(nhi, nut[t]);
+            if (nut[t] >= 0) nlo = min(nlo, nut[t]);
+        }
+        nhi = __reduce_max_sync(kFull, nhi);
+        nlo = __reduce_min_sync(kFull, nlo);
+        if (nhi < 0) continue;
+        // ranks in descending nu_top order; lane v keeps cnt(v), the elements with nu_top >= v
+        uint32_t placed = 0, mycnt = 0;
+        for (int v = nhi; v >= nlo; --v) {
+#pragma unroll
+            for (int t = 0; t < kSegTiles; ++t) {
+                const unsigned mv = __ballot_sync(kFull, nut[t] == v);
+                if (nut[t] == v) rank[t] = placed + __popc(mv & lt);
+                placed += __popc(mv);
+            }
+            if (lane == v) mycnt = placed;
+        }
+        if (lane < nlo) mycnt = placed;
+#pragma unroll
+        for (int t = 0; t < kSegTiles; ++t)
+            if (nut[t] >= 0)
+                *reinterpret_cast<uint4 *>(&m.el[rank[t]]) =
+                    make_uint4((uint32_t)et[t], (uint32_t)(et[t] >> 32), 0u, vt[t] | ((uint32_t)nut[t] << 24));
+        // region nu = lane holds cnt(nu) rows(nu) areas; C(nu) is their offset in the segment
+        const uint64_t A = (uint64_t)mycnt * myrows;
+        const uint64_t incl = warp_incl_scan(A, lane);
+        const uint64_t base = __shfl_sync(kFull, incl, 31);
         if (base >= (1ull << 31)) return kDefer;
+        m.rb[lane].cnt = mycnt;
+        m.rb[lane].C = (uint32_t)(incl - A);
         __syncwarp();
-        if (base == 0) continue;
-        const int n_el = nt * 32;
         const uint32_t total = (uint32_t)base, lanes = 32u * (uint32_t)nparts;
         const uint32_t share = (total + lanes - 1) / lanes;
         const uint32_t lo = share * (32u * (uint32_t)part + (uint32_t)lane);
@@ -627,7 +652,7 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         const uint32_t lo0 = share * 32u * (uint32_t)part;
         const uint32_t steps = lo0 < total ? min(share, total - lo0) : 0u;
         WalkF s{};
-        if (left) s.locate(lo, n_el, m);
+        if (left) s.locate(lo, m);
         for (uint32_t st = 0; st < steps; ++st) {
             if (max(kt - kh, xt - xh) >= 32u) {
                 for (;;) {                        // serve full queues (each below 32 afterwards)
@@ -651,7 +676,7 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
             if (COUNT) { cnt[0] += act; cnt[1] += act ? (uint32_t)poisson1(ua, c_pois) : 0u; }
             push_kept(keep, d, s.r, (uint32_t)s.nu);
             push_darts(x2, a + 2 * kGolden, uthr | (1u << 26), s.vmax | ((uint32_t)s.nu << 24), s.r, ua, ulo);
-            if (act && --left) s.advance(n_el, m);
+            if (act && --left) s.advance(m);
         }
     }
     for (;;) {                                    // drain both queues
