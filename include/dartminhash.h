@@ -90,7 +90,8 @@ int dm_sketch_bbit(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, 
  * keys in increasing order, from h = 0x082EFA98EC4E6C89.  Two sets collide in a table with
  * probability J^K, independently across tables.  out: uint32[n_sets * L] (row-major); a set
  * with no positive weight gets 0xFFFFFFFF.  1 <= L <= 1024, 1 <= K <= 32, and a set's bucket
- * state (about 8 L (K + 3.5) + 650 bytes) must fit in shared memory, else DM_EINVAL. */
+ * state (8 L K + 4 L bytes, plus about 4.9 KB of walk tables and queues per warp) must fit in
+ * shared memory, else DM_EINVAL. */
 int dm_lsh(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *weights,
            int64_t n_sets, int32_t L, int32_t K, uint64_t seed, uint32_t *out, void *stream);
 

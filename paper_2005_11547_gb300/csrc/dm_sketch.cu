@@ -37,7 +37,6 @@ __constant__ uint32_t c_pois[12];
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kMaxPasses = 21;     // phi0 * 2^20 at most (Theorem 1's loop limit)
 constexpr int kDefer = -1;         // a pass the fast kernel leaves to the general kernel
-constexpr int kOverflow = 64;      // LSH: appends past a full bucket within one batch
 // batched form: hist[0..96) bin counts, [96..192) bin cursors, [192..195) class totals
 constexpr int kClasses = 3, kBins = 32, kCursors = kClasses * kBins, kTotals = 2 * kClasses * kBins;
 constexpr size_t kHeaderBytes = 1024;   // queue count, 3 work counters, histogram, totals
@@ -56,19 +55,8 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
 // Sinks
 // ==========================================================================================
 
-// LSH buckets hold K + kLshSlack candidates between compactions: a small slack keeps a warp's
-// shared memory small (more resident warps), and compacting a few entries is cheap.
-constexpr uint32_t kLshSlack = 1;
-
-size_t lsh_sink_bytes(int L, int K) {
-    size_t B = (size_t)K + kLshSlack;
-    size_t b = (size_t)L * 8 * (B + 2)           // candidate buffers (stride B + 1) and thresholds
-             + (size_t)kOverflow * 8               // overflow keys
-             + (size_t)L * 4                       // counts
-             + 16                                  // overflow count
-             + (size_t)kOverflow * 2;              // overflow buckets
-    return (b + 15) & ~(size_t)15;
-}
+// LSH: L buckets of K sorted keys, then the L counts.
+size_t lsh_sink_bytes(int L, int K) { return ((size_t)L * K * 8 + (size_t)L * 4 + 15) & ~(size_t)15; }
 
 // k buckets, each the minimum key of the darts hashed to it (Theorem 1).  Two layouts, with the
 // same bits:
@@ -123,7 +111,10 @@ struct SketchSinkT {
         }
         return false;
     }
-    __device__ __forceinline__ void after_batch(int, bool) {}
+    // called by the whole warp; lanes with have = true hold a kept dart
+    __device__ __forceinline__ void put_batch(bool have, uint64_t qh, uint32_t code, int) {
+        if (have) put(qh, code);
+    }
     __device__ bool empty_bucket(uint32_t j) const {
         if constexpr (KEYROW) return codes[j] == 0xFFFFFFFFu;
         return slots[j] == ~0ull;
@@ -178,90 +169,59 @@ struct SketchSinkT {
 using SketchSink = SketchSinkT<false>;   // bucket minima in shared memory
 using RowSink = SketchSinkT<true>;       // codes in shared memory, minima in the output row
 
-// L buckets, each the K smallest keys of the darts hashed to it ((L, K) LSH).  A bucket keeps
-// up to B = K + kLshSlack candidates and a threshold tau (its K-th smallest key after the last
-// compaction; keys >= tau can never enter the bottom K).  Appends past B go to an overflow
-// list; after each batch, buckets that filled up are compacted to their K smallest keys.
-// Band passes must not add a dart twice, so darts below the previous limit are cut.  Bucket
-// arrays are B + 1 entries apart, so that lanes compacting neighbouring buckets at once hit
-// different shared-memory banks.
+// L buckets, each the K smallest keys of the darts hashed to it ((L, K) LSH), kept sorted in
+// shared memory.  A batch of kept darts is inserted by the whole warp: darts of different buckets
+// go in at once, and darts of one bucket (grouped by __match_any_sync) take turns, so no bucket is
+// written by two lanes at a time.  A key at or above a full bucket's K-th key is dropped.  Band
+// passes must not add a dart twice, so darts below the previous limit are cut before they reach
+// the sink.  Table l's value is a hash of bucket l's K keys in increasing order.
 struct LshSink {
-    uint64_t *buf, *tau, *ovf_k;
-    uint32_t *cnt, *ovf_n;
-    uint16_t *ovf_b;
-    uint32_t L, K, B, S;                          // S = B + 1: stride between bucket arrays
+    uint64_t *buf;                                // [L][K], ascending
+    uint32_t *cnt;                                // [L]
+    uint32_t L, K;
     static constexpr bool kLowerCut = true;
 
     __device__ void bind(unsigned char *base, const SketchParams &p) {
         L = (uint32_t)p.k;
         K = (uint32_t)p.K;
-        B = K + kLshSlack;
-        S = B + 1;
         buf = reinterpret_cast<uint64_t *>(base);
-        tau = buf + (size_t)L * S;
-        ovf_k = tau + L;
-        cnt = reinterpret_cast<uint32_t *>(ovf_k + kOverflow);
-        ovf_n = cnt + L;
-        ovf_b = reinterpret_cast<uint16_t *>(ovf_n + 4);
+        cnt = reinterpret_cast<uint32_t *>(buf + (size_t)L * K);
     }
     __device__ void set_row(const SketchParams &, int64_t) {}
     __device__ void reset(int lane) {
-        for (uint32_t b = lane; b < L; b += 32) {
-            cnt[b] = 0;
-            tau[b] = ~0ull;
-        }
-        if (lane == 0) *ovf_n = 0;
+        for (uint32_t b = lane; b < L; b += 32) cnt[b] = 0;
         __syncwarp();
     }
-    // Returns true when the bucket is now full (or overflowed): after_batch must compact.
-    __device__ __forceinline__ bool put(uint64_t qh, uint32_t code) {
+    // insertion of key into bucket b's sorted keys (the caller owns bucket b for this call)
+    __device__ __forceinline__ void insert(uint32_t b, uint64_t key) {
+        uint64_t *v = buf + (size_t)b * K;
+        uint32_t n = cnt[b];
+        if (n == K) {
+            if (key >= v[K - 1]) return;
+            n = K - 1;                            // the largest key leaves
+        } else {
+            cnt[b] = n + 1;
+        }
+        uint32_t j = n;
+        while (j > 0 && v[j - 1] > key) {
+            v[j] = v[j - 1];
+            --j;
+        }
+        v[j] = key;
+    }
+    // Called by the whole warp; lanes with have = true hold a kept dart (bucket hash qh, code).
+    __device__ __forceinline__ void put_batch(bool have, uint64_t qh, uint32_t code, int lane) {
         const uint32_t b = fastrange32((uint32_t)(qh >> 32), L);
         const uint64_t key = ((uint64_t)code << 32) | (uint32_t)qh;
-        if (key >= tau[b]) return false;
-        const uint32_t pos = atomicAdd(&cnt[b], 1u);
-        if (pos < B) {
-            buf[(size_t)b * S + pos] = key;
-        } else {
-            const uint32_t o = atomicAdd(ovf_n, 1u);       // < kOverflow: a batch has <= 64 darts
-            ovf_k[o] = key;
-            ovf_b[o] = (uint16_t)b;
+        // a stale look at the K-th key only lets more darts through; insert decides exactly
+        const bool go = have && (cnt[b] < K || key < buf[(size_t)b * K + K - 1]);
+        const unsigned grp = __match_any_sync(kFull, go ? b : L + (uint32_t)lane);
+        const uint32_t rank = __popc(grp & ((1u << lane) - 1u));
+        const uint32_t rounds = __reduce_max_sync(kFull, go ? (uint32_t)__popc(grp) : 0u);
+        for (uint32_t it = 0; it < rounds; ++it) {
+            if (go && rank == it) insert(b, key);
+            __syncwarp();
         }
-        return pos + 1 >= B;
-    }
-    // Sort a bucket's candidates, merge its overflow entries and keep the K smallest.
-    __device__ void compact(uint32_t b, uint32_t no) {
-        uint64_t *v = buf + (size_t)b * S;
-        uint32_t n = min(cnt[b], B);
-        for (uint32_t i = 1; i < n; ++i) {               // insertion sort
-            uint64_t x = v[i];
-            uint32_t j = i;
-            while (j > 0 && v[j - 1] > x) { v[j] = v[j - 1]; --j; }
-            v[j] = x;
-        }
-        if (n > K) n = K;
-        for (uint32_t o = 0; o < no; ++o) {
-            if (ovf_b[o] != b) continue;
-            uint64_t x = ovf_k[o];
-            if (n == K && x >= v[K - 1]) continue;
-            uint32_t j = n < K ? n++ : K - 1;
-            while (j > 0 && v[j - 1] > x) { v[j] = v[j - 1]; --j; }
-            v[j] = x;
-        }
-        cnt[b] = n;
-        if (n == K) tau[b] = v[K - 1];
-    }
-    // Called by the whole warp after at most 64 puts; need: this lane's puts asked for it.
-    __device__ void after_batch(int lane, bool need) {
-        if (!__any_sync(kFull, need)) return;
-        const uint32_t no = *ovf_n;
-        for (uint32_t b = lane; b < L; b += 32) {
-            bool hit = cnt[b] >= B;
-            for (uint32_t o = 0; o < no && !hit; ++o) hit = ovf_b[o] == b;
-            if (hit) compact(b, no);
-        }
-        __syncwarp();
-        if (lane == 0) *ovf_n = 0;
-        __syncwarp();
     }
     __device__ bool filled(int lane) {
         bool lack = false;
@@ -277,8 +237,7 @@ struct LshSink {
                 o[b] = 0xFFFFFFFFu;
                 continue;
             }
-            compact(b, 0);                               // sorted, exactly K
-            const uint64_t *v = buf + (size_t)b * S;
+            const uint64_t *v = buf + (size_t)b * K;
             uint64_t h = kLshInit;
             for (uint32_t m = 0; m < K; ++m) h = mix64(h ^ v[m]);
             o[b] = (uint32_t)(h >> 32);
@@ -319,7 +278,7 @@ struct BottomKSink {
         }
         __syncwarp();
     }
-    // Returns true when the buffer is within 32 of full: after_batch must compact.
+    // Returns true when the buffer is within 32 of full: the batch ends with a compaction.
     __device__ __forceinline__ bool put(uint64_t qh, uint32_t code) {
         const uint64_t key = ((uint64_t)code << 32) | (uint32_t)qh;
         if (key >= *tau) return false;
@@ -339,7 +298,10 @@ struct BottomKSink {
         }
         __syncwarp();
     }
-    __device__ void after_batch(int lane, bool need) {
+    // called by the whole warp with at most 32 darts; lanes with have = true hold one
+    __device__ __forceinline__ void put_batch(bool have, uint64_t qh, uint32_t code, int lane) {
+        const bool need = have && put(qh, code);
+        __syncwarp();
         if (__any_sync(kFull, need)) compact(lane);
     }
     __device__ bool filled(int) { return *cnt >= k; }
@@ -554,10 +516,8 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         // round-toward-zero mode, then the exponent lowered by S
         const uint64_t P = ((uint64_t)q.z << 24) | (uint32_t)(d >> 40);
         const uint32_t code = P ? __float_as_uint(__ull2float_rz(P)) - ((q.w + 24u) << 23) : 0u;
-        bool need = false;
-        if (v) need = sink.put(h, code);
+        sink.put_batch(v, h, code, lane);
         __syncwarp();
-        sink.after_batch(lane, need);
     };
     // dart step over the n (<= 32) oldest queued areas
     auto dart_step = [&](uint32_t n) {
@@ -876,10 +836,8 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
         if (v) q = m.kq[(kh + (uint32_t)lane) & (kQ - 1)];
         kh += n;
         const uint64_t h = mix64((((uint64_t)q.y << 32) | q.x) ^ kSlotSalt);
-        bool need = false;
-        if (v) need = sink.put(h, q.z);
+        sink.put_batch(v, h, q.z, lane);
         __syncwarp();
-        sink.after_batch(lane, need);
     };
     // dart step over the n (<= 32) oldest queued areas: dart j of each; the area goes back to
     // the queue when dart j + 1 exists (its Poisson uniform reaches T[j + 1])
