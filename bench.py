@@ -406,6 +406,38 @@ def measure(args, wl, local, dist, props, full):
         plain = {"ms_per_step": p_max * 1e3, "value": all_sets / args.steps / p_max, "unit": "sets/s",
                  "batched_over_plain": value / (all_sets / args.steps / p_max)}
 
+    # the one-kernel-per-set form: every set of a sample is its own dm_sketch call (plain form,
+    # one set), so each set pays its own launches; timed on the device over the sample, and each
+    # set's keys checked against the batched call's
+    per_set = None
+    if wl == "W2" and plain is not None:
+        sctx = dmx.dm_create(local)
+        dmx.dm_set_option(sctx, dmx.OPT_FORM, dmx.FORM_PLAIN)
+        ns = min(n, 2000)
+        got = torch.empty((ns, kk), dtype=torch.int64, device="cuda")
+
+        def one(i):
+            dmx.dm_sketch(sctx, ip[i:i + 2], ix, w, kk, SEED, out=got[i], stream=stream)
+
+        for i in range(min(ns, 64)):
+            one(i)
+        se = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        barrier(dist, True)
+        se[0].record(stream)
+        for i in range(ns):
+            one(i)
+        se[1].record(stream)
+        barrier(dist, True)
+        dmx.dm_sync_status(sctx)
+        sctx.close()
+        if not torch.equal(got, keys[:ns]):
+            raise RuntimeError("per-set calls differ from the batched call's keys")
+        s_max = max_over_ranks(dist, se[0].elapsed_time(se[1]) / 1e3, True)
+        rate = world * ns / s_max
+        per_set = {"value": rate, "unit": "sets/s", "ms_per_step_extrapolated": n / (ns / s_max) * 1e3,
+                   "sample": f"first {ns} sets, one dm_sketch call (plain form, one set) each, device time",
+                   "batched_over_per_set": value / rate}
+
     # end to end through the host-buffer C-ABI entry (copies inside the timed region)
     e2e = None
     if full and not args.no_e2e and wl == "W1":
@@ -474,15 +506,17 @@ def measure(args, wl, local, dist, props, full):
                         "sample": f"first {ns} sets of W1 ({dt:.1f} s wall on {cores} threads)",
                         "single_thread": {"value": v1, "unit": "sets/s", "cores": 1,
                                           "sample": f"first {ns1} sets of W1 ({dt1:.1f} s wall on 1 thread)"}}
-    # kernels per step: fast + general; the batched form adds classify, scan, scatter and, for
-    # sketches with a large-set threshold, the block-per-set kernel; W3S adds the class kernel
+    # kernels per step: fast + general; the batched form adds classify, scan, scatter, a second
+    # general launch (the fast kernel's deferrals) and, for sketches with a large-set threshold,
+    # the block-per-set kernel; W3S adds the class kernel
     eff = tuning or {"form": form_id, "large_nnz": 2048 if args.large_nnz is None else args.large_nnz,
                      "large_work": 0}
     large_on = wl in ("W1", "W2") and (eff["large_nnz"] > 0 or eff["large_work"] > 0)
-    launches_per_step = (2 if eff["form"] != dmx.FORM_BATCHED else 5 + (1 if large_on else 0)) \
+    launches_per_step = (2 if eff["form"] != dmx.FORM_BATCHED else 6 + (1 if large_on else 0)) \
         + (1 if wl == "W3S" else 0)
     ctx.close()
     return {"value": value, "t_max": t_max, "n": n, "kk": kk, "roofline": roofline, "plain_form": plain,
+            "per_set_form": per_set,
             "e2e": e2e, "cpu_baseline": cpu_baseline, "clocks": clocks, "tuning": tuning,
             "gpu_launches": launches_per_step * args.steps, "wall_s_timed": t_wall}
 
@@ -510,7 +544,8 @@ def gpu_arm(args):
         r2 = measure(args, "W2", local, dist, props, full=False)
         w2 = {"workload": WL_DESC["W2"], "value": r2["value"], "unit": "sets/s",
               "ms_per_step": r2["t_max"] * 1e3 / args.steps, "minhashes_per_s": r2["value"] * 1024,
-              "plain_form": r2["plain_form"], "roofline": r2["roofline"], "tuning": r2["tuning"],
+              "plain_form": r2["plain_form"], "per_set_form": r2["per_set_form"], "roofline": r2["roofline"],
+              "tuning": r2["tuning"],
               "clocks": r2["clocks"], "gpu_launches": r2["gpu_launches"]}
     desc = dict(WL_DESC)
     desc["W3S"] = (f"W3 sets with each set's weight class normalised to ||x||_1 in [2^{args.norm_exp}, "
@@ -528,7 +563,7 @@ def gpu_arm(args):
                                + (" + autotuned" if r["tuning"] else ""),
                        "l2": "inputs and outputs of a step are GBs, > 129 MB L2: no flush needed"},
             "roofline": r["roofline"], "cpu_baseline": r["cpu_baseline"], "e2e": r["e2e"], "clocks": r["clocks"],
-            "plain_form": r["plain_form"], "tuning": r["tuning"],
+            "plain_form": r["plain_form"], "per_set_form": r["per_set_form"], "tuning": r["tuning"],
             "gpu_launches": r["gpu_launches"] + (w2["gpu_launches"] if w2 else 0),
             "wall_s_timed": r["wall_s_timed"], "w2": w2,
         }

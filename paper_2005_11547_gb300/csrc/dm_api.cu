@@ -88,7 +88,7 @@ struct dm_ctx {
     cudaStream_t capture_stream = nullptr;
     // resident blocks per SM, per kernel and launch shape
     std::vector<std::pair<uint64_t, int>> occupancy;
-    // side stream of the large-set kernel (created on first use)
+    // side stream of the batched form's large-set and general kernels (created on first use)
     dm::SideStream side = {nullptr, nullptr, nullptr};
     bool side_ready = false;
 };
@@ -330,12 +330,10 @@ cudaError_t ensure_side(dm_ctx *ctx) {
 
 cudaError_t launch_plan(dm_ctx *ctx, const Plan &pl, cudaStream_t st) {
     if (pl.form == 0) {
-        const dm::SideStream *side = nullptr;
-        if (pl.grid_large > 0 && pl.kind == dm::kSketch) {
-            cudaError_t e = ensure_side(ctx);
-            if (e != cudaSuccess) return e;
-            side = &ctx->side;
-        }
+        // the side stream carries the large-set kernel and the general kernel beside the fast one
+        cudaError_t e = ensure_side(ctx);
+        if (e != cudaSuccess) return e;
+        const dm::SideStream *side = &ctx->side;
         return dm::launch_batched(pl.p, pl.kind, pl.bbit, pl.count, pl.grid_fast, pl.grid_general, pl.grid_large, st,
                                   side);
     }

@@ -50,6 +50,10 @@ struct SketchParams {
     float large_work;           // so do sets whose Lemma 2 work estimate reaches this (0: off)
     int32_t large_warps;        // warps per block of the large-set kernel
     int32_t key_row;            // sketches: bucket minima in out_keys, shared memory holds codes only
+    // general kernel of the batched form: 0 every queued set; 1 the sets classified general
+    // (queue[0, class total), runs beside the fast kernel); 2 the sets the fast kernel deferred
+    // (queue[class total, queue count), after the fast kernel)
+    int32_t gen_part;
 };
 
 // Shared memory per warp of the fast (mode 0) or general (mode 1) kernel, and of its sink
@@ -79,8 +83,9 @@ cudaError_t launch_sets(const SketchParams &p, int kind, bool bbit, bool count, 
 // estimate), then the persistent
 // fast kernel, the persistent general kernel (general sets and those the fast kernel defers)
 // and, for sketches, the block-per-set kernel over large sets.  grid_large = 0: no large class.
-// A second stream for the large-set kernel, forked from and joined back to the call's stream
-// with the two events (so the sequence stays capturable as a graph).
+// A second stream for the large-set kernel and the general kernel over the sets classified
+// general, forked from and joined back to the call's stream with the two events (so the sequence
+// stays capturable as a graph).
 struct SideStream {
     cudaStream_t st;
     cudaEvent_t fork, join;

@@ -163,8 +163,9 @@ class CudaExecutor : public dm::serve::Executor {
                 for (int i = 0; i < kGroupStreams; ++i) cudaStreamSynchronize(L.gst[i]);
                 return rc;
             }
-            // kernels of the form: fast + general, plus classify, scan, scatter, large (batched)
-            kernel_launches += form == 0 ? 6 : 2;
+            // kernels of the form: fast + general, plus classify, scan, scatter, large and the
+            // general kernel's second launch over the fast kernel's deferrals (batched)
+            kernel_launches += form == 0 ? 7 : 2;
         }
         if (fork)
             for (int i = 0; i < kGroupStreams && (size_t)i < groups.size(); ++i)

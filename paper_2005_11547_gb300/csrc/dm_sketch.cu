@@ -39,7 +39,9 @@ constexpr int kMaxPasses = 21;     // phi0 * 2^20 at most (Theorem 1's loop limi
 constexpr int kDefer = -1;         // a pass the fast kernel leaves to the general kernel
 // batched form: hist[0..96) bin counts, [96..192) bin cursors, [192..195) class totals
 constexpr int kClasses = 3, kBins = 32, kCursors = kClasses * kBins, kTotals = 2 * kClasses * kBins;
+constexpr int kDeferNext = kTotals + kClasses;   // hist word: next deferred set of the general kernel
 constexpr size_t kHeaderBytes = 1024;   // queue count, 3 work counters, histogram, totals
+static_assert((4 + kDeferNext + 1) * sizeof(unsigned int) <= kHeaderBytes, "header holds every counter");
 constexpr int kMaxDevices = 64;
 
 __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
@@ -940,9 +942,12 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) set_kernel(const Sketc
     sink.bind(wbase, p);
     const FastMem fm = carve_fast(wbase + p.sink_bytes);
     const GenMem gm = carve_gen(wbase + p.sink_bytes);
-    const int64_t n_work = MODE == 1 ? (int64_t)*p.queue_count
+    // general kernel: the queued sets [w0, n_work) (see gen_part); fast kernel: the fast sets of
+    // the batched form, or every set
+    const int64_t w0 = MODE == 1 && p.gen_part == 2 ? (int64_t)p.hist[kTotals + 1] : 0;
+    const int64_t n_work = MODE == 1 ? (p.gen_part == 1 ? (int64_t)p.hist[kTotals + 1] : (int64_t)*p.queue_count)
                                      : (p.sched == 2 ? (int64_t)p.hist[kTotals] : p.n_sets);
-    unsigned int *next = p.work_next + MODE;
+    unsigned int *next = MODE == 1 && p.gen_part == 2 ? p.hist + kDeferNext : p.work_next + MODE;
     const int64_t static_wi = (int64_t)blockIdx.x * p.warps_per_block + wib;
     for (int round = 0;; ++round) {
         int64_t wi;
@@ -952,7 +957,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) set_kernel(const Sketc
         } else {
             unsigned int c = 0;
             if (lane == 0) c = atomicAdd(next, 1u);
-            wi = (int64_t)__shfl_sync(kFull, c, 0);
+            wi = w0 + (int64_t)__shfl_sync(kFull, c, 0);
         }
         if (wi >= n_work) break;
         const int64_t set = MODE == 1 ? (int64_t)p.queue[wi] : (p.sched == 2 ? (int64_t)p.order[wi] : wi);
@@ -1357,39 +1362,49 @@ cudaError_t launch_batched(const SketchParams &p0, int kind, bool bbit, bool cou
     const int sgrid = (int)((p.n_sets + 255) / 256 < 4096 ? (p.n_sets + 255) / 256 : 4096);
     scatter_kernel<<<sgrid, 256, 0, st>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // the large sets are independent of the fast kernel's deferrals: with a side stream their
-    // kernel runs beside the fast and general kernels (each fills the SMs the other leaves),
-    // else first, so that their blocks become resident before the fast kernel's
+    // With a side stream, the large sets' block kernel and then the general kernel over the sets
+    // classified general run there, beside the fast kernel (none of them waits for another: each
+    // takes the SMs the others leave, so the fast kernel's tail fills with general work); the
+    // general kernel over the fast kernel's deferrals follows the fast kernel.  The fast kernel
+    // is launched before the general one, so it is the first to fill the SMs.  Without one, the
+    // large kernel runs first (its blocks become resident before the fast kernel's), then the
+    // fast kernel, then the general kernel over every queued set.
     const bool large = !lsh && grid_large > 0 && (p.large_nnz > 0 || p.large_work > 0.f);
-    cudaStream_t lst = st;
-    if (large && side) {
+    if (side) {
         if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(side->st, side->fork, 0)) != cudaSuccess)
             return e;
-        lst = side->st;
     }
+    cudaStream_t sst = side ? side->st : st;
     if (large) {
-        if ((e = count ? (bbit ? launch_large<true, true>(p, grid_large, lst) : launch_large<false, true>(p, grid_large, lst))
-                       : (bbit ? launch_large<true, false>(p, grid_large, lst) : launch_large<false, false>(p, grid_large, lst)))
+        if ((e = count ? (bbit ? launch_large<true, true>(p, grid_large, sst) : launch_large<false, true>(p, grid_large, sst))
+                       : (bbit ? launch_large<true, false>(p, grid_large, sst) : launch_large<false, false>(p, grid_large, sst)))
             != cudaSuccess)
             return e;
     }
-    if (kind == kLsh) {
-        if ((e = launch_mode<LshSink, 0>(p, false, count, grid_fast, st)) != cudaSuccess) return e;
-        return launch_mode<LshSink, 1>(p, false, count, grid_general, st);
-    }
-    if (kind == kBottomK) {
-        if ((e = launch_mode<BottomKSink, 0>(p, false, count, grid_fast, st)) != cudaSuccess) return e;
-        return launch_mode<BottomKSink, 1>(p, false, count, grid_general, st);
-    }
-    if (p.key_row) {
-        if ((e = launch_mode<RowSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
-        if ((e = launch_mode<RowSink, 1>(p, bbit, count, grid_general, st)) != cudaSuccess) return e;
-    } else {
-        if ((e = launch_mode<SketchSink, 0>(p, bbit, count, grid_fast, st)) != cudaSuccess) return e;
-        if ((e = launch_mode<SketchSink, 1>(p, bbit, count, grid_general, st)) != cudaSuccess) return e;
-    }
-    if (large && side) {
+    SketchParams pa = p, pb = p;
+    pa.gen_part = side ? 1 : 0;
+    pb.gen_part = 2;
+    auto run = [&](auto fast, auto general) -> cudaError_t {
+        cudaError_t r;
+        if ((r = fast(p, st)) != cudaSuccess) return r;
+        if (side && (r = general(pa, sst)) != cudaSuccess) return r;
+        return general(side ? pb : pa, st);
+    };
+    if (kind == kLsh)
+        e = run([&](const SketchParams &q, cudaStream_t s) { return launch_mode<LshSink, 0>(q, false, count, grid_fast, s); },
+                [&](const SketchParams &q, cudaStream_t s) { return launch_mode<LshSink, 1>(q, false, count, grid_general, s); });
+    else if (kind == kBottomK)
+        e = run([&](const SketchParams &q, cudaStream_t s) { return launch_mode<BottomKSink, 0>(q, false, count, grid_fast, s); },
+                [&](const SketchParams &q, cudaStream_t s) { return launch_mode<BottomKSink, 1>(q, false, count, grid_general, s); });
+    else if (p.key_row)
+        e = run([&](const SketchParams &q, cudaStream_t s) { return launch_mode<RowSink, 0>(q, bbit, count, grid_fast, s); },
+                [&](const SketchParams &q, cudaStream_t s) { return launch_mode<RowSink, 1>(q, bbit, count, grid_general, s); });
+    else
+        e = run([&](const SketchParams &q, cudaStream_t s) { return launch_mode<SketchSink, 0>(q, bbit, count, grid_fast, s); },
+                [&](const SketchParams &q, cudaStream_t s) { return launch_mode<SketchSink, 1>(q, bbit, count, grid_general, s); });
+    if (e != cudaSuccess) return e;
+    if (side) {
         if ((e = cudaEventRecord(side->join, side->st)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess)
             return e;
