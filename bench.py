@@ -500,8 +500,8 @@ def measure(args, wl, local, dist, props, full):
     cpu_baseline = None
     if full and rank == 0 and world == 1 and not args.no_cpu_baseline and wl == "W1":
         cores = os.cpu_count() or 1
-        v, ns, dt = time_oracle(b, 16000 * cores // 4, cores)
-        v1, ns1, dt1 = time_oracle(b, 4000, 1)
+        v, ns, dt = time_oracle(b, 8000 * cores, cores)         # about 30 core-seconds
+        v1, ns1, dt1 = time_oracle(b, 40000, 1)                 # about 10 seconds
         cpu_baseline = {"value": v, "unit": "sets/s", "cores": cores, "kind": "oracle",
                         "sample": f"first {ns} sets of W1 ({dt:.1f} s wall on {cores} threads)",
                         "single_thread": {"value": v1, "unit": "sets/s", "cores": 1,

@@ -276,12 +276,20 @@ enum dm_option {
     DM_OPT_HOST_CHUNKS = 10,    /* dm_sketch_host: number of chunks (1..256, default 8) a batch is
                                    split into, so that one chunk's copies overlap another's kernels
                                    (chunks hold at least 4,096 sets) */
-    DM_OPT_HOST_MODE = 11       /* dm_sketch_host: 0 = staged (chunked copies to device buffers);
+    DM_OPT_HOST_MODE = 11,      /* dm_sketch_host: 0 = staged (chunked copies to device buffers);
                                    1 = in place (the kernels read the input arrays and write the
                                    outputs through the device's mapping of page-locked host memory,
                                    so the transfers ride on the kernels' own loads and stores; the
                                    call fails with DM_EINVAL if an array is not mapped); 2 (default)
                                    = in place when every array is page-locked and mapped, else staged */
+    DM_OPT_SLOTS = 12           /* sketches: where the k bucket minima live while a set is sketched.
+                                   0 (default) = automatic (the row layout for k >= 512 when keys
+                                   are written to device memory, else shared memory); 1 = shared
+                                   memory (k 64-bit minima per warp); 2 = the output row (shared
+                                   memory holds each bucket's 32-bit rank code as a filter, the
+                                   64-bit minimum is taken with an atomic minimum on the key in
+                                   the output row; needs out_keys in device memory, else the call
+                                   falls back to shared memory) */
 };
 int dm_set_option(dm_ctx *ctx, int option, int64_t value);
 
@@ -295,6 +303,7 @@ typedef struct dm_tuning {
     int64_t sets_timed;       /* rows of the batch the trials ran on */
     float ms_default;         /* median time of the trial batch with the context's options */
     float ms_tuned;           /* median time with the chosen settings */
+    int32_t slots;            /* DM_OPT_SLOTS value */
 } dm_tuning;
 
 /* Launch-setting search (the paper has no counterpart; results never depend on the choice).
@@ -302,7 +311,7 @@ typedef struct dm_tuning {
  * (lsh = 1, k = L, K_or_b = K) or dm_bottomk (lsh = 2, K_or_b = 0) would make on the first min(n_sets, max_sets) rows (max_sets <= 0:
  * 65536) of the given device batch, timing each candidate with CUDA events on `stream` (median of
  * three runs after a warm-up): initial phi, then warps per block, then the large-set threshold,
- * then the form, each kept when it is faster.  Outputs of the trials go to temporary device
+ * then the form, then (sketches with keys) the slot storage, each kept when it is faster.  Outputs of the trials go to temporary device
  * memory (counted against the budget); the caller's batch is only read.  The choice is stored in
  * the context for later calls with the same (kind, k, K, b) (see DM_OPT_TUNED) and, when result is
  * not NULL, written there.  Synchronous.  Returns DM_EINVAL for n_sets == 0 or bad arguments and

@@ -21,11 +21,12 @@ from .build import LIB, build
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
            "dm_sketch_host", "dm_bottomk", "dm_compare", "dm_lsh_scaled", "dm_weight_classes", "LshIndex", "estimate_jaccard", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
            "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
-           "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "OPT_LARGE_WORK", "OPT_HOST_CHUNKS", "OPT_HOST_MODE", "HOST_STAGED", "HOST_IN_PLACE", "HOST_AUTO", "FORM_BATCHED",
+           "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "OPT_LARGE_WORK", "OPT_HOST_CHUNKS", "OPT_HOST_MODE", "OPT_SLOTS", "SLOTS_AUTO", "SLOTS_SHARED", "SLOTS_ROW", "HOST_STAGED", "HOST_IN_PLACE", "HOST_AUTO", "FORM_BATCHED",
            "FORM_PLAIN", "FORM_PERSISTENT", "dm_autotune", "Tuning", "Server", "EAGAIN"]
 
 OPT_PHI0, OPT_COUNTERS, OPT_FORM, OPT_WARPS_PER_BLOCK, OPT_LSH_PHI0, OPT_LARGE_NNZ = 1, 2, 3, 4, 5, 6
-OPT_GRAPH, OPT_TUNED, OPT_LARGE_WORK, OPT_HOST_CHUNKS, OPT_HOST_MODE = 7, 8, 9, 10, 11
+OPT_GRAPH, OPT_TUNED, OPT_LARGE_WORK, OPT_HOST_CHUNKS, OPT_HOST_MODE, OPT_SLOTS = 7, 8, 9, 10, 11, 12
+SLOTS_AUTO, SLOTS_SHARED, SLOTS_ROW = 0, 1, 2
 HOST_STAGED, HOST_IN_PLACE, HOST_AUTO = 0, 1, 2
 EAGAIN, ETIMEOUT = 7, 4
 FORM_BATCHED, FORM_PLAIN, FORM_PERSISTENT = 0, 1, 2
@@ -442,7 +443,7 @@ class Tuning(ctypes.Structure):
     """dm_tuning: the settings dm_autotune chose."""
     _fields_ = [("form", ctypes.c_int32), ("warps_per_block", ctypes.c_int32), ("phi0_1024", ctypes.c_int32),
                 ("large_nnz", ctypes.c_int32), ("large_work", ctypes.c_int32), ("sets_timed", ctypes.c_int64),
-                ("ms_default", ctypes.c_float), ("ms_tuned", ctypes.c_float)]
+                ("ms_default", ctypes.c_float), ("ms_tuned", ctypes.c_float), ("slots", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -467,6 +468,7 @@ def dm_set_tuning(ctx: Context, k: int, tuning: dict, b: int = 0, lsh_K: int = 0
     t = Tuning()
     for f in ("form", "warps_per_block", "phi0_1024", "large_nnz", "large_work"):
         setattr(t, f, int(tuning[f]))
+    t.slots = int(tuning.get("slots", 0))
     lsh = 2 if bottomk else (1 if lsh_K > 0 else 0)
     _check(load().dm_set_tuning(ctx.handle, lsh, int(k), int(lsh_K if lsh else b),
                                 ctypes.cast(ctypes.byref(t), ctypes.c_void_p)), "dm_set_tuning")

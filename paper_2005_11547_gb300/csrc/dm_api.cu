@@ -29,6 +29,7 @@ struct Choice {
     float phi0;         // initial phi of Theorem 1's loop
     int large_nnz;      // batched form: element count from which a set gets a whole block
     float large_work;   // batched form: Lemma 2 work estimate from which a set gets one (0: off)
+    int slots;          // sketch bucket minima: 0 automatic, 1 shared memory, 2 the output row
 };
 
 struct TunedEntry {
@@ -67,6 +68,7 @@ struct dm_ctx {
     int warps_per_block = 0;       // 0 = automatic
     int large_nnz = 2048;          // batched form: sets with this many elements get a block
     float large_work = 0.f;        // batched form: sets with this work estimate get a block
+    int slots = 0;                 // sketch bucket minima: 0 automatic, 1 shared memory, 2 output row
     int host_chunks = 8;           // host-buffer entry: chunks a batch is split into
     int host_mode = 2;             // host-buffer entry: 0 staged, 1 in place, 2 in place when possible
     bool host_out = false;         // the current call writes host memory in place: no key-row layout
@@ -180,6 +182,8 @@ int auto_warps(int kind, int k, int K, bool key_row = false) {
 int check_csr(const int64_t *indptr, const uint32_t *indices, const float *weights, int64_t n) {
     if (n < 0) return DM_EINVAL;
     if (n > 0 && (!indptr || !indices || !weights)) return DM_EINVAL;
+    // every array aligned to its element size (a misaligned load would fault on the device)
+    if (((uintptr_t)indptr & 7u) || ((uintptr_t)indices & 3u) || ((uintptr_t)weights & 3u)) return DM_EINVAL;
     return DM_OK;
 }
 
@@ -214,7 +218,7 @@ int occupancy(dm_ctx *ctx, int which, int kind, bool bbit, int wpb, size_t smem,
 
 Choice choose(const dm_ctx *ctx, int kind, int k, int K, int b) {
     Choice c{ctx->form, ctx->warps_per_block, kind == dm::kLsh ? ctx->phi0_lsh : ctx->phi0, ctx->large_nnz,
-             ctx->large_work};
+             ctx->large_work, ctx->slots};
     if (ctx->use_tuned)
         for (const auto &e : ctx->tuned)
             if (e.kind == kind && e.k == k && e.K == K && e.b == b) return e.c;
@@ -252,8 +256,10 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
     if (bbit && !out_words) return DM_EINVAL;
     if (n_sets == 0) return DM_OK;
     if (n_sets > 0x7FFFFFFF) return DM_EINVAL;
-    // large sketches with keys: codes in shared memory, minima in the output row
-    const bool key_row = kind == dm::kSketch && out_keys && k >= dm::kKeyRowMinK && !ctx->host_out;
+    // sketches with keys in device memory may keep their minima in the output row (codes in
+    // shared memory): by default from k = 512 on, or as DM_OPT_SLOTS says
+    const bool row_ok = kind == dm::kSketch && out_keys && !ctx->host_out;
+    const bool key_row = row_ok && (ch.slots == 2 || (ch.slots == 0 && k >= dm::kKeyRowMinK));
     const int wpb = ch.wpb > 0 ? ch.wpb : auto_warps(kind, k, K, key_row);
     const size_t smem_fast = dm::warp_bytes(kind, k, K, 0, key_row) * wpb,
                  smem = dm::warp_bytes(kind, k, K, 1, key_row) * wpb;
@@ -790,7 +796,7 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
     const bool use_graph = ctx->use_graph;
     ctx->use_graph = false;                          // trials of one-off plans
     Choice best{ctx->form == 1 ? 0 : ctx->form, ctx->warps_per_block, is_lsh ? ctx->phi0_lsh : ctx->phi0,
-                ctx->large_nnz, ctx->large_work};
+                ctx->large_nnz, ctx->large_work, ctx->slots};
     float best_ms = 0.f, default_ms = 0.f;
     rc = e == cudaSuccess ? time_choice(best, best_ms) : cuda_fail(e);
     default_ms = best_ms;
@@ -819,6 +825,9 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
             try_set([](Choice &c, float v) { c.large_work = v; },
                     std::vector<float>{0.f, 16384.f, 32768.f, 65536.f, 131072.f});
         try_set([](Choice &c, int v) { c.form = v; }, std::vector<int>{0, 2});
+        // slot storage: the bucket minima in shared memory or in the output row (sketches whose
+        // trials write keys, i.e. b = 0)
+        if (kind == dm::kSketch && b == 0) try_set([](Choice &c, int v) { c.slots = v; }, std::vector<int>{1, 2});
     }
     ctx->use_graph = use_graph;
     for (auto &x : ev)
@@ -836,14 +845,15 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
     if (!found) ctx->tuned.push_back(TunedEntry{kind, k, K, b, best});
     if (result) {
         result->form = best.form;
-        result->warps_per_block =
-            best.wpb > 0 ? best.wpb : auto_warps(kind, k, K, kind == dm::kSketch && b == 0 && k >= dm::kKeyRowMinK);
+        const bool row = kind == dm::kSketch && b == 0 && (best.slots == 2 || (best.slots == 0 && k >= dm::kKeyRowMinK));
+        result->warps_per_block = best.wpb > 0 ? best.wpb : auto_warps(kind, k, K, row);
         result->phi0_1024 = (int32_t)(best.phi0 * 1024.0f + 0.5f);
         result->large_nnz = best.large_nnz;
         result->large_work = (int32_t)best.large_work;
         result->sets_timed = n;
         result->ms_default = default_ms;
         result->ms_tuned = best_ms;
+        result->slots = best.slots;
     }
     return DM_OK;
 }
@@ -908,6 +918,10 @@ int dm_set_option(dm_ctx *ctx, int option, int64_t value) {
             if (value < 0 || value > 2) return DM_EINVAL;
             ctx->host_mode = (int)value;
             return DM_OK;
+        case DM_OPT_SLOTS:
+            if (value < 0 || value > 2) return DM_EINVAL;
+            ctx->slots = (int)value;
+            return DM_OK;
         case DM_OPT_LSH_PHI0:
             if (value < 1 || value > 1024 * 1024) return DM_EINVAL;
             ctx->phi0_lsh = (float)value / 1024.0f;
@@ -938,10 +952,11 @@ int dm_set_tuning(dm_ctx *ctx, int32_t lsh, int32_t k, int32_t K_or_b, const dm_
     if (!ctx || !tuning || lsh < 0 || lsh > 2 || k < 1) return DM_EINVAL;
     const dm_tuning &t = *tuning;
     if (t.form < 0 || t.form > 2 || t.warps_per_block < 0 || t.warps_per_block > 8 || t.phi0_1024 < 1 ||
-        t.phi0_1024 > 1024 * 1024 || t.large_nnz < 0 || t.large_work < 0)
+        t.phi0_1024 > 1024 * 1024 || t.large_nnz < 0 || t.large_work < 0 || t.slots < 0 || t.slots > 2)
         return DM_EINVAL;
     const int kind = lsh, K = kind == dm::kLsh ? K_or_b : 0, b = kind == dm::kSketch ? K_or_b : 0;
-    const Choice c{t.form, t.warps_per_block, (float)t.phi0_1024 / 1024.0f, t.large_nnz, (float)t.large_work};
+    const Choice c{t.form, t.warps_per_block, (float)t.phi0_1024 / 1024.0f, t.large_nnz, (float)t.large_work,
+                   t.slots};
     for (auto &e : ctx->tuned)
         if (e.kind == kind && e.k == k && e.K == K && e.b == b) {
             e.c = c;

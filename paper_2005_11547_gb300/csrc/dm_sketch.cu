@@ -932,6 +932,29 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
 // 32-bit walk, send the set to the queue.  MODE 1 (general): sets from the queue, every pass
 // with the general walk.  Warps are persistent and claim work items from a global counter.
 // ==========================================================================================
+// Visits the weights w[beg, end) of a row with n threads (this one is number i < n): 128-bit
+// loads over the row's 16-byte-aligned middle, 32-bit loads for the at most three weights before
+// it and three after it.  Each weight is visited by exactly one thread, in no particular order.
+template <class F>
+__device__ __forceinline__ void for_row_weights(const float *w, int64_t beg, int64_t end, int i, int n, F &&f) {
+    const float *row = w + beg;
+    const int64_t len = end - beg;
+    const uint32_t mis = (uint32_t)reinterpret_cast<uintptr_t>(row) & 15u;
+    int64_t head = (mis & 3u) ? len : (int64_t)(((16u - mis) & 15u) >> 2);   // a float* is 4-byte aligned
+    if (head > len) head = len;
+    const int64_t nv = (len - head) >> 2;
+    for (int64_t j = i; j < head; j += n) f(row[j]);
+    const float4 *v = reinterpret_cast<const float4 *>(row + head);
+    for (int64_t j = i; j < nv; j += n) {
+        const float4 q = v[j];
+        f(q.x);
+        f(q.y);
+        f(q.z);
+        f(q.w);
+    }
+    for (int64_t j = head + 4 * nv + i; j < len; j += n) f(row[j]);
+}
+
 template <class Sink, bool BBIT, bool COUNT, int MODE>
 __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) set_kernel(const SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -965,11 +988,10 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) set_kernel(const Sketc
         // ||x||_1 and input validation
         float l1 = 0.f;
         bool bad = false;
-        for (int64_t i = beg + lane; i < end; i += 32) {
-            float x = p.weights[i];
+        for_row_weights(p.weights, beg, end, lane, 32, [&](float x) {
             if (!(x >= 0.f) || isinf(x)) bad = true;
             else l1 += x;
-        }
+        });
 #pragma unroll
         for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(kFull, l1, o);
         int err = __any_sync(kFull, bad) ? DM_EINVAL : 0;
@@ -1050,11 +1072,10 @@ __global__ void __launch_bounds__(256) classify_kernel(const SketchParams p) {
     for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < p.n_sets; s += nw) {
         const int64_t beg = p.indptr[s], end = p.indptr[s + 1], nnz = end - beg;
         float l1 = 0.f, wlog = 0.f;
-        for (int64_t i = beg + lane; i < end; i += 32) {
-            const float x = p.weights[i];
+        for_row_weights(p.weights, beg, end, lane, 32, [&](float x) {
             l1 += x;
             if (x > 0.f) wlog += __log2f(1.0f + t * x) + 1.0f;
-        }
+        });
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             l1 += __shfl_xor_sync(kFull, l1, o);
@@ -1099,16 +1120,16 @@ __global__ void __launch_bounds__(32 * kClassWarps) weight_class_kernel(const in
     for (int64_t s = (int64_t)blockIdx.x * kClassWarps + wid; s < n_sets; s += nw) {
 #pragma unroll
         for (int d = 0; d < kClassDigits; ++d) acc[wid][d][lane] = 0;
-        for (int64_t i = indptr[s] + lane; i < indptr[s + 1]; i += 32) {
-            const uint32_t xb = __float_as_uint(weights[i]), ex = xb >> 23;
-            if (xb == 0 || ex >= 255u) continue;          // zero, negative (sign bit set), NaN or infinite
+        for_row_weights(weights, indptr[s], indptr[s + 1], lane, 32, [&](float x) {
+            const uint32_t xb = __float_as_uint(x), ex = xb >> 23;
+            if (xb == 0 || ex >= 255u) return;            // zero, negative (sign bit set), NaN or infinite
             const uint32_t M = ex ? (xb & 0x7FFFFFu) | 0x800000u : xb;
             const uint32_t sh = (ex ? ex : 1u) - 1u;
             const uint64_t v = (uint64_t)M << (sh & 31u);   // below 2^55: digits sh / 32 and sh / 32 + 1
             const uint32_t d = sh >> 5;
             acc[wid][d][lane] += (uint32_t)v;
             acc[wid][d + 1][lane] += v >> 32;
-        }
+        });
         __syncwarp();
         if (lane < kClassDigits) {                       // digit sums over the 32 columns
             uint64_t t = 0;
@@ -1190,11 +1211,10 @@ __global__ void __launch_bounds__(256, 2) large_kernel(const SketchParams p) {
         const bool split = end - beg < 64 * (int64_t)nwarps;
         float l1 = 0.f;
         int bad = 0;
-        for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-            float x = p.weights[i];
+        for_row_weights(p.weights, beg, end, (int)threadIdx.x, (int)blockDim.x, [&](float x) {
             if (!(x >= 0.f) || isinf(x)) bad = 1;
             else l1 += x;
-        }
+        });
 #pragma unroll
         for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(kFull, l1, o);
         if (lane == 0) wsum[wid] = l1;

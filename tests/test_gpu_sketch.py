@@ -189,6 +189,29 @@ def test_invalid_and_out_of_range_weights(dmx, torch_mod, ctx, oracle_mod):
         assert e.value.code == 5
 
 
+def test_misaligned_arrays_are_rejected(dmx, torch_mod, ctx):
+    """An array not aligned to its element size is refused before any launch (DM_EINVAL); the
+    weights of aligned rows at every offset mod 4 (the 128-bit row scans' ragged ends) are
+    covered by the ragged-set tests."""
+    torch = torch_mod
+    b = workloads.random_sets(10, 1, 20, 1000, seed=3)
+    ip, ix, w = to_dev(torch, b)
+    out = torch.empty((10, 64), dtype=torch.int64, device="cuda")
+    lib = dmx.load()
+    cases = ((ip.data_ptr() + 4, ix.data_ptr(), w.data_ptr()), (ip.data_ptr(), ix.data_ptr() + 2, w.data_ptr()),
+             (ip.data_ptr(), ix.data_ptr(), w.data_ptr() + 1))
+    for dip, dix, dw in cases:
+        rc = lib.dm_sketch(ctx.handle, ctypes_ptr(dip), ctypes_ptr(dix), ctypes_ptr(dw), 10, 64, 1,
+                           ctypes_ptr(out.data_ptr()), dmx._stream(None))
+        assert rc == 1
+    assert dmx.dm_sync_status(ctx, raise_on_error=False) == 0
+
+
+def ctypes_ptr(v):
+    import ctypes
+    return ctypes.c_void_p(v)
+
+
 @pytest.mark.parametrize("bits", [1, 2, 4, 8, 16, 32])
 def test_bbit_parity(dmx, torch_mod, ctx, oracle_mod, bits):
     b = workloads.random_sets(200, 1, 120, 1 << 20, seed=70 + bits)
@@ -211,7 +234,8 @@ def test_options_do_not_change_bits(dmx, torch_mod, ctx):
     for opt, val in [(dmx.OPT_PHI0, 512), (dmx.OPT_PHI0, 4096), (dmx.OPT_PHI0, 1024 * 3),
                      (dmx.OPT_WARPS_PER_BLOCK, 1), (dmx.OPT_WARPS_PER_BLOCK, 3),
                      (dmx.OPT_FORM, dmx.FORM_PLAIN), (dmx.OPT_FORM, dmx.FORM_PERSISTENT),
-                     (dmx.OPT_LARGE_NNZ, 0), (dmx.OPT_LARGE_NNZ, 40), (dmx.OPT_LARGE_NNZ, 150)]:
+                     (dmx.OPT_LARGE_NNZ, 0), (dmx.OPT_LARGE_NNZ, 40), (dmx.OPT_LARGE_NNZ, 150),
+                     (dmx.OPT_SLOTS, dmx.SLOTS_SHARED), (dmx.OPT_SLOTS, dmx.SLOTS_ROW)]:
         c2 = dmx.dm_create(0)
         dmx.dm_set_option(c2, opt, val)
         got, rc = gpu_sketch(dmx, torch_mod, c2, b, 256, 77)
@@ -239,6 +263,32 @@ def test_forms_on_heavy_tailed_batch(dmx, torch_mod, oracle_mod, form):
         got, rc = gpu_sketch(dmx, torch_mod, c2, b, k, 17)
         assert rc == 0
         assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 17, threads=THREADS), f"form {form} k={k}")
+    c2.close()
+
+
+@pytest.mark.parametrize("slots", [1, 2])
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_slot_storage_layouts(dmx, torch_mod, oracle_mod, form, slots):
+    """Bucket minima in shared memory (1) or in the output row with shared rank codes as a filter
+    (2), at small and large k, in every form (the batched one with a block-per-set class): the
+    oracle's bits either way."""
+    rng = np.random.default_rng(91)
+    rows = []
+    for s in range(300):
+        nnz = int(min(5000, max(1, np.exp(np.log(60) + 1.3 * rng.standard_normal()))))
+        idx = np.sort(rng.choice(1 << 24, nnz, replace=False)).astype(np.uint32)
+        z = rng.lognormal(size=nnz)
+        rows.append((idx, (z / z.sum() * 10 ** rng.uniform(-3, 3)).astype(np.float32)))
+    b = workloads.csr_of(rows)
+    c2 = dmx.dm_create(0)
+    dmx.dm_set_option(c2, dmx.OPT_FORM, form)
+    dmx.dm_set_option(c2, dmx.OPT_SLOTS, slots)
+    dmx.dm_set_option(c2, dmx.OPT_LARGE_NNZ, 400)
+    for k in (7, 256, 1024):
+        got, rc = gpu_sketch(dmx, torch_mod, c2, b, k, 29)
+        assert rc == 0
+        assert_same(got, oracle_mod.sketch(b.indptr, b.indices, b.weights, k, 29, threads=THREADS),
+                    f"form {form} slots {slots} k={k}")
     c2.close()
 
 

@@ -128,6 +128,7 @@ def test_autotune_keeps_bits_sketch(dmx, torch_mod, oracle_mod, heavy):
     assert 1 <= res["warps_per_block"] <= 8
     assert res["phi0_1024"] in (1024, 1280, 1536, 2048)
     assert res["sets_timed"] == 1000
+    assert res["slots"] in (0, 1, 2)
     assert 0 < res["ms_tuned"] <= res["ms_default"]
     after = dmx.dm_sketch(ctx, ip, ix, w, k, 3)
     assert torch.equal(before, after)
@@ -191,6 +192,11 @@ def test_saved_tunings_reinstall(dmx, torch_mod, tmp_path):
     bad = dict(t, form=7)
     with pytest.raises(dmx.DartMinHashError):
         dmx.dm_set_tuning(c2, 256, bad)
+    with pytest.raises(dmx.DartMinHashError):
+        dmx.dm_set_tuning(c2, 256, dict(t, slots=3))
+    # the other slot layout, installed as a tuning, gives the same bits
+    dmx.dm_set_tuning(c2, 256, dict(t, slots=2 if t["slots"] != 2 else 1))
+    assert torch.equal(dmx.dm_sketch(c2, ip, ix, w, 256, 9), ref)
     assert dmx.dm_sync_status(c2, raise_on_error=False) == 0
     c1.close()
     c2.close()
