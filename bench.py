@@ -283,12 +283,14 @@ def measure(args, wl, local, dist, props, full):
     import workloads
 
     rank, world, _ = dist_env()
+    # every rank sketches a batch of its own, drawn from the same distribution (rank 0's is the
+    # workload itself): independent problems, no data-path collective
     if wl in ("W1", "W1B"):
-        b = workloads.workload1(args.sets or 1_000_000)
+        b = workloads.workload1(args.sets or 1_000_000, shard=rank)
     elif wl == "W2":
-        b = workloads.workload2(args.sets or 200_000)
+        b = workloads.workload2(args.sets or 200_000, shard=rank)
     else:
-        b = workloads.workload3(args.sets or 1_000_000)
+        b = workloads.workload3(args.sets or 1_000_000, shard=rank)
     lsh_kind = wl in ("W3", "W3S")
     n = b.n_sets
     kk = {"W1": K_SLOTS, "W2": 1024, "W3": 64, "W1B": K_SLOTS, "W3S": 64}[wl]

@@ -94,9 +94,10 @@ def workload0(n: int = 1000) -> Batch:
     return fixed_nnz_batch(n, 64, 100_000, "uniform01", 1000, "W0")
 
 
-def workload1(n: int = 1_000_000) -> Batch:
-    """W1: 1,000,000 sets x 256 distinct indices over d = 2^20, weights Exp(1)."""
-    return fixed_nnz_batch(n, 256, 1 << 20, "exp1", 1001, "W1")
+def workload1(n: int = 1_000_000, shard: int = 0) -> Batch:
+    """W1: 1,000,000 sets x 256 distinct indices over d = 2^20, weights Exp(1).  shard > 0 draws
+    another batch of the same distribution (data seed 1001 + 1000 shard), one per rank."""
+    return fixed_nnz_batch(n, 256, 1 << 20, "exp1", 1001 + 1000 * shard, "W1")
 
 
 def _ragged_distinct(rng, lens: np.ndarray, d: int) -> np.ndarray:
@@ -119,10 +120,11 @@ def _ragged_distinct(rng, lens: np.ndarray, d: int) -> np.ndarray:
         vals[dup] = rng.integers(0, d, size=int(dup.sum()), dtype=np.int64)
 
 
-def workload2(n: int = 200_000) -> Batch:
+def workload2(n: int = 200_000, shard: int = 0) -> Batch:
     """W2: heavy-tailed nnz (log-normal, median 100, sigma 1.5, clipped to [1, 1e5]) over
-    d = 2^24; weights lognormal(0, 1) rescaled so ||x||_1 is log-uniform on [1e-3, 1e3]."""
-    rng = _rng(1002)
+    d = 2^24; weights lognormal(0, 1) rescaled so ||x||_1 is log-uniform on [1e-3, 1e3].
+    shard > 0 draws another batch of the same distribution (data seed 1002 + 1000 shard)."""
+    rng = _rng(1002 + 1000 * shard)
     lens = np.clip(np.rint(np.exp(np.log(100.0) + 1.5 * rng.standard_normal(n))), 1, 100_000)
     lens = lens.astype(np.int64)
     idx = _ragged_distinct(rng, lens, 1 << 24)
@@ -198,9 +200,10 @@ def zipf_batch(n: int, nnz_lo: int, nnz_hi: int, d: int, s: float, seed: int, th
     return Batch(ip, idx, w, name, dict(n=n, d=d, zipf=s, seed=seed))
 
 
-def workload3(n: int = 1_000_000, threads: int | None = None) -> Batch:
-    """W3: tf-idf-like sets for (L, K) = (64, 8) LSH (see the module docstring)."""
-    return zipf_batch(n, 200, 2000, 1 << 20, 1.1, 1003, threads, "W3")
+def workload3(n: int = 1_000_000, threads: int | None = None, shard: int = 0) -> Batch:
+    """W3: tf-idf-like sets for (L, K) = (64, 8) LSH (see the module docstring).  shard > 0 draws
+    another batch of the same distribution (data seed 1003 + 1000 shard)."""
+    return zipf_batch(n, 200, 2000, 1 << 20, 1.1, 1003 + 1000 * shard, threads, "W3")
 
 
 def workload4_requests(rate: float = 50_000.0, seconds: float = 60.0, max_requests: int | None = None):
