@@ -616,13 +616,6 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         WalkF s{};
         if (left) s.locate(lo, m);
         for (uint32_t st = 0; st < steps; ++st) {
-            if (max(kt - kh, xt - xh) >= 32u) {
-                for (;;) {                        // serve full queues (each below 32 afterwards)
-                    if (kt - kh >= 32u) kept_step(32u);
-                    else if (xt - xh >= 32u) dart_step(32u);
-                    else break;
-                }
-            }
             // area step: X >= 1 and X >= 2 decide the first dart and the dart queue; the count
             // itself is resolved dart by dart from the Poisson uniform ua
             const bool act = left != 0;
@@ -639,6 +632,12 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
             push_kept(keep, d, s.r, (uint32_t)s.nu);
             push_darts(x2, a + 2 * kGolden, uthr | (1u << 26), s.vmax | ((uint32_t)s.nu << 24), s.r, ua, ulo);
             if (act && --left) s.advance(m);
+            // serve the full queues: each holds fewer than 32 entries before an area step, so
+            // fewer than 64 after it, and fewer than 32 again once served
+            while (((kt - kh) | (xt - xh)) >= 32u) {
+                if (kt - kh >= 32u) kept_step(32u);
+                else dart_step(32u);
+            }
         }
     }
     for (;;) {                                    // drain both queues
@@ -894,13 +893,6 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
         WalkG s{};
         if (left) s.locate(lo, m, pc);
         for (uint64_t st = 0; st < steps; ++st) {
-            if (max(kt - kh, xt - xh) >= 32u) {
-                for (;;) {                        // serve full queues (each below 32 afterwards)
-                    if (kt - kh >= 32u) kept_step(32u);
-                    else if (xt - xh >= 32u) dart_step(32u);
-                    else break;
-                }
-            }
             // area step: X >= 1 and X >= 2 from the Poisson uniform ua; the first dart at once
             const bool act = left != 0;
             const uint64_t a = mix64(s.ctr);
@@ -915,6 +907,10 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
             push_kept(x1 && vv <= ((uint32_t)pv & kUMask) && in_band(code), d, code);
             push_darts(x2, a + 2 * kGolden, pv, 1u | ((uint32_t)s.nu << 4) | ((uint32_t)s.rho << 10), ua);
             if (act && --left) s.advance(m, pc);
+            while (((kt - kh) | (xt - xh)) >= 32u) {   // serve the full queues (as in the fast pass)
+                if (kt - kh >= 32u) kept_step(32u);
+                else dart_step(32u);
+            }
         }
     }
     for (;;) {                                    // drain both queues
