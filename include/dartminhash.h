@@ -18,7 +18,9 @@
  *   - Unless a call says otherwise, every array argument is a DEVICE pointer owned by the
  *     caller; the library reads/writes it only on `stream` and keeps no reference after the
  *     work queued on `stream` completes.  `stream` is a cudaStream_t passed as void* (NULL =
- *     the legacy default stream).
+ *     the legacy default stream).  indptr, indices and weights must be aligned to their
+ *     element size (8, 4 and 4 bytes); a misaligned one is refused with DM_EINVAL before any
+ *     launch.
  *   - Output key layout: out[s * k + j] is minhash j of set s, the 64-bit key
  *         (code(rank) << 32) | fingerprint
  *     where code(rank) is the IEEE binary32 bit pattern of the winning dart's rank rounded
