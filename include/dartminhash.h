@@ -288,10 +288,11 @@ enum dm_option {
                                    0 (default) = automatic (the row layout for k >= 512 when keys
                                    are written to device memory, else shared memory); 1 = shared
                                    memory (k 64-bit minima per warp); 2 = the output row (shared
-                                   memory holds each bucket's 32-bit rank code as a filter, the
-                                   64-bit minimum is taken with an atomic minimum on the key in
-                                   the output row; needs out_keys in device memory, else the call
-                                   falls back to shared memory) */
+                                   memory holds a 16-bit filter per bucket, the high half of a
+                                   rank code already in the bucket's minimum; the 64-bit minimum
+                                   is taken with an atomic minimum on the key in the output row;
+                                   needs out_keys in device memory, else the call falls back to
+                                   shared memory).  The choice never changes an output bit. */
 };
 int dm_set_option(dm_ctx *ctx, int option, int64_t value);
 

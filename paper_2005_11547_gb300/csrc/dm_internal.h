@@ -61,7 +61,7 @@ struct SketchParams {
 size_t warp_bytes(int kind, int k, int K, int mode, bool key_row = false);
 size_t sink_bytes(int kind, int k, int K, bool key_row = false);
 
-// Sketches with at least this many buckets keep only rank codes in shared memory and their 64-bit
+// Sketches with at least this many buckets keep only a 16-bit filter per bucket in shared memory and their 64-bit
 // minima in the output row (key-row layout), when the call writes keys.
 constexpr int kKeyRowMinK = 512;
 

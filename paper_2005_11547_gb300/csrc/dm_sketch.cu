@@ -70,13 +70,13 @@ size_t lsh_sink_bytes(int L, int K) { return ((size_t)L * K * 8 + (size_t)L * 4 
 //    the row.  Ties in the code reach the row, whose 64-bit minimum decides them.
 // 0xFFFFFFFF marks an empty bucket's code: a kept dart's code is below bits(theta) < 0x7F800000.
 __host__ __device__ size_t sketch_sink_bytes(int k, bool key_row) {
-    return ((size_t)k * (key_row ? 4 : 8) + 15) & ~(size_t)15;
+    return ((size_t)k * (key_row ? 2 : 8) + 15) & ~(size_t)15;
 }
 
 template <bool KEYROW>
 struct SketchSinkT {
     uint64_t *slots;                              // shared layout: the k minima
-    uint32_t *codes;                              // key-row layout: the k smallest codes
+    uint16_t *codes;                              // key-row layout: a filter per bucket (see put)
     uint64_t *row;                                // key-row layout: the set's output row
     uint32_t k;
     uint32_t sbase;                               // shared-space address of the bucket array
@@ -84,7 +84,7 @@ struct SketchSinkT {
 
     __device__ void bind(unsigned char *base, const SketchParams &p) {
         slots = reinterpret_cast<uint64_t *>(base);
-        codes = reinterpret_cast<uint32_t *>(base);
+        codes = reinterpret_cast<uint16_t *>(base);
         k = (uint32_t)p.k;
         sbase = (uint32_t)__cvta_generic_to_shared(base);
         row = nullptr;
@@ -95,7 +95,7 @@ struct SketchSinkT {
     __device__ void reset(int lane) {
         if constexpr (KEYROW)
             for (uint32_t j = lane; j < k; j += 32) {
-                codes[j] = 0xFFFFFFFFu;
+                codes[j] = (uint16_t)0xFFFFu;
                 row[j] = ~0ull;
             }
         else
@@ -106,8 +106,16 @@ struct SketchSinkT {
         const uint32_t slot = fastrange32((uint32_t)(qh >> 32), k);
         const uint64_t key = ((uint64_t)code << 32) | (uint32_t)qh;
         if constexpr (KEYROW) {
-            if (code <= codes[slot] && code <= shared_min_u32(sbase + 4u * slot, code))
+            // The filter holds the high 16 bits of the code of a dart already in the bucket's
+            // row minimum, so it is at least the high half of the row minimum's code; a dart
+            // whose high half exceeds it cannot lower the minimum and is dropped.  Lanes may race
+            // on the plain store: whichever value is left is such a code, so the filter only ever
+            // lets more darts through to the exact 64-bit atomic minimum on the row.
+            const uint32_t c16 = code >> 16, cur = codes[slot];
+            if (c16 <= cur) {
+                if (c16 < cur) codes[slot] = (uint16_t)c16;
                 atomicMin(reinterpret_cast<unsigned long long *>(&row[slot]), (unsigned long long)key);
+            }
         } else {
             shared_min_u64(sbase + 8u * slot, key);
         }
@@ -118,7 +126,7 @@ struct SketchSinkT {
         if (have) put(qh, code);
     }
     __device__ bool empty_bucket(uint32_t j) const {
-        if constexpr (KEYROW) return codes[j] == 0xFFFFFFFFu;
+        if constexpr (KEYROW) return codes[j] == (uint16_t)0xFFFFu;        // codes are below 0x7F80_0000
         return slots[j] == ~0ull;
     }
     __device__ bool filled(int lane) {
@@ -169,7 +177,7 @@ struct SketchSinkT {
     }
 };
 using SketchSink = SketchSinkT<false>;   // bucket minima in shared memory
-using RowSink = SketchSinkT<true>;       // codes in shared memory, minima in the output row
+using RowSink = SketchSinkT<true>;       // 16-bit filters in shared memory, minima in the output row
 
 // L buckets, each the K smallest keys of the darts hashed to it ((L, K) LSH), kept sorted in
 // shared memory.  A batch of kept darts is inserted by the whole warp: darts of different buckets
