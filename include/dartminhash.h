@@ -285,8 +285,8 @@ enum dm_option {
                                    call fails with DM_EINVAL if an array is not mapped); 2 (default)
                                    = in place when every array is page-locked and mapped, else staged */
     DM_OPT_SLOTS = 12           /* sketches: where the k bucket minima live while a set is sketched.
-                                   0 (default) = automatic (the row layout for k >= 512 when keys
-                                   are written to device memory, else shared memory); 1 = shared
+                                   0 (default) = automatic (the row layout when keys are written
+                                   to device memory, else shared memory); 1 = shared
                                    memory (k 64-bit minima per warp); 2 = the output row (shared
                                    memory holds a 16-bit filter per bucket, the high half of a
                                    rank code already in the bucket's minimum; the 64-bit minimum

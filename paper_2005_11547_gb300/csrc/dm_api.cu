@@ -256,10 +256,10 @@ int plan_call(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const
     if (bbit && !out_words) return DM_EINVAL;
     if (n_sets == 0) return DM_OK;
     if (n_sets > 0x7FFFFFFF) return DM_EINVAL;
-    // sketches with keys in device memory may keep their minima in the output row (codes in
-    // shared memory): by default from k = 512 on, or as DM_OPT_SLOTS says
+    // sketches with keys in device memory keep their minima in the output row (a 16-bit filter
+    // per bucket in shared memory) unless DM_OPT_SLOTS asks for shared minima
     const bool row_ok = kind == dm::kSketch && out_keys && !ctx->host_out;
-    const bool key_row = row_ok && (ch.slots == 2 || (ch.slots == 0 && k >= dm::kKeyRowMinK));
+    const bool key_row = row_ok && ch.slots != 1;
     const int wpb = ch.wpb > 0 ? ch.wpb : auto_warps(kind, k, K, key_row);
     const size_t smem_fast = dm::warp_bytes(kind, k, K, 0, key_row) * wpb,
                  smem = dm::warp_bytes(kind, k, K, 1, key_row) * wpb;
@@ -845,7 +845,7 @@ int dm_autotune(dm_ctx *ctx, const int64_t *indptr, const uint32_t *indices, con
     if (!found) ctx->tuned.push_back(TunedEntry{kind, k, K, b, best});
     if (result) {
         result->form = best.form;
-        const bool row = kind == dm::kSketch && b == 0 && (best.slots == 2 || (best.slots == 0 && k >= dm::kKeyRowMinK));
+        const bool row = kind == dm::kSketch && b == 0 && best.slots != 1;
         result->warps_per_block = best.wpb > 0 ? best.wpb : auto_warps(kind, k, K, row);
         result->phi0_1024 = (int32_t)(best.phi0 * 1024.0f + 0.5f);
         result->large_nnz = best.large_nnz;

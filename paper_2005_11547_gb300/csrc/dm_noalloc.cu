@@ -89,7 +89,7 @@ extern "C" int dm_sketch_noalloc(const int64_t *indptr, const uint32_t *indices,
     if (cap != cudaStreamCaptureStatusNone) return DM_EINVAL;     // the call synchronises its stream
 
     // warps per block: as many as fit 96 KB of shared memory, at most 8
-    const bool key_row = k >= dm::kKeyRowMinK;    // out is always given
+    const bool key_row = true;                    // out is always given: minima in the output row
     const size_t wf = dm::warp_bytes(dm::kSketch, k, 0, 0, key_row), wg = dm::warp_bytes(dm::kSketch, k, 0, 1, key_row);
     int wpb = (int)((96 * 1024) / (wf > wg ? wf : wg));
     wpb = wpb > 8 ? 8 : (wpb < 1 ? 1 : wpb);
