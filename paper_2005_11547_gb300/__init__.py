@@ -325,8 +325,9 @@ class LshIndex:
 
 
 def dm_weight_classes(ctx: Context, indptr, weights, out=None, scale_out=None, norm_exp: int = 0, stream=None):
-    """int32 weight class floor(log2 ||x||_1) of each set (fp32 norm); scale_out, when given,
-    receives norm_exp - class, the scales that put every class's norms in [2^norm_exp, 2^(norm_exp+1))."""
+    """int32 weight class floor(log2 ||x||_1) of each set, from the exact sum of its positive
+    finite weights (0 for a set without one); scale_out, when given, receives norm_exp - class,
+    the scales that put every class's norms in [2^norm_exp, 2^(norm_exp+1))."""
     import torch
     n = indptr.numel() - 1
     if out is None:

@@ -111,6 +111,28 @@ def test_bottomk_w1_prefix_autotune_graph(dmx, torch_mod, oracle_mod):
     assert_same(after.cpu().numpy().view(np.uint64), exp, "W1 prefix")
 
 
+def test_w1b_full_size_sampled(dmx, torch_mod, oracle_mod):
+    """The W1B bench workload at full size (bottom-k sketches, k = 256, of the 1,000,000 W1 sets)
+    in the bench's launch configuration (autotuned, graph replay): 300 sampled rows, including
+    the first and the last, equal the oracle's."""
+    torch = torch_mod
+    b = workloads.workload1()
+    ip, ix, w = to_dev(torch, b)
+    ctx = dmx.dm_create(0)
+    dmx.dm_autotune(ctx, ip, ix, w, 256, 1, bottomk=True)
+    dmx.dm_set_option(ctx, dmx.OPT_GRAPH, 1)
+    out = dmx.dm_bottomk(ctx, ip, ix, w, 256, 1)
+    again = dmx.dm_bottomk(ctx, ip, ix, w, 256, 1)
+    assert dmx.dm_sync_status(ctx, raise_on_error=False) == 0
+    assert torch.equal(out, again)
+    ctx.close()
+    rng = np.random.default_rng(17)
+    sel = np.unique(np.concatenate([rng.choice(b.n_sets, 298, replace=False), [0, b.n_sets - 1]]))
+    sub = b.rows(sel)
+    exp = oracle_mod.bottomk(sub.indptr, sub.indices, sub.weights, 256, 1, threads=THREADS)
+    assert_same(out.cpu().numpy().view(np.uint64)[sel], exp, "W1B")
+
+
 def test_bottomk_rejects_bad_k(dmx, torch_mod):
     b = workloads.random_sets(10, 1, 10, 1000, seed=2)
     ctx = dmx.dm_create(0)

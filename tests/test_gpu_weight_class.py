@@ -88,3 +88,29 @@ def test_weight_classes(dmx, torch_mod, oracle_mod):
     assert np.array_equal(got, exp)
     e0 = rand.n_sets
     assert got[e0:e0 + 2 * len(edges):2].tolist() == [c for _, c in edges]
+
+
+def test_w3s_full_size_sampled(dmx, torch_mod, oracle_mod):
+    """The W3S bench workload at full size: exact weight classes of the 1,000,000 W3 sets, each set
+    normalised to ||x||_1 in [4, 8) (norm_exp 2), then (64, 8) LSH values, in the bench's form;
+    the classes and values of 300 sampled rows, including the first and the last, equal the
+    oracle's."""
+    torch = torch_mod
+    b = workloads.workload3()
+    ip, ix, w = to_dev(torch, b)
+    ctx = dmx.dm_create(0)
+    dmx.dm_set_option(ctx, dmx.OPT_GRAPH, 1)
+    cls = torch.empty(b.n_sets, dtype=torch.int32, device="cuda")
+    scl = torch.empty(b.n_sets, dtype=torch.int32, device="cuda")
+    dmx.dm_weight_classes(ctx, ip, w, out=cls, scale_out=scl, norm_exp=2)
+    got = dmx.dm_lsh_scaled(ctx, ip, ix, w, 64, 8, 1, scl)
+    assert dmx.dm_sync_status(ctx, raise_on_error=False) == 0
+    ctx.close()
+    assert torch.equal(scl, 2 - cls)
+    rng = np.random.default_rng(19)
+    sel = np.unique(np.concatenate([rng.choice(b.n_sets, 298, replace=False), [0, b.n_sets - 1]]))
+    sub = b.rows(sel)
+    assert np.array_equal(cls.cpu().numpy()[sel], oracle_mod.weight_class(sub.indptr, sub.weights))
+    exp = oracle_mod.lsh(sub.indptr, sub.indices, sub.weights, 64, 8, 1, scale=scl.cpu().numpy()[sel],
+                         threads=THREADS)
+    assert np.array_equal(got.cpu().numpy().view(np.uint32)[sel], exp)
