@@ -784,20 +784,24 @@ struct WalkG {
         ++r;
         ctr += kGolden;
         if (r < rhi) return;
-        ++w;
-        if (w >= ncols) {
-            w = 0;
-            if (++rho > pc.rho_top) {
-                rho = pc.rho_lo;
-                if (++nu > nutop) {
-                    nu = 0;
-                    do { ++el; } while (el < 32 && m.tnu[el] < 0);
-                    if (el >= 32) return;         // past the tile: the lane is done
-                    load(m);
-                }
-            }
-            region(pc);
+        if (++w < ncols) {
+            // next column of the region: its row rlo is (2^nu - rhi + rlo) counter steps on
+            // (the pack holds w 2^nu + r with r < 2^nu)
+            r = rlo;
+            ctr += kGolden * ((1ull << nu) + rlo - rhi);
+            return;
         }
+        w = 0;
+        if (++rho > pc.rho_top) {
+            rho = pc.rho_lo;
+            if (++nu > nutop) {
+                nu = 0;
+                do { ++el; } while (el < 32 && m.tnu[el] < 0);
+                if (el >= 32) return;             // past the tile: the lane is done
+                load(m);
+            }
+        }
+        region(pc);
         r = rlo;
         set_ctr();
     }
