@@ -172,12 +172,17 @@ def summarize_clocks(rows):
 # traffic from the committed ncu capture (valid only for the kernel source it was taken on)
 # ------------------------------------------------------------------------------------------
 def kernel_fingerprint() -> str:
-    """Hash of the kernel sources (device code only)."""
+    """Hash of the kernel sources (device code only) with comments and blank space removed, so
+    that a change of wording does not retire a capture but any change of code does."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2005_11547_gb300", "csrc")
     for f in ("dm_sketch.cu", "dm_device.cuh"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        text = open(os.path.join(csrc, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

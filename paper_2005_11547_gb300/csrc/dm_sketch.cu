@@ -63,12 +63,13 @@ size_t lsh_sink_bytes(int L, int K) { return ((size_t)L * K * 8 + (size_t)L * 4 
 // k buckets, each the minimum key of the darts hashed to it (Theorem 1).  Two layouts, with the
 // same bits:
 //  * shared: the k 64-bit minima live in shared memory (8 k bytes per warp);
-//  * key row (p.key_row, for large k): shared memory holds only each bucket's smallest rank code
-//    (4 k bytes) and the 64-bit minimum goes straight to the set's output row in global memory
-//    (L2-resident while the set runs).  A candidate whose code exceeds the bucket's code cannot
-//    be its minimum: a dart with a smaller code was put before it, and that dart's key reached
-//    the row.  Ties in the code reach the row, whose 64-bit minimum decides them.
-// 0xFFFFFFFF marks an empty bucket's code: a kept dart's code is below bits(theta) < 0x7F800000.
+//  * key row (p.key_row, the default when keys go to device memory): shared memory holds a
+//    16-bit filter per bucket (2 k bytes) and the 64-bit minimum goes straight to the set's
+//    output row in global memory (L2-resident while the set runs).  The filter is the high half
+//    of the rank code of a dart already in the row's minimum (see put), so a candidate whose
+//    high half exceeds it cannot be the minimum; the others reach the row, whose 64-bit atomic
+//    minimum decides.
+// 0xFFFF marks an empty bucket's filter: a kept dart's code is below bits(theta) < 0x7F800000.
 __host__ __device__ size_t sketch_sink_bytes(int k, bool key_row) {
     return ((size_t)k * (key_row ? 2 : 8) + 15) & ~(size_t)15;
 }
