@@ -56,7 +56,9 @@ enum dm_status {
     DM_ETIMEOUT = 4,   /* a bounded device wait gave up */
     DM_ERANGE = 5,     /* input outside the supported numeric range (see above) */
     DM_EOVERFLOW = 6,  /* the doubling loop of Theorem 1 reached its limit */
-    DM_EAGAIN = 7      /* dm_server_submit: the admission budget is full now; retry later */
+    DM_EAGAIN = 7,     /* dm_server_submit: the admission budget is full now; retry later */
+    DM_ECHECK = 8      /* checked build only (dm_build_flags() & 1): an internal index check
+                          failed, a defect of the library; the access it guarded was skipped */
 };
 
 /* Create a context on CUDA device `device`.  `mem_budget_bytes` caps the device scratch the
@@ -244,6 +246,12 @@ int dm_sync_status(dm_ctx *ctx, void *stream);
 
 /* Static English description of a status code. */
 const char *dm_strerror(int status);
+
+/* Build flags of the loaded library: bit 0 set = the checked build (libdartminhash_checked.so,
+ * compiled with -DDM_CHECKED): every kernel also checks its shared-memory ring, table and bucket
+ * indices, records the first failed check instead of making the access, and dm_sync_status then
+ * returns DM_ECHECK.  The product build (bit 0 clear) has no such checks. */
+int32_t dm_build_flags(void);
 
 /* Tuning and instrumentation options (dm_set_option).  None of them changes any output bit. */
 enum dm_option {

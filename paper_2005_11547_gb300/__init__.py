@@ -16,11 +16,12 @@ import ctypes
 import os
 import threading
 
-from .build import LIB, build
+from .build import LIB, LIB_CHECKED, build
 
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
            "dm_sketch_host", "dm_bottomk", "dm_compare", "dm_lsh_scaled", "dm_weight_classes", "LshIndex", "estimate_jaccard", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
-           "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
+           "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "LIB_CHECKED",
+           "dm_build_flags", "ECHECK", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
            "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "OPT_LARGE_WORK", "OPT_HOST_CHUNKS", "OPT_HOST_MODE", "OPT_SLOTS", "SLOTS_AUTO", "SLOTS_SHARED", "SLOTS_ROW", "HOST_STAGED", "HOST_IN_PLACE", "HOST_AUTO", "FORM_BATCHED",
            "FORM_PLAIN", "FORM_PERSISTENT", "dm_autotune", "Tuning", "Server", "EAGAIN"]
 
@@ -28,7 +29,7 @@ OPT_PHI0, OPT_COUNTERS, OPT_FORM, OPT_WARPS_PER_BLOCK, OPT_LSH_PHI0, OPT_LARGE_N
 OPT_GRAPH, OPT_TUNED, OPT_LARGE_WORK, OPT_HOST_CHUNKS, OPT_HOST_MODE, OPT_SLOTS = 7, 8, 9, 10, 11, 12
 SLOTS_AUTO, SLOTS_SHARED, SLOTS_ROW = 0, 1, 2
 HOST_STAGED, HOST_IN_PLACE, HOST_AUTO = 0, 1, 2
-EAGAIN, ETIMEOUT = 7, 4
+EAGAIN, ETIMEOUT, ECHECK = 7, 4, 8
 FORM_BATCHED, FORM_PLAIN, FORM_PERSISTENT = 0, 1, 2
 _lock = threading.Lock()
 _lib = None
@@ -42,7 +43,8 @@ class DartMinHashError(RuntimeError):
 
 
 def load(path: str | None = None):
-    """Load libdartminhash.so (built in-tree by build()).  Raises if it is absent."""
+    """Load libdartminhash.so (built in-tree by build()), or the library at `path` (e.g.
+    LIB_CHECKED, the checked build), once per process.  Raises if it is absent."""
     global _lib
     with _lock:
         if _lib is not None:
@@ -75,6 +77,7 @@ def load(path: str | None = None):
             "dm_mix64_burn": ([i64, i32, u64, P, P], ctypes.c_int),
             "dm_sync_status": ([P, P], ctypes.c_int),
             "dm_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "dm_build_flags": ([], ctypes.c_int32),
             "dm_set_option": ([P, ctypes.c_int, i64], ctypes.c_int),
             "dm_t_of_k": ([i32], i64),
             "dm_set_tuning": ([P, i32, i32, i32, P], ctypes.c_int),
@@ -510,6 +513,12 @@ def dm_sync_status(ctx: Context, stream=None, raise_on_error: bool = True) -> in
 
 def dm_strerror(code: int) -> str:
     return load().dm_strerror(int(code)).decode()
+
+
+def dm_build_flags() -> int:
+    """Build flags of the loaded library: bit 0 = the checked build (index checks in every kernel,
+    failures reported as DM_ECHECK by dm_sync_status)."""
+    return int(load().dm_build_flags())
 
 
 def dm_set_option(ctx: Context, option: int, value: int) -> None:

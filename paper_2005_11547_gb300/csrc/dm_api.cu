@@ -871,7 +871,18 @@ int dm_sync_status(dm_ctx *ctx, void *stream) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return DM_ECUDA;
     }
+    int line = 0;                                 // the checked build's index checks
+    if (dm::take_check_line(&line, st) != cudaSuccess) return DM_ECUDA;
+    if (line) return DM_ECHECK;
     return s;
+}
+
+int32_t dm_build_flags(void) {
+#ifdef DM_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 const char *dm_strerror(int status) {
@@ -884,6 +895,7 @@ const char *dm_strerror(int status) {
         case DM_ERANGE: return "input outside the supported numeric range";
         case DM_EOVERFLOW: return "rank-limit doubling reached its limit";
         case DM_EAGAIN: return "admission budget full; retry later";
+        case DM_ECHECK: return "an index check of the checked build failed (a library defect)";
         default: return "unknown status";
     }
 }

@@ -194,4 +194,19 @@ __device__ __forceinline__ void set_status(int *status, int code) {
     if (status) atomicCAS(status, 0, code);
 }
 
+// Index checks of the checked build (compiled with -DDM_CHECKED; the product build compiles them
+// out).  DM_EXPECT(cond) is true when cond holds; when it does not, the source line of the first
+// failed check is recorded in g_dm_check (read and cleared by dm_sync_status, which then returns
+// DM_ECHECK) and the caller skips the access it guards.
+#ifdef DM_CHECKED
+static __device__ int g_dm_check = 0;             // per translation unit; the sketch kernels' is read
+__device__ __forceinline__ bool dm_expect(bool ok, int line) {
+    if (!ok) atomicCAS(&g_dm_check, 0, line);
+    return ok;
+}
+#define DM_EXPECT(cond) ::dm::dm_expect((cond), __LINE__)
+#else
+#define DM_EXPECT(cond) true
+#endif
+
 }  // namespace dm

@@ -71,6 +71,10 @@ int blocks_per_sm(int kind, int mode, bool bbit, int warps_per_block, size_t sme
 
 cudaError_t upload_poisson_table(const uint32_t *T);
 
+// Checked build only (-DDM_CHECKED): the line of the first failed index check since the last call,
+// cleared on reading (0: none; the product build always reports 0).  Synchronises st.
+cudaError_t take_check_line(int *line, cudaStream_t st);
+
 // Raises the dynamic shared-memory limit of every sketch kernel to the device's opt-in maximum,
 // once per device (thread-safe; the device must be current).  Must precede the first launch.
 cudaError_t allow_max_shared_memory(int device);

@@ -106,6 +106,7 @@ struct SketchSinkT {
     __device__ __forceinline__ bool put(uint64_t qh, uint32_t code) {
         const uint32_t slot = fastrange32((uint32_t)(qh >> 32), k);
         const uint64_t key = ((uint64_t)code << 32) | (uint32_t)qh;
+        if (!DM_EXPECT(slot < k)) return false;
         if constexpr (KEYROW) {
             // The filter holds the high 16 bits of the code of a dart already in the bucket's
             // row minimum, so it is at least the high half of the row minimum's code; a dart
@@ -205,6 +206,7 @@ struct LshSink {
     }
     // insertion of key into bucket b's sorted keys (the caller owns bucket b for this call)
     __device__ __forceinline__ void insert(uint32_t b, uint64_t key) {
+        if (!DM_EXPECT(b < L && cnt[b] <= K)) return;
         uint64_t *v = buf + (size_t)b * K;
         uint32_t n = cnt[b];
         if (n == K) {
@@ -294,7 +296,7 @@ struct BottomKSink {
         const uint64_t key = ((uint64_t)code << 32) | (uint32_t)qh;
         if (key >= *tau) return false;
         const uint32_t pos = atomicAdd(cnt, 1u);          // < C: at most 32 puts per batch
-        buf[pos] = key;
+        if (DM_EXPECT(pos < C)) buf[pos] = key;
         return pos + 33 > C;
     }
     __device__ void compact(int lane) {
@@ -429,6 +431,7 @@ struct WalkF {
     uint64_t kt, ctr;
 
     __device__ __forceinline__ void region(const FastMem &m) {
+        if (!DM_EXPECT(nu >= 0 && nu < kFastRegions)) nu = 0;
         const uint4 a = *reinterpret_cast<const uint4 *>(&m.ra[nu]);          // kt, lastthr, firstlo
         const uint4 b = *reinterpret_cast<const uint4 *>(&m.rb[nu]);          // rlo, rhi, cnt, C
         kt = ((uint64_t)a.y << 32) | a.x;
@@ -441,6 +444,7 @@ struct WalkF {
     // element q of region nu at row r: counter e + kt + gamma (r - rlo); the v limit of the
     // element's last region
     __device__ __forceinline__ void element(const FastMem &m) {
+        if (!DM_EXPECT(q >= 0 && q < kSeg)) q = 0;
         const uint4 e = *reinterpret_cast<const uint4 *>(&m.el[q]);
         ctr = (((uint64_t)e.y << 32) | e.x) + kt + kGolden * (uint64_t)(r - rlo);
         vmax = (int)(signed char)(e.w >> 24) == nu ? (e.w & kUMask) : kUMask;
@@ -502,6 +506,7 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         const unsigned km = __ballot_sync(kFull, keep);
         if (keep) m.kq[(kt + __popc(km & lt)) & (kQ - 1)] = make_uint4((uint32_t)d, (uint32_t)(d >> 32), r, nu);
         kt += __popc(km);
+        (void)DM_EXPECT(kt - kh <= (uint32_t)kQ);     // the ring never overwrites an unserved entry
         if (COUNT && keep) cnt[2]++;
     };
     auto push_darts = [&](bool more, uint64_t op, uint32_t w0, uint32_t w1, uint32_t r, uint32_t up, uint32_t ulo) {
@@ -513,6 +518,7 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
             if constexpr (LOWER) m.xl[i] = ulo;
         }
         xt += __popc(xm);
+        (void)DM_EXPECT(xt - xh <= (uint32_t)kQ);
     };
     // bucket step over the n (<= 32) oldest kept darts
     auto kept_step = [&](uint32_t n) {
@@ -604,7 +610,7 @@ __device__ int fast_pass(const SketchParams &p, int64_t first, int64_t stride, i
         if (lane < nlo) mycnt = placed;
 #pragma unroll
         for (int t = 0; t < kSegTiles; ++t)
-            if (nut[t] >= 0)
+            if (nut[t] >= 0 && DM_EXPECT(rank[t] < (uint32_t)kSeg))
                 *reinterpret_cast<uint4 *>(&m.el[rank[t]]) =
                     make_uint4((uint32_t)et[t], (uint32_t)(et[t] >> 32), 0u, vt[t] | ((uint32_t)nut[t] << 24));
         // region nu = lane holds cnt(nu) rows(nu) areas; C(nu) is their offset in the segment
@@ -748,6 +754,7 @@ struct WalkG {
     }
     __device__ void set_ctr() { ctr = e + kGolden * ((packhi | (w << nu) | r) + 1); }
     __device__ void load(const GenMem &m) {
+        if (!DM_EXPECT(el >= 0 && el < 32)) el = 0;
         e = m.te[el];
         F = m.tF[el];
         nutop = m.tnu[el];
@@ -831,6 +838,7 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
         const unsigned km = __ballot_sync(kFull, keep);
         if (keep) m.kq[(kt + __popc(km & lt)) & (kQ - 1)] = make_uint4((uint32_t)d, (uint32_t)(d >> 32), code, 0u);
         kt += __popc(km);
+        (void)DM_EXPECT(kt - kh <= (uint32_t)kQ);
         if (COUNT && keep) cnt[2]++;
     };
     auto push_darts = [&](bool more, uint64_t op, uint64_t pv, uint32_t w, uint32_t ua) {
@@ -841,6 +849,7 @@ __device__ int gen_pass(const SketchParams &p, int64_t first, int64_t stride, in
             m.xb[i] = make_uint2(w, ua);
         }
         xt += __popc(xm);
+        (void)DM_EXPECT(xt - xh <= (uint32_t)kQ);
     };
     // bucket step over the n (<= 32) oldest kept darts
     auto kept_step = [&](uint32_t n) {
@@ -1329,6 +1338,25 @@ void carve_call_scratch(void *base, int64_t n_sets, SketchParams &p) {
     p.queue_count = (unsigned int *)(b + 2 * a + c);
     p.work_next = p.queue_count + 1;
     p.hist = p.queue_count + 4;
+}
+
+// Checked build: the source line of the first failed index check since the last call (0:
+// none), cleared on reading.  The product build has no checks and returns 0.
+cudaError_t take_check_line(int *line, cudaStream_t st) {
+    *line = 0;
+#ifdef DM_CHECKED
+    cudaError_t e = cudaMemcpyFromSymbolAsync(line, g_dm_check, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && *line) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbolAsync(g_dm_check, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    return e;
+#else
+    (void)st;
+    return cudaSuccess;
+#endif
 }
 
 cudaError_t upload_poisson_table(const uint32_t *T) {

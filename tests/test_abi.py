@@ -42,6 +42,19 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n)
 
 
+def test_checked_build_exports_the_same_symbols(lib):
+    """The checked build (index checks compiled in) is built beside the product library, loads
+    without a GPU, exports every declared symbol and says that it is the checked build."""
+    import paper_2005_11547_gb300 as pkg
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.LIB_CHECKED], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (dm_[a-z_0-9]+)", out))
+    assert not [n for n in declared_functions() if n not in exported]
+    checked = ctypes.CDLL(pkg.LIB_CHECKED)
+    checked.dm_build_flags.restype = ctypes.c_int32
+    assert checked.dm_build_flags() & 1 == 1
+    assert pkg.dm_build_flags() & 1 == 0
+
+
 def test_header_compiles_as_c(tmp_path):
     src = tmp_path / "h.c"
     src.write_text('#include "dartminhash.h"\nint main(void){return DM_OK;}\n')
