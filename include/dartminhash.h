@@ -172,6 +172,19 @@ int dm_compare(dm_ctx *ctx, const uint64_t *a, const uint64_t *c, int64_t n_a, i
  * context; runs on the current device, asynchronously on `stream`. */
 int dm_estimate_jaccard(const uint32_t *matches, int64_t n, int32_t k, int32_t bits, double *out, void *stream);
 
+/* Top-k neighbours by estimated similarity (Section 1.1, "Similarity estimation": the agreeing
+ * slots m of two sketches estimate their weighted Jaccard similarity, so the rows of c with the
+ * largest m are the most similar): for each row i of a, the `topk` rows j of c with the largest
+ * dm_compare count m(i, j), in decreasing order of m, rows with equal m in increasing order of j.
+ * Rows as for dm_compare (bits = 0: k uint64 keys; bits = b: W = ceil(k b / 64) words of b-bit
+ * fields, W <= 64), from the same k, b and seed.  out_idx, out_count: device uint32[n_a * topk];
+ * entry i * topk + t is the t-th neighbour of row i and its count; when n_c < topk the entries
+ * past n_c are 0xFFFFFFFF with count 0.  1 <= topk <= 32, n_c < 2^31.  Asynchronous on `stream`
+ * (scratch of 8 n_a topk bytes per span of c rows is allocated stream-ordered when the search
+ * splits c into spans). */
+int dm_compare_topk(dm_ctx *ctx, const uint64_t *a, const uint64_t *c, int64_t n_a, int64_t n_c, int32_t k,
+                    int32_t bits, int32_t topk, uint32_t *out_idx, uint32_t *out_count, void *stream);
+
 /* Wide-range minhash keys: 64-bit element ids and binary64 weights, for the norms the binary32
  * entry points cannot reach (Section 4, "Synthetic data", hashes 64-bit ids with double weights;
  * Table 1 runs ||x||_1 = 2^{+-64} and 2^{+-512}).  Same dart process as dm_sketch (Section 2,

@@ -354,6 +354,28 @@ def compare(a, c, k: int, bits: int = 0, mode: str = "pairs"):
     return np.stack([(va[i][None, :] == vc).sum(axis=1) for i in range(len(va))]).astype(np.uint32)
 
 
+def compare_topk(a, c, k: int, topk: int, bits: int = 0):
+    """Top-k neighbours by estimated similarity (Section 1.1, "Similarity estimation": m / k
+    estimates J, so the rows with the most agreeing slots are the most similar): for each row i
+    of a, the topk rows j of c with the largest count m(i, j) of compare(..., mode="cross"), in
+    decreasing order of m, equal m in increasing order of j.  Returns (rows uint32[n_a, topk],
+    counts uint32[n_a, topk]); entries past n_c are 0xFFFFFFFF with count 0.  The selection is a
+    stable sort of each row of counts."""
+    a = np.asarray(a, dtype=np.uint64)
+    c = np.asarray(c, dtype=np.uint64)
+    n_a = len(a)
+    rows = np.full((n_a, topk), 0xFFFFFFFF, dtype=np.uint32)
+    counts = np.zeros((n_a, topk), dtype=np.uint32)
+    if len(c) == 0:
+        return rows, counts
+    m = compare(a, c, k, bits, mode="cross").astype(np.int64)
+    for i in range(n_a):
+        order = np.argsort(-m[i], kind="stable")[:topk]      # stable: equal counts keep row order
+        rows[i, :len(order)] = order
+        counts[i, :len(order)] = m[i, order]
+    return rows, counts
+
+
 def estimate_jaccard(matches, k: int, bits: int = 0):
     """Weighted Jaccard estimates from agreeing-slot counts m (Section 1.1, "Similarity estimation"):
     m / k for keys, since E[m] = k J (Eq. 1); for b-bit fields E[m] = k (J + (1 - J) 2^-b), which

@@ -19,7 +19,7 @@ import threading
 from .build import LIB, LIB_CHECKED, build
 
 __all__ = ["DartMinHashError", "dm_create", "dm_destroy", "dm_sketch", "dm_sketch_bbit", "dm_lsh",
-           "dm_sketch_host", "dm_bottomk", "dm_compare", "dm_lsh_scaled", "dm_weight_classes", "LshIndex", "estimate_jaccard", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
+           "dm_sketch_host", "dm_bottomk", "dm_compare", "dm_compare_topk", "dm_lsh_scaled", "dm_weight_classes", "LshIndex", "estimate_jaccard", "dm_sync_status", "dm_strerror", "dm_set_option", "dm_t_of_k",
            "dm_poisson_thresholds", "dm_sketch_noalloc", "NOALLOC_MAX_SETS", "load", "build", "LIB", "LIB_CHECKED",
            "dm_build_flags", "ECHECK", "OPT_PHI0", "OPT_COUNTERS", "OPT_FORM",
            "OPT_WARPS_PER_BLOCK", "OPT_LSH_PHI0", "OPT_LARGE_NNZ", "OPT_GRAPH", "OPT_TUNED", "OPT_LARGE_WORK", "OPT_HOST_CHUNKS", "OPT_HOST_MODE", "OPT_SLOTS", "SLOTS_AUTO", "SLOTS_SHARED", "SLOTS_ROW", "HOST_STAGED", "HOST_IN_PLACE", "HOST_AUTO", "FORM_BATCHED",
@@ -63,6 +63,7 @@ def load(path: str | None = None):
             "dm_bottomk": ([P, P, P, P, i64, i32, u64, P, P], ctypes.c_int),
             "dm_compare": ([P, P, P, i64, i64, i32, i32, i32, P, P], ctypes.c_int),
             "dm_estimate_jaccard": ([P, i64, i32, i32, P, P], ctypes.c_int),
+            "dm_compare_topk": ([P, P, P, i64, i64, i32, i32, i32, P, P, P], ctypes.c_int),
             "dm_lsh_scaled": ([P, P, P, P, i64, i32, i32, u64, P, P, P], ctypes.c_int),
             "dm_lsh_index_create": ([ctypes.POINTER(P), ctypes.c_int, i32, i64], ctypes.c_int),
             "dm_lsh_index_insert": ([P, P, P, i64, P], ctypes.c_int),
@@ -377,6 +378,29 @@ def dm_compare(ctx: Context, a, c, k: int, bits: int = 0, cross: bool = False, o
                              int(bits), 1 if cross else 0, _dev_ptr(out, "uint32", "out"), _stream(stream)),
            "dm_compare")
     return out
+
+
+def dm_compare_topk(ctx: Context, a, c, k: int, topk: int, bits: int = 0, out_idx=None, out_count=None,
+                    stream=None):
+    """For each row of a, the `topk` rows of c with the most agreeing slots (ties: smaller row
+    first), as (rows, counts): uint32 tensors (int32 holding the same bits) of shape
+    (n_a, topk); rows past n_c are 0xFFFFFFFF with count 0.  Rows as for dm_compare."""
+    import torch
+    n_a, n_c = a.shape[0], c.shape[0]
+    if k >= 1 and bits in (0, 1, 2, 4, 8, 16, 32):        # other values: the library rejects them
+        row = k if bits == 0 else (k * bits + 63) // 64
+        _need(a, n_a * row, "a")
+        _need(c, n_c * row, "c")
+    if out_idx is None:
+        out_idx = torch.empty((n_a, topk), dtype=torch.int32, device=a.device)
+    if out_count is None:
+        out_count = torch.empty((n_a, topk), dtype=torch.int32, device=a.device)
+    _need(out_idx, n_a * topk, "out_idx")
+    _need(out_count, n_a * topk, "out_count")
+    _check(load().dm_compare_topk(ctx.handle, _dev_ptr(a, "uint64", "a"), _dev_ptr(c, "uint64", "c"), n_a, n_c,
+                                  int(k), int(bits), int(topk), _dev_ptr(out_idx, "uint32", "out_idx"),
+                                  _dev_ptr(out_count, "uint32", "out_count"), _stream(stream)), "dm_compare_topk")
+    return out_idx, out_count
 
 
 def estimate_jaccard(matches, k: int, bits: int = 0, out=None, stream=None):

@@ -116,3 +116,70 @@ def test_compare_rejects_bad_arguments(dmx, torch_mod, ctx):
         dmx.dm_compare(ctx, a, a, 8, bits=3)
     with pytest.raises(dmx.DartMinHashError):
         dmx.dm_compare(ctx, a, a, 0)
+
+
+@pytest.mark.parametrize("bits", [0, 1, 8])
+@pytest.mark.parametrize("nc", [5, 70, 3000])
+def test_topk_parity(dmx, torch_mod, ctx, oracle_mod, bits, nc):
+    """dm_compare_topk against the oracle's stable selection: counts drawn from a small alphabet,
+    so many candidates tie and the row order decides; n_c below topk, within one tile, and over
+    several spans of c (folded by the merge kernel); query rows ragged against the tile."""
+    rng = np.random.default_rng(77 + bits + nc)
+    k, na = (37 if bits == 0 else 64), 45
+    if bits == 0:
+        a = rng.integers(0, 3, size=(na, k), dtype=np.uint64)
+        c = rng.integers(0, 3, size=(nc, k), dtype=np.uint64)
+    else:
+        W = (k * bits + 63) // 64
+        pat = rng.integers(0, 2 ** 63, size=(4, W), dtype=np.uint64)     # few distinct words: ties
+        a = pat[rng.integers(0, 4, size=(na, W)), np.arange(W)]
+        c = pat[rng.integers(0, 4, size=(nc, W)), np.arange(W)]
+    for topk in (1, 7, 32):
+        rows, counts = dmx.dm_compare_topk(ctx, dev(torch_mod, a), dev(torch_mod, c), k, topk, bits=bits)
+        er, ec = oracle_mod.compare_topk(a, c, k, topk, bits=bits)
+        assert np.array_equal(rows.cpu().numpy().view(np.uint32), er), (bits, nc, topk)
+        assert np.array_equal(counts.cpu().numpy().view(np.uint32), ec), (bits, nc, topk)
+
+
+def test_topk_many_spans_and_library_sketches(dmx, torch_mod, ctx, oracle_mod):
+    """Sketches made by dm_sketch: 5 queries against 50,000 candidates (many spans) that include
+    a copy of each query and a J = 0.9 neighbour; the result equals the oracle's selection and
+    ranks the copy first with all k slots agreeing."""
+    torch = torch_mod
+    rng = np.random.default_rng(31)
+    k = 64
+    base = workloads.random_sets(50_000 - 10, 10, 60, 1 << 20, seed=41)
+    q_rows, near_rows = [], []
+    for _ in range(5):
+        ix, wx, iy, wy = workloads.similar_pair(rng, 40, 2 * 0.9 / 1.9)
+        q_rows.append((ix, wx))
+        near_rows.append((iy, wy))
+    qb = workloads.csr_of(q_rows)
+    rows_c = [(base.indices[base.indptr[i]:base.indptr[i + 1]], base.weights[base.indptr[i]:base.indptr[i + 1]])
+              for i in range(base.n_sets)] + near_rows + q_rows
+    cb = workloads.csr_of(rows_c)
+
+    def sketch(b):
+        return dmx.dm_sketch(ctx, torch.from_numpy(b.indptr).cuda(), torch.from_numpy(b.indices.view(np.int32)).cuda(),
+                             torch.from_numpy(b.weights).cuda(), k, 4)
+
+    qa, ca = sketch(qb), sketch(cb)
+    rows, counts = dmx.dm_compare_topk(ctx, qa, ca, k, 10)
+    er, ec = oracle_mod.compare_topk(qa.cpu().numpy().view(np.uint64), ca.cpu().numpy().view(np.uint64), k, 10)
+    assert np.array_equal(rows.cpu().numpy().view(np.uint32), er)
+    assert np.array_equal(counts.cpu().numpy().view(np.uint32), ec)
+    n0 = base.n_sets
+    for i in range(5):
+        assert ec[i, 0] == k and n0 + 5 + i in er[i, :2]           # the copy (the neighbour may tie it)
+        assert n0 + i in er[i, :3]
+
+
+def test_topk_rejects_bad_arguments(dmx, torch_mod, ctx):
+    a = torch_mod.zeros((4, 16), dtype=torch_mod.int64, device="cuda")
+    for topk in (0, 33):
+        with pytest.raises(dmx.DartMinHashError):
+            dmx.dm_compare_topk(ctx, a, a, 16, topk)
+    with pytest.raises(dmx.DartMinHashError):
+        dmx.dm_compare_topk(ctx, a, a, 16, 4, bits=3)
+    rows, counts = dmx.dm_compare_topk(ctx, a, a[:0], 16, 4)             # no candidates
+    assert np.all(rows.cpu().numpy().view(np.uint32) == 0xFFFFFFFF) and not counts.any()

@@ -86,3 +86,45 @@ def test_estimator_is_unbiased_and_fixes_its_end_points(oracle_mod):
             p = J if bits == 0 else J + (1 - J) / 2 ** bits
             mean = sum(comb(k, i) * p ** i * (1 - p) ** (k - i) * Fraction(float(est[i])) for i in range(k + 1))
             assert abs(float(mean - J)) < 1e-12, (bits, J)
+
+
+def test_topk_matches_a_plain_selection(oracle_mod):
+    """compare_topk against a selection written out here: the topk rows by (count descending,
+    row ascending), counts recounted slot by slot, padding past n_c."""
+    rng = np.random.default_rng(21)
+    k = 16
+    a = rng.integers(0, 3, size=(7, k), dtype=np.uint64)
+    c = rng.integers(0, 3, size=(23, k), dtype=np.uint64)
+    for topk in (1, 5, 23, 30):
+        rows, counts = oracle_mod.compare_topk(a, c, k, topk)
+        for i in range(7):
+            m = [sum(1 for q in range(k) if a[i, q] == c[j, q]) for j in range(23)]
+            ranked = sorted(range(23), key=lambda j: (-m[j], j))[:topk]
+            assert list(rows[i, :len(ranked)]) == ranked
+            assert list(counts[i, :len(ranked)]) == [m[j] for j in ranked]
+            assert np.all(rows[i, len(ranked):] == 0xFFFFFFFF) and np.all(counts[i, len(ranked):] == 0)
+    rows, counts = oracle_mod.compare_topk(a, c[:0], k, 4)
+    assert np.all(rows == 0xFFFFFFFF) and np.all(counts == 0)
+
+
+def test_topk_finds_planted_copies(oracle_mod):
+    """Through real sketches: a set's own sketch among others is its first neighbour with all k
+    slots agreeing, and a near-duplicate (J = 0.9) outranks unrelated sets."""
+    rng = np.random.default_rng(8)
+    k, n = 128, 60
+    base = workloads.random_sets(n, 20, 60, 1 << 20, seed=33)
+    q_rows, near_rows = [], []
+    for i in range(3):
+        ix, wx, iy, wy = workloads.similar_pair(rng, 40, 2 * 0.9 / 1.9)     # J = 0.9
+        q_rows.append((ix, wx))
+        near_rows.append((iy, wy))
+    qb = workloads.csr_of(q_rows)
+    base_rows = [(base.indices[base.indptr[i]:base.indptr[i + 1]], base.weights[base.indptr[i]:base.indptr[i + 1]])
+                 for i in range(n)]
+    cb = workloads.csr_of(base_rows + near_rows + [q_rows[0]])
+    qa = oracle_mod.sketch(qb.indptr, qb.indices, qb.weights, k, 4, threads=THREADS)
+    ca = oracle_mod.sketch(cb.indptr, cb.indices, cb.weights, k, 4, threads=THREADS)
+    rows, counts = oracle_mod.compare_topk(qa, ca, k, 3)
+    assert rows[0, 0] == n + 3 and counts[0, 0] == k               # the planted copy of query 0
+    for i in range(3):
+        assert n + i in rows[i, :2]                                 # the J = 0.9 neighbour
