@@ -751,6 +751,16 @@ def compare_arm(args):
     e2[1].record(stream)
     torch.cuda.synchronize()
     cross1_s = e2[0].elapsed_time(e2[1]) / 3e3
+    # top-10 neighbours of each query row among the 131,072 rows (dm_compare_topk), keys and 1-bit
+    topk_s = {}
+    for name, qq, cc, bits in (("keys", qa, qc, 0), ("one_bit", wa, wc, 1)):
+        dmx.dm_compare_topk(ctx, qq, cc, k, 10, bits=bits, stream=stream)
+        e2[0].record(stream)
+        for _ in range(3):
+            dmx.dm_compare_topk(ctx, qq, cc, k, 10, bits=bits, stream=stream)
+        e2[1].record(stream)
+        torch.cuda.synchronize()
+        topk_s[name] = e2[0].elapsed_time(e2[1]) / 3e3
     ctx.close()
     if rank == 0:
         line = {
@@ -765,6 +775,10 @@ def compare_arm(args):
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"},
             "cross": {"keys_pairs_per_s": 2048 * 131072 / cross_s, "one_bit_pairs_per_s": 2048 * 131072 / cross1_s,
                       "shape": "2,048 x 131,072 rows, k = 256"},
+            "topk": {"k_neighbours": 10, "shape": "2,048 queries x 131,072 rows, k = 256",
+                     "keys_queries_per_s": 2048 / topk_s["keys"], "keys_pairs_per_s": 2048 * 131072 / topk_s["keys"],
+                     "one_bit_queries_per_s": 2048 / topk_s["one_bit"],
+                     "one_bit_pairs_per_s": 2048 * 131072 / topk_s["one_bit"]},
             "cpu_baseline": None, "e2e": None, "clocks": clocks, "gpu_launches": args.steps,
         }
         print(json.dumps(line), flush=True)
